@@ -1,0 +1,166 @@
+"""CPU oracle for the dense assignment problem (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
+import this package. It shares no code with the CUDA path in
+``paper_1110_6231_gb300``; the two meet only in the seeded inputs of
+``paper_1110_6231_gb300.synth``.
+
+The arithmetic lives in ``oracle.c`` (plain C, exact int64); this module
+builds it with gcc on first use and marshals numpy arrays. Functions:
+
+* ``brute_force(C)``      -- min over all n! permutations (n <= 10).
+* ``hungarian(C)``        -- shortest-augmenting-path Hungarian method with
+  integer duals ``u, v`` (Kuhn 1955 / Munkres 1957; not from the paper).
+* ``cost_scaling(C, ...)`` -- the paper's sequential cost scaling: Algorithm
+  5.0's epsilon loop, Algorithm 5.2's refine initialisation and Algorithm 5.4's
+  push/relabel taken as the Goldberg-Kennedy double push, on costs scaled by
+  n + 1.
+* ``check_matching``, ``check_duals``, ``check_eps_cs`` -- certificates.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, INVALID, INVARIANT, OVERFLOW, NOMEM = 0, 1, 2, 3, 4
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``liboracle.so`` next to it (gcc, -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                               "-Wall", "-Wextra", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            i32, i64 = ctypes.c_int32, ctypes.c_int64
+            lib.or_brute_force.argtypes = [P, i32, P, P]
+            lib.or_hungarian.argtypes = [P, i32, P, P, P, P]
+            lib.or_cost_scaling.argtypes = [P, i32, i32, i64, P, i64, i32, P, P, P, P]
+            lib.or_check_matching.argtypes = [P, i32, P, i64]
+            lib.or_check_duals.argtypes = [P, i32, P, P, P]
+            lib.or_check_eps_cs.argtypes = [P, i32, P, P, i64]
+            for f in (lib.or_brute_force, lib.or_hungarian, lib.or_cost_scaling,
+                      lib.or_check_matching, lib.or_check_duals, lib.or_check_eps_cs):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _costs(C) -> np.ndarray:
+    C = np.ascontiguousarray(C, dtype=np.int32)
+    if C.ndim != 2 or C.shape[0] != C.shape[1]:
+        raise ValueError("cost matrix must be square")
+    return C
+
+
+def brute_force(C):
+    """Exact optimum by enumeration. Returns ``(cost, match)``."""
+    C = _costs(C)
+    n = C.shape[0]
+    match = np.zeros(n, dtype=np.int32)
+    cost = np.zeros(1, dtype=np.int64)
+    rc = _load().or_brute_force(_ptr(C), n, _ptr(match), _ptr(cost))
+    if rc:
+        raise OracleError(f"or_brute_force returned {rc}")
+    return int(cost[0]), match
+
+
+def hungarian(C):
+    """Exact optimum with integer duals. Returns ``(cost, match, u, v)``."""
+    C = _costs(C)
+    n = C.shape[0]
+    match = np.zeros(n, dtype=np.int32)
+    cost = np.zeros(1, dtype=np.int64)
+    u = np.zeros(n, dtype=np.int64)
+    v = np.zeros(n, dtype=np.int64)
+    rc = _load().or_hungarian(_ptr(C), n, _ptr(match), _ptr(cost), _ptr(u), _ptr(v))
+    if rc:
+        raise OracleError(f"or_hungarian returned {rc}")
+    return int(cost[0]), match, u, v
+
+
+def cost_scaling(C, alpha: int = 10, eps0: int = 0, init_prices=None,
+                 final_eps: int = 1, check: bool = False):
+    """Sequential cost scaling. Returns ``(cost, match, prices, stats)``.
+
+    ``prices`` are the final column prices in the paper's sign, on costs
+    scaled by n + 1; ``stats`` is a dict with ``phases``, ``scans``
+    (row scans = double pushes), ``displaced`` and ``eps_first``.
+    """
+    C = _costs(C)
+    n = C.shape[0]
+    match = np.zeros(n, dtype=np.int32)
+    cost = np.zeros(1, dtype=np.int64)
+    prices = np.zeros(n, dtype=np.int64)
+    stats = np.zeros(4, dtype=np.int64)
+    ip = None if init_prices is None else np.ascontiguousarray(init_prices, dtype=np.int64)
+    rc = _load().or_cost_scaling(_ptr(C), n, int(alpha), int(eps0), _ptr(ip),
+                                 int(final_eps), int(bool(check)), _ptr(match),
+                                 _ptr(cost), _ptr(prices), _ptr(stats))
+    if rc:
+        raise OracleError(f"or_cost_scaling returned {rc}")
+    st = dict(phases=int(stats[0]), scans=int(stats[1]), displaced=int(stats[2]),
+              eps_first=int(stats[3]))
+    return int(cost[0]), match, prices, st
+
+
+def check_matching(C, match, claimed_cost) -> int:
+    C = _costs(C)
+    m = np.ascontiguousarray(match, dtype=np.int32)
+    return _load().or_check_matching(_ptr(C), C.shape[0], _ptr(m), int(claimed_cost))
+
+
+def check_duals(C, match, u, v) -> int:
+    C = _costs(C)
+    m = np.ascontiguousarray(match, dtype=np.int32)
+    u = np.ascontiguousarray(u, dtype=np.int64)
+    v = np.ascontiguousarray(v, dtype=np.int64)
+    return _load().or_check_duals(_ptr(C), C.shape[0], _ptr(m), _ptr(u), _ptr(v))
+
+
+def check_eps_cs(C, match, prices, eps: int = 1) -> int:
+    C = _costs(C)
+    m = np.ascontiguousarray(match, dtype=np.int32)
+    p = np.ascontiguousarray(prices, dtype=np.int64)
+    return _load().or_check_eps_cs(_ptr(C), C.shape[0], _ptr(m), _ptr(p), int(eps))
+
+
+def eps_schedule(Ct: int, alpha: int = 10, eps0: int = 0, final_eps: int = 1):
+    """The epsilon of every refine phase: eps <- max(1, eps // alpha), starting
+    from eps0 (default C~), until the phase run at eps <= final_eps."""
+    eps = eps0 if eps0 > 0 else Ct
+    out = []
+    while True:
+        eps = max(1, eps // alpha)
+        out.append(eps)
+        if eps <= final_eps:
+            return out

@@ -1,0 +1,339 @@
+/*
+ * Oracle for the dense assignment problem: plain, sequential, slow and
+ * obviously correct CPU code.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and the CPU
+ * baseline legs of bench.py load this library. The CUDA product path shares
+ * no code, header, table or helper with it and never calls it.
+ *
+ * Problem (Sect. 2, definitions of matching, perfect matching, assignment and
+ * cost; Sect. 5, reduction of the assignment problem to min-cost flow with
+ * u(x,y)=1, c(x,y)=w(x,y)): given an n x n integer matrix C (row x = left
+ * vertex, column y = right vertex), find a perfect matching M minimising
+ * sum_x C[x][M(x)]. The paper states assignment as a maximum-weight problem
+ * but its reduction sets c = w and runs a min-cost flow; this oracle
+ * minimises, and a maximising caller passes a negated or offset matrix.
+ *
+ * Three independent computations of the same optimum:
+ *   or_brute_force  - the definition itself, all n! permutations (n <= 10).
+ *   or_hungarian    - the shortest-augmenting-path Hungarian method with
+ *                     integer dual potentials (Kuhn 1955, Munkres 1957, with
+ *                     the potentials of Edmonds and Karp 1972). Not from the
+ *                     paper: an independent ground truth that certifies itself
+ *                     by LP duality.
+ *   or_cost_scaling - the paper's sequential cost-scaling method: the outer
+ *                     epsilon loop of Algorithm 5.0, the refine initialisation
+ *                     of Algorithm 5.2 (unmatch all, p(x) implicit), and the
+ *                     push/relabel step of Algorithm 5.4 taken as the
+ *                     Goldberg-Kennedy double push (the paper's reference [9]).
+ * and certificate checkers for any claimed matching.
+ *
+ * All arithmetic is exact int64.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_INVALID 1
+#define OR_INVARIANT 2
+#define OR_OVERFLOW 3
+#define OR_NOMEM 4
+
+#define OR_INF (INT64_MAX / 4)
+
+/* ------------------------------------------------------------------ */
+/* Brute force: enumerate every permutation (Heap's algorithm).        */
+/* ------------------------------------------------------------------ */
+int or_brute_force(const int32_t *C, int32_t n, int32_t *match, int64_t *cost)
+{
+    if (n < 0 || n > 10 || (n > 0 && (!C || !match)) || !cost)
+        return OR_INVALID;
+    if (n == 0) { *cost = 0; return OR_OK; }
+    int32_t perm[10], cnt[10];
+    for (int i = 0; i < n; ++i) { perm[i] = i; cnt[i] = 0; }
+    int64_t best = 0;
+    for (int x = 0; x < n; ++x) best += C[(int64_t)x * n + perm[x]];
+    memcpy(match, perm, sizeof(int32_t) * n);
+    int i = 1;
+    while (i < n) {
+        if (cnt[i] < i) {
+            int j = (i % 2 == 0) ? 0 : cnt[i];
+            int32_t t = perm[j]; perm[j] = perm[i]; perm[i] = t;
+            int64_t s = 0;
+            for (int x = 0; x < n; ++x) s += C[(int64_t)x * n + perm[x]];
+            if (s < best) { best = s; memcpy(match, perm, sizeof(int32_t) * n); }
+            cnt[i]++;
+            i = 1;
+        } else {
+            cnt[i] = 0;
+            i++;
+        }
+    }
+    *cost = best;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Hungarian method, shortest augmenting paths, O(n^3).                */
+/*                                                                     */
+/* Rows enter one at a time. For the entering row a Dijkstra search    */
+/* over columns, with reduced costs C[i][j] - u[i] - v[j] >= 0, finds  */
+/* the cheapest alternating path to a free column; the duals move by   */
+/* the search distances so that every tree edge stays tight, then the  */
+/* path is flipped. Invariants: u[i] + v[j] <= C[i][j] for all i, j,   */
+/* with equality on matched pairs. Column index n is a virtual column  */
+/* that holds the entering row.                                        */
+/* ------------------------------------------------------------------ */
+int or_hungarian(const int32_t *C, int32_t n, int32_t *match, int64_t *cost,
+                 int64_t *u_out, int64_t *v_out)
+{
+    if (n < 0 || (n > 0 && (!C || !match)) || !cost) return OR_INVALID;
+    if (n == 0) { *cost = 0; return OR_OK; }
+    const int N = n + 1;
+    int64_t *u = calloc((size_t)n, sizeof(int64_t));
+    int64_t *v = calloc((size_t)N, sizeof(int64_t));
+    int64_t *dist = malloc(sizeof(int64_t) * N);
+    int32_t *owner = malloc(sizeof(int32_t) * N);   /* row holding column j */
+    int32_t *from = malloc(sizeof(int32_t) * N);    /* previous column on path */
+    char *intree = malloc((size_t)N);
+    if (!u || !v || !dist || !owner || !from || !intree) {
+        free(u); free(v); free(dist); free(owner); free(from); free(intree);
+        return OR_NOMEM;
+    }
+    for (int j = 0; j < N; ++j) owner[j] = -1;
+
+    for (int32_t r = 0; r < n; ++r) {
+        int32_t jcur = n;
+        owner[n] = r;
+        for (int j = 0; j < N; ++j) { dist[j] = OR_INF; intree[j] = 0; }
+        for (;;) {
+            intree[jcur] = 1;
+            const int32_t i = owner[jcur];
+            const int32_t *row = C + (int64_t)i * n;
+            int64_t delta = OR_INF;
+            int32_t jnext = -1;
+            for (int32_t j = 0; j < n; ++j) {
+                if (intree[j]) continue;
+                int64_t red = (int64_t)row[j] - u[i] - v[j];
+                if (red < dist[j]) { dist[j] = red; from[j] = jcur; }
+                if (dist[j] < delta) { delta = dist[j]; jnext = j; }
+            }
+            for (int j = 0; j < N; ++j) {
+                if (intree[j]) { u[owner[j]] += delta; v[j] -= delta; }
+                else dist[j] -= delta;
+            }
+            jcur = jnext;
+            if (owner[jcur] < 0) break;
+        }
+        while (jcur != n) {            /* flip the augmenting path */
+            int32_t jprev = from[jcur];
+            owner[jcur] = owner[jprev];
+            jcur = jprev;
+        }
+    }
+    int64_t total = 0;
+    for (int32_t j = 0; j < n; ++j) {
+        match[owner[j]] = j;
+        total += C[(int64_t)owner[j] * n + j];
+    }
+    *cost = total;
+    if (u_out) memcpy(u_out, u, sizeof(int64_t) * n);
+    if (v_out) memcpy(v_out, v, sizeof(int64_t) * n);
+    free(u); free(v); free(dist); free(owner); free(from); free(intree);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sequential cost scaling (Sect. 5.1-5.3).                            */
+/*                                                                     */
+/* Costs are scaled by (n+1): c~ = (n+1) C. Column prices p(y) use the */
+/* paper's sign (c_p(x,y) = c(x,y) + p(x) - p(y), c'_p = c - p(y)) and */
+/* start at 0 (Alg. 5.0) or at init_prices. Row prices are implicit:   */
+/* p(x) = -min_y (c'_p(x,y) + eps) (Alg. 5.2, refine initialisation).  */
+/*                                                                     */
+/* Outer loop (Alg. 5.0): eps <- eps0 (default C~ = (n+1)(max C -      */
+/* min C)); repeat refine with eps <- max(1, floor(eps / alpha)) until */
+/* the refine run at eps <= final_eps has finished. With final_eps = 1 */
+/* the result is optimal: summing the eps-complementary slackness of   */
+/* every row over the matching gives (n+1) cost <= (n+1) OPT + n.      */
+/*                                                                     */
+/* Refine (Alg. 5.2 + Alg. 5.4): f <- 0 (every row unmatched, prices    */
+/* kept). While an unmatched row x exists (FIFO order): scan all        */
+/* columns for the smallest c'_p(x,y) (best, at w; lowest index on     */
+/* ties) and the second smallest over y != w (second). Push x -> w     */
+/* (admissible under the implicit p(x)); then w is relabelled to        */
+/* p(w) <- p(w) - (second - best + eps) and pushes the unit of its old */
+/* mate back, which becomes unmatched (double push).                   */
+/*                                                                     */
+/* stats (optional, 4 entries): phases, row scans, displacements,      */
+/* eps of the first phase. check != 0 verifies after every phase that  */
+/* no price rose (Lemma 5.2) and that every row is eps-optimal          */
+/* (Lemma 5.6); a violation returns OR_INVARIANT.                       */
+/* ------------------------------------------------------------------ */
+int or_cost_scaling(const int32_t *C, int32_t n, int32_t alpha, int64_t eps0,
+                    const int64_t *init_prices, int64_t final_eps, int32_t check,
+                    int32_t *match, int64_t *cost, int64_t *prices_out,
+                    int64_t *stats)
+{
+    if (n < 0 || alpha < 2 || final_eps < 1 || (n > 0 && (!C || !match)) || !cost)
+        return OR_INVALID;
+    if (stats) for (int k = 0; k < 4; ++k) stats[k] = 0;
+    if (n == 0) { *cost = 0; return OR_OK; }
+    if (n == 1) {
+        match[0] = 0; *cost = C[0];
+        if (prices_out) prices_out[0] = init_prices ? init_prices[0] : 0;
+        return OR_OK;
+    }
+    const int64_t np1 = (int64_t)n + 1;
+    int32_t cmin = C[0], cmax = C[0];
+    for (int64_t k = 0; k < (int64_t)n * n; ++k) {
+        if (C[k] < cmin) cmin = C[k];
+        if (C[k] > cmax) cmax = C[k];
+    }
+    const int64_t Ct = np1 * ((int64_t)cmax - (int64_t)cmin);
+    int64_t eps = eps0 > 0 ? eps0 : Ct;
+
+    int64_t *p = malloc(sizeof(int64_t) * n);
+    int64_t *p_start = check ? malloc(sizeof(int64_t) * n) : NULL;
+    int32_t *holder = malloc(sizeof(int32_t) * n);   /* row matched to column y */
+    int32_t *col = malloc(sizeof(int32_t) * n);      /* column matched to row x */
+    int32_t *queue = malloc(sizeof(int32_t) * n);
+    if (!p || (check && !p_start) || !holder || !col || !queue) {
+        free(p); free(p_start); free(holder); free(col); free(queue);
+        return OR_NOMEM;
+    }
+    for (int32_t y = 0; y < n; ++y) p[y] = init_prices ? init_prices[y] : 0;
+
+    int rc = OR_OK;
+    int64_t phases = 0, scans = 0, displaced = 0, eps_first = 0;
+    do {
+        eps = eps / alpha;
+        if (eps < 1) eps = 1;
+        if (phases == 0) eps_first = eps;
+        if (check) memcpy(p_start, p, sizeof(int64_t) * n);
+        for (int32_t y = 0; y < n; ++y) holder[y] = -1;
+        for (int32_t x = 0; x < n; ++x) { col[x] = -1; queue[x] = x; }
+        int64_t head = 0, tail = n;               /* ring buffer of n slots */
+        while (head != tail) {
+            const int32_t x = queue[head % n];
+            head++;
+            const int32_t *row = C + (int64_t)x * n;
+            int64_t best = OR_INF, second = OR_INF;
+            int32_t w = -1;
+            for (int32_t y = 0; y < n; ++y) {
+                const int64_t cp = np1 * (int64_t)row[y] - p[y];   /* c'_p(x,y) */
+                if (cp < best) { second = best; best = cp; w = y; }
+                else if (cp < second) second = cp;
+            }
+            scans++;
+            p[w] -= (second - best) + eps;
+            if (p[w] < -(INT64_MAX / 8)) { rc = OR_OVERFLOW; goto done; }
+            const int32_t old = holder[w];
+            holder[w] = x;
+            col[x] = w;
+            if (old >= 0) {
+                col[old] = -1;
+                queue[tail % n] = old;
+                tail++;
+                displaced++;
+            }
+        }
+        phases++;
+        if (check) {
+            for (int32_t y = 0; y < n; ++y)
+                if (p[y] > p_start[y]) { rc = OR_INVARIANT; goto done; }
+            for (int32_t x = 0; x < n; ++x) {
+                const int32_t *row = C + (int64_t)x * n;
+                int64_t mn = OR_INF;
+                for (int32_t y = 0; y < n; ++y) {
+                    const int64_t cp = np1 * (int64_t)row[y] - p[y];
+                    if (cp < mn) mn = cp;
+                }
+                const int64_t mine = np1 * (int64_t)row[col[x]] - p[col[x]];
+                if (mine > mn + eps) { rc = OR_INVARIANT; goto done; }
+            }
+        }
+    } while (eps > final_eps);
+
+    {
+        int64_t total = 0;
+        for (int32_t x = 0; x < n; ++x) {
+            match[x] = col[x];
+            total += C[(int64_t)x * n + col[x]];
+        }
+        *cost = total;
+        if (prices_out) memcpy(prices_out, p, sizeof(int64_t) * n);
+    }
+done:
+    if (stats) { stats[0] = phases; stats[1] = scans; stats[2] = displaced; stats[3] = eps_first; }
+    free(p); free(p_start); free(holder); free(col); free(queue);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Certificates.                                                       */
+/* ------------------------------------------------------------------ */
+
+/* 0: match is a permutation of 0..n-1 and sum C[x][match[x]] equals
+ * claimed_cost; 10: not a permutation; 11: cost differs. */
+int or_check_matching(const int32_t *C, int32_t n, const int32_t *match,
+                      int64_t claimed_cost)
+{
+    if (n < 0) return OR_INVALID;
+    if (n == 0) return claimed_cost == 0 ? OR_OK : 11;
+    char *seen = calloc((size_t)n, 1);
+    if (!seen) return OR_NOMEM;
+    int64_t total = 0;
+    int rc = OR_OK;
+    for (int32_t x = 0; x < n; ++x) {
+        int32_t y = match[x];
+        if (y < 0 || y >= n || seen[y]) { rc = 10; break; }
+        seen[y] = 1;
+        total += C[(int64_t)x * n + y];
+    }
+    free(seen);
+    if (rc == OR_OK && total != claimed_cost) rc = 11;
+    return rc;
+}
+
+/* LP duality certificate for a matching and integer duals (u, v):
+ * 12: u[x] + v[y] > C[x][y] somewhere (infeasible dual);
+ * 13: a matched pair is not tight; 14: sum u + sum v != cost of the matching. */
+int or_check_duals(const int32_t *C, int32_t n, const int32_t *match,
+                   const int64_t *u, const int64_t *v)
+{
+    if (n < 0) return OR_INVALID;
+    int64_t dual = 0, primal = 0;
+    for (int32_t x = 0; x < n; ++x) {
+        const int32_t *row = C + (int64_t)x * n;
+        for (int32_t y = 0; y < n; ++y)
+            if (u[x] + v[y] > (int64_t)row[y]) return 12;
+        if (u[x] + v[match[x]] != (int64_t)row[match[x]]) return 13;
+        dual += u[x] + v[x];          /* x also runs over every column */
+        primal += row[match[x]];
+    }
+    return dual == primal ? OR_OK : 14;
+}
+
+/* eps-complementary slackness of a matching with column prices p (paper's
+ * sign) on costs scaled by (n+1): for every row x,
+ *   (n+1)C[x][M(x)] - p(M(x)) <= min_y ((n+1)C[x][y] - p(y)) + eps.
+ * With eps = 1 this implies optimality. 15: violated. */
+int or_check_eps_cs(const int32_t *C, int32_t n, const int32_t *match,
+                    const int64_t *p, int64_t eps)
+{
+    if (n < 0) return OR_INVALID;
+    const int64_t np1 = (int64_t)n + 1;
+    for (int32_t x = 0; x < n; ++x) {
+        const int32_t *row = C + (int64_t)x * n;
+        int64_t mn = OR_INF;
+        for (int32_t y = 0; y < n; ++y) {
+            const int64_t cp = np1 * (int64_t)row[y] - p[y];
+            if (cp < mn) mn = cp;
+        }
+        const int64_t mine = np1 * (int64_t)row[match[x]] - p[match[x]];
+        if (mine > mn + eps) return 15;
+    }
+    return OR_OK;
+}

@@ -1,0 +1,255 @@
+"""Seeded synthetic assignment instances.
+
+This module only draws inputs. It holds none of the solver's arithmetic, and
+both the CUDA path (through the tests and ``bench.py``) and the CPU oracle
+consume the int32 matrices it returns, so the two sides always see the same
+bytes.
+
+Random numbers come from SplitMix64 (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) used as a counter-based
+generator: value ``i`` of a stream is ``mix64(key + (i + 1) * GAMMA)``. Every
+transcendental function the generators need (``log``, ``exp``, ``cos``,
+``sin``) is evaluated here from its power series with IEEE-754 ``+ - * /``
+and ``sqrt`` only, one numpy ufunc per operation (no fused multiply-add), so
+the same seed gives the same matrix bit for bit on x86-64 and on AArch64.
+
+Workload shapes follow the paper's problem statement (Sect. 2 and Sect. 5:
+complete bipartite graphs ``|X| = |Y| = n`` with integer edge costs) and its
+motivating application, optical flow by assignment (Sect. 1):
+
+* ``uniform_costs``   -- i.i.d. integer costs, uniform on ``[lo, hi]``.
+* ``geometric_costs`` -- points ``a_i`` uniform in the unit square, targets
+  ``b_j = a_{pi(j)} + N(0, sigma^2)`` per coordinate, cost
+  ``round_half_even(scale * |a_i - b_j|^2)``.
+* ``batch``           -- many independent instances of uneven size,
+  ``n = floor(exp(U(ln lo, ln hi)))``, half uniform and half geometric.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "u64_stream",
+    "uniform_ints",
+    "uniform_doubles",
+    "normal_pairs",
+    "uniform_costs",
+    "geometric_costs",
+    "batch_sizes",
+    "batch",
+    "instance",
+    "WORKLOADS",
+]
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# stream tags keep the draws of one instance independent of each other
+_TAG_UNIFORM = 1
+_TAG_POINTS = 2
+_TAG_PERM = 3
+_TAG_JITTER = 4
+_TAG_SIZES = 5
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def u64_stream(seed: int, tag: int, count: int, start: int = 0) -> np.ndarray:
+    """``count`` 64-bit words of stream ``(seed, tag)``, from index ``start``."""
+    with np.errstate(over="ignore"):
+        key = _mix64(np.array([(seed * 0x100 + tag) & 0xFFFFFFFFFFFFFFFF],
+                              dtype=np.uint64) * _GAMMA)[0]
+        ctr = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+        return _mix64(key + ctr * _GAMMA)
+
+
+def uniform_ints(seed: int, tag: int, count: int, lo: int, hi: int,
+                 start: int = 0) -> np.ndarray:
+    """Integers uniform on ``[lo, hi]`` (inclusive) by multiply-shift.
+
+    The range ``hi - lo + 1`` must be at most ``2**32``; the bias of the
+    multiply-shift map is below ``range / 2**32``.
+    """
+    r = hi - lo + 1
+    if not (1 <= r <= 1 << 32):
+        raise ValueError("range must be in [1, 2**32]")
+    z = u64_stream(seed, tag, count, start) >> np.uint64(32)
+    with np.errstate(over="ignore"):
+        return (np.int64(lo) + ((z * np.uint64(r)) >> np.uint64(32)).astype(np.int64))
+
+
+def uniform_doubles(seed: int, tag: int, count: int, start: int = 0) -> np.ndarray:
+    """Doubles uniform on ``[0, 1)`` with 53 random bits."""
+    z = u64_stream(seed, tag, count, start) >> np.uint64(11)
+    return z.astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+# ---------------------------------------------------------------- elementary
+# functions from their series, so that results do not depend on the libm or
+# on numpy's SIMD kernels of the machine.
+
+_LN2 = 0.6931471805599453
+_TWO_PI = 6.283185307179586
+_SQRT_HALF = 0.7071067811865476
+
+
+def _ln(x: np.ndarray) -> np.ndarray:
+    """Natural log for x > 0: x = m 2^e, ln m = 2 artanh((m-1)/(m+1))."""
+    m, e = np.frexp(x)
+    small = m < _SQRT_HALF
+    m = np.where(small, m * 2.0, m)
+    e = np.where(small, e - 1, e).astype(np.float64)
+    s = (m - 1.0) / (m + 1.0)
+    s2 = s * s
+    acc = np.full_like(s, 1.0 / 29.0)
+    for k in range(13, -1, -1):
+        acc = acc * s2
+        acc = acc + (1.0 / (2 * k + 1))
+    return e * _LN2 + 2.0 * (s * acc)
+
+
+def _exp(x: np.ndarray) -> np.ndarray:
+    """exp(x) = 2^k exp(r), r = x - k ln 2, |r| <= ln2 / 2."""
+    k = np.rint(x * (1.0 / _LN2))
+    r = x - k * _LN2
+    acc = np.full_like(r, 1.0 / math.factorial(22))
+    for j in range(21, -1, -1):
+        acc = acc * r
+        acc = acc + (1.0 / math.factorial(j))
+    return np.ldexp(acc, k.astype(np.int32))
+
+
+def _cos_sin_turns(t: np.ndarray):
+    """cos and sin of 2 pi t for t in [0, 1), reduced to |angle| <= pi / 4."""
+    q = np.rint(t * 4.0)
+    f = t - q * 0.25                       # exact
+    a = f * _TWO_PI
+    a2 = a * a
+    c = np.full_like(a, 1.0 / math.factorial(20))
+    for j in range(18, -1, -2):
+        c = c * a2
+        c = c + ((-1.0) ** (j // 2)) / math.factorial(j)
+    s = np.full_like(a, -1.0 / math.factorial(19))
+    for j in range(17, 0, -2):
+        s = s * a2
+        s = s + ((-1.0) ** ((j - 1) // 2)) / math.factorial(j)
+    s = s * a
+    quad = (q.astype(np.int64)) & 3
+    cos = np.select([quad == 0, quad == 1, quad == 2], [c, -s, -c], s)
+    sin = np.select([quad == 0, quad == 1, quad == 2], [s, c, -s], -c)
+    return cos, sin
+
+
+def normal_pairs(seed: int, tag: int, count: int):
+    """``2 * count`` standard normal deviates by the Box-Muller transform
+    (Box and Muller, Ann. Math. Stat. 29, 1958), returned as two arrays."""
+    u = uniform_doubles(seed, tag, 2 * count)
+    u1 = 1.0 - u[0::2]                     # (0, 1]
+    u2 = u[1::2]
+    r = np.sqrt(-2.0 * _ln(u1))
+    c, s = _cos_sin_turns(u2)
+    return r * c, r * s
+
+
+# ---------------------------------------------------------------- workloads
+
+def uniform_costs(n: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """n x n int32 costs, i.i.d. uniform on ``[lo, hi]``, row-major."""
+    if n < 0:
+        raise ValueError("n must be >= 0")
+    if not (-(1 << 31) <= lo <= hi < (1 << 31)):
+        raise ValueError("costs must fit int32")
+    v = uniform_ints(seed, _TAG_UNIFORM, n * n, lo, hi)
+    return v.astype(np.int32).reshape(n, n)
+
+
+def _permutation(n: int, seed: int) -> np.ndarray:
+    keys = u64_stream(seed, _TAG_PERM, n)
+    return np.argsort(keys, kind="stable").astype(np.int64)
+
+
+def geometric_points(n: int, seed: int, sigma: float = 0.01):
+    """Source points ``a`` (n x 2), permutation ``pi`` and targets ``b``."""
+    a = uniform_doubles(seed, _TAG_POINTS, 2 * n).reshape(n, 2)
+    pi = _permutation(n, seed)
+    zx, zy = normal_pairs(seed, _TAG_JITTER, n)
+    b = np.empty_like(a)
+    b[:, 0] = a[pi, 0] + sigma * zx
+    b[:, 1] = a[pi, 1] + sigma * zy
+    return a, pi, b
+
+
+def geometric_costs(n: int, seed: int, sigma: float = 0.01,
+                    scale: float = 1.0e4, block: int = 1024) -> np.ndarray:
+    """Optical-flow-like n x n int32 costs: ``rint(scale * |a_i - b_j|^2)``."""
+    if n < 0:
+        raise ValueError("n must be >= 0")
+    a, _, b = geometric_points(n, seed, sigma)
+    out = np.empty((n, n), dtype=np.int32)
+    bx = b[:, 0][None, :]
+    by = b[:, 1][None, :]
+    for r0 in range(0, n, block):
+        r1 = min(n, r0 + block)
+        dx = a[r0:r1, 0][:, None] - bx
+        dy = a[r0:r1, 1][:, None] - by
+        d2 = dx * dx + dy * dy
+        out[r0:r1] = np.rint(d2 * scale).astype(np.int32)
+    return out
+
+
+def batch_sizes(count: int, seed: int, lo: int = 16, hi: int = 1024) -> np.ndarray:
+    """``n = floor(exp(U(ln lo, ln hi)))`` clamped to ``[lo, hi]``."""
+    u = uniform_doubles(seed, _TAG_SIZES, count)
+    llo, lhi = _ln(np.array([float(lo)]))[0], _ln(np.array([float(hi)]))[0]
+    n = np.floor(_exp(llo + u * (lhi - llo))).astype(np.int64)
+    return np.clip(n, lo, hi).astype(np.int32)
+
+
+def batch(count: int, seed: int, lo: int = 16, hi: int = 1024,
+          cost_hi: int = 10_000):
+    """``count`` independent instances packed back to back.
+
+    Even-numbered instances are uniform on ``[0, cost_hi]``; odd-numbered ones
+    are geometric. Instance ``i`` draws from seed ``seed * 1_000_003 + i``.
+    Returns ``(costs_flat int32, offsets int64, ns int32)`` where instance
+    ``i`` is ``costs_flat[offsets[i] : offsets[i] + ns[i]**2]`` (row-major).
+    """
+    ns = batch_sizes(count, seed, lo, hi)
+    sizes = ns.astype(np.int64) ** 2
+    offsets = np.zeros(count, dtype=np.int64)
+    if count > 1:
+        offsets[1:] = np.cumsum(sizes)[:-1]
+    flat = np.empty(int(sizes.sum()), dtype=np.int32)
+    for i in range(count):
+        s = seed * 1_000_003 + i
+        n = int(ns[i])
+        c = uniform_costs(n, 0, cost_hi, s) if i % 2 == 0 else geometric_costs(n, s)
+        flat[offsets[i]:offsets[i] + n * n] = c.ravel()
+    return flat, offsets, ns
+
+
+# Named workloads: the sizes, cost ranges and structure of the dense
+# assignment instances this library is measured on.
+WORKLOADS = {
+    "uniform-n256-c1000": dict(kind="uniform", n=256, lo=0, hi=1000),
+    "uniform-n4096-c2^20": dict(kind="uniform", n=4096, lo=0, hi=(1 << 20) - 1),
+    "geometric-n8192": dict(kind="geometric", n=8192),
+}
+
+
+def instance(name: str, seed: int, n: int | None = None) -> np.ndarray:
+    """One instance of a named workload (optionally at another size ``n``)."""
+    w = WORKLOADS[name]
+    nn = w["n"] if n is None else n
+    if w["kind"] == "uniform":
+        return uniform_costs(nn, w["lo"], w["hi"], seed)
+    return geometric_costs(nn, seed)

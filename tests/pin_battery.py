@@ -1,0 +1,87 @@
+"""A compact battery of the oracle's pins, runnable against any build of
+``oracle.c``. ``tests/test_oracle_mutations.py`` runs it on the real oracle
+(it must pass) and on copies with planted mistakes (each must fail).
+
+Usage: ``python pin_battery.py [path/to/oracle.c]`` exits 0 when every pin
+holds and 1 at the first failure.
+"""
+
+import glob
+import itertools
+import os
+import sys
+import tempfile
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def _fixture(path):
+    lines = [l for l in open(path) if l.strip() and not l.startswith("#")]
+    cost = int(lines[0].split()[1])
+    m = lines[1].split()[1:]
+    match = None if m == ["any"] else [int(t) for t in m]
+    C = np.array([[int(t) for t in l.split()] for l in lines[3:]], dtype=np.int32)
+    return C, cost, match
+
+
+def _enumerate(C):
+    n = C.shape[0]
+    return min(sum(int(C[x, p[x]]) for x in range(n))
+               for p in itertools.permutations(range(n)))
+
+
+def run_all_pins(orc):
+    from paper_1110_6231_gb300 import synth
+    for path in sorted(glob.glob(os.path.join(HERE, "golden", "*.txt"))):
+        C, cost, match = _fixture(path)
+        outs = [orc.hungarian(C)[:2], orc.cost_scaling(C)[:2]]
+        if C.shape[0] <= 10:
+            outs.append(orc.brute_force(C))
+        for c, m in outs:
+            assert c == cost, path
+            assert sum(int(C[x, m[x]]) for x in range(len(m))) == cost, path
+            if match is not None:
+                assert list(m) == match, path
+    rng = np.random.default_rng(5)
+    for t in range(200):
+        n = int(rng.integers(1, 7))
+        C = rng.integers(-30, 30, size=(n, n)).astype(np.int32)
+        ref = _enumerate(C)
+        assert orc.brute_force(C)[0] == ref
+        assert orc.hungarian(C)[0] == ref
+        g, gm, p, _ = orc.cost_scaling(C)
+        assert g == ref
+    from scipy.optimize import linear_sum_assignment
+    for seed in range(3):
+        for C in (synth.uniform_costs(97, 0, 10**5, seed), synth.geometric_costs(96, seed)):
+            r, c = linear_sum_assignment(C)
+            ref = int(C[r, c].sum())
+            h, hm, u, v = orc.hungarian(C)
+            assert h == ref and orc.check_duals(C, hm, u, v) == 0
+            g, gm, p, st = orc.cost_scaling(C)
+            assert g == ref and orc.check_eps_cs(C, gm, p, 1) == 0
+            Ct = 97 * (int(C.max()) - int(C.min()))
+            assert st["phases"] == len(orc.eps_schedule(Ct))
+
+
+def main(argv):
+    import oracle as orc
+    if len(argv) > 1:
+        src = os.path.abspath(argv[1])
+        tmp = tempfile.mkdtemp(prefix="oracle_mut_")
+        orc._SRC = src
+        orc._LIB = os.path.join(tmp, "liboracle.so")
+    try:
+        run_all_pins(orc)
+    except AssertionError:
+        return 1
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv))

@@ -1,0 +1,68 @@
+"""Plant plausible mistakes in copies of the oracle and check that the pins
+catch every one (a mutation test of the oracle; nothing here touches a GPU).
+
+Each mutant is compiled from a patched copy of ``oracle/oracle.c`` in a
+temporary directory and run through ``tests/pin_battery.py`` in a child
+process with a time limit: a failing pin or a refine that no longer ends
+(dropping eps, for instance, can stall a price war) both count as caught.
+"""
+
+import os
+import subprocess
+import sys
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+BATTERY = os.path.join(HERE, "pin_battery.py")
+
+# (name, original text, planted mistake)
+MUTANTS = [
+    ("no-scaling", "const int64_t np1 = (int64_t)n + 1;\n    int32_t cmin",
+     "const int64_t np1 = 1;\n    int32_t cmin"),
+    ("price-sign", "const int64_t cp = np1 * (int64_t)row[y] - p[y];   /* c'_p(x,y) */",
+     "const int64_t cp = np1 * (int64_t)row[y] + p[y];   /* c'_p(x,y) */"),
+    ("transposed-scan", "const int64_t cp = np1 * (int64_t)row[y] - p[y];   /* c'_p(x,y) */",
+     "const int64_t cp = np1 * (int64_t)C[(int64_t)y * n + x] - p[y];"),
+    ("no-eps-in-bid", "p[w] -= (second - best) + eps;", "p[w] -= (second - best) + 0;"),
+    ("no-second-update", "else if (cp < second) second = cp;", ";"),
+    ("skip-final-phase", "} while (eps > final_eps);", "} while (eps / alpha > final_eps);"),
+    ("displaced-not-requeued", "queue[tail % n] = old;\n                tail++;", ";"),
+    ("hungarian-dual-sign", "int64_t red = (int64_t)row[j] - u[i] - v[j];",
+     "int64_t red = (int64_t)row[j] - u[i] + v[j];"),
+    ("hungarian-no-dual-update", "if (intree[j]) { u[owner[j]] += delta; v[j] -= delta; }",
+     "if (intree[j]) { u[owner[j]] += delta; }"),
+    ("hungarian-transposed", "const int32_t *row = C + (int64_t)i * n;\n            int64_t delta",
+     "const int32_t *row = C + (int64_t)i;\n            int64_t delta"),
+    ("brute-force-skips-perms", "while (i < n) {", "while (i < n - 1) {"),
+]
+
+
+def _run_battery(src, tmp_path, timeout=120):
+    env = dict(os.environ, PYTHONPATH=ROOT)
+    try:
+        r = subprocess.run([sys.executable, BATTERY, src], cwd=str(tmp_path), env=env,
+                           capture_output=True, timeout=timeout)
+        return r.returncode
+    except subprocess.TimeoutExpired:
+        return "timeout"
+
+
+def test_battery_passes_on_real_oracle(tmp_path):
+    assert _run_battery(SRC, tmp_path) == 0
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(name, old, new, tmp_path):
+    text = open(SRC).read()
+    assert text.count(old) >= 1, f"mutation site for {name} not found"
+    if name == "hungarian-transposed":
+        # the transposed row walks down column i: stride n instead of 1
+        text = text.replace("int64_t red = (int64_t)row[j] - u[i] - v[j];",
+                            "int64_t red = (int64_t)row[(int64_t)j * n] - u[i] - v[j];")
+    mutant = tmp_path / "oracle.c"
+    mutant.write_text(text.replace(old, new, 1))
+    rc = _run_battery(str(mutant), tmp_path, timeout=15)
+    assert rc != 0, f"planted mistake {name} was not caught"
