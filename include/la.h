@@ -1,0 +1,145 @@
+/*
+ * la.h -- C ABI of the GB300 dense assignment solver.
+ *
+ * Problem. Given an n x n int32 cost matrix C (row x = left vertex of X,
+ * column y = right vertex of Y of a complete bipartite graph), find a perfect
+ * matching M that minimises sum_x C[x][M(x)] (Sect. 2 of the paper defines
+ * matchings, perfect matchings and the assignment problem; Sect. 5 reduces the
+ * assignment problem to a min-cost flow with u(x,y) = 1, c(x,y) = w(x,y), and
+ * this library solves that minimisation; a maximising caller passes
+ * max_w - w or -w).
+ *
+ * Method. Cost scaling (Sect. 5.1, Algorithm 5.0's epsilon loop) on costs
+ * scaled by n + 1, with a lock-free parallel refine (Sect. 5.3, Algorithm 5.4)
+ * whose push/relabel step is taken as the Goldberg-Kennedy double push: a
+ * free row x scans its row for the best and second-best part-reduced cost
+ * c'_p(x,y) = (n+1) C[x][y] - p(y), takes the best column w and lowers p(w)
+ * by (second - best + eps), displacing w's previous mate. All arithmetic is
+ * exact integer arithmetic, so the returned cost is the exact optimum.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named "device" must point to memory the current CUDA device can
+ *    read or write (cudaMalloc, cudaMallocAsync, managed memory). They are
+ *    owned by the caller; the library never frees them.
+ *  - Matrices are row-major: C[x][y] is element x * n + y.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Work is ordered on that stream.
+ *  - The library keeps a per-device workspace (allocated on first use and
+ *    grown on demand, freed by la_release_workspace or at exit). Calls from
+ *    several host threads are serialised by an internal lock.
+ *  - Argument errors return LA_ERR_INVALID before anything is enqueued.
+ *  - The la_solve* calls block the calling host thread until the result is
+ *    in place (they read a few scalars back from the device), so outputs are
+ *    valid when the call returns LA_OK.
+ */
+#ifndef LA_H
+#define LA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LA_OK = 0,
+    LA_ERR_INVALID = 1,     /* bad argument (n < 0, NULL pointer, n too large) */
+    LA_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    LA_ERR_OVERFLOW = 3,    /* cost range too large for the exact integer
+                               price field: (n+1)(max C - min C) >= 2^40 */
+    LA_ERR_ITER_LIMIT = 4,  /* the row-scan budget ran out before the
+                               refine finished (see la_options.scan_budget) */
+    LA_ERR_NOMEM = 5,       /* device workspace allocation failed */
+    LA_ERR_INTERNAL = 6     /* a device-side consistency check failed */
+} la_status;
+
+/* Largest n accepted by the solver (the mate field of a column key is 20
+ * bits wide, with one value reserved for "no mate"). */
+#define LA_MAX_N ((1 << 20) - 1)
+
+/* Options for la_solve_ex. Zero-initialise and set what you need. */
+typedef struct {
+    /* Divisor of eps between refine phases (Algorithm 5.0; the paper uses
+       alpha = 10). 0 selects 10. Must be >= 2 otherwise. */
+    int32_t alpha;
+    /* Starting eps. 0 selects C~ = (n+1)(max C - min C) (Algorithm 5.0
+       starts at the largest cost). The first phase runs at
+       max(1, eps0 / alpha); the last phase always runs at eps = 1. */
+    int64_t eps0;
+    /* Device int64[n] or NULL: starting column prices, in the paper's sign
+       (c_p(x,y) = c(x,y) + p(x) - p(y)) and in units of the scaled costs
+       (n+1) C. NULL starts from p = 0 (Algorithm 5.0). Any values give the
+       same optimal cost; good ones need fewer row scans. */
+    const int64_t *init_prices;
+    /* Device int64[n] or NULL: receives the final column prices in the same
+       units and sign, shifted so that max_y p(y) = 0. With them every row
+       satisfies (n+1)C[x][M(x)] - p(M(x)) <= min_y((n+1)C[x][y] - p(y)) + 1. */
+    int64_t *prices_out;
+    /* Maximum number of row scans over the whole solve; 0 selects
+       256 * n * phases + 2^22. Exhausting it returns LA_ERR_ITER_LIMIT with
+       the outputs unspecified. */
+    int64_t scan_budget;
+    /* Nonzero: record CUDA events around every refine launch and report
+       their summed duration in la_stats.refine_ms. */
+    int32_t profile;
+    /* Tuning: threads per block of the refine kernel (0 = default 256). */
+    int32_t block_threads;
+} la_options;
+
+/* Phases whose counters la_stats records one by one. */
+#define LA_STATS_PHASES 32
+
+/* Counters of one solve (filled by la_solve_ex when stats_out != NULL). */
+typedef struct {
+    int64_t n;
+    int64_t phases;          /* refine phases run */
+    int64_t scans;           /* row scans (one per double push attempt) */
+    int64_t wins;            /* successful double pushes */
+    int64_t displaced;       /* wins that displaced a previous mate */
+    int64_t eps_first;       /* eps of the first phase */
+    int64_t scaled_range;    /* C~ = (n+1)(max C - min C) */
+    int32_t wide;            /* 1 if the 64-bit reduced-cost path ran */
+    int32_t vector_loads;    /* 1 if the 128-bit row-load path ran */
+    int64_t launches;        /* kernels this call launched */
+    int64_t refine_launches; /* of which refine kernels */
+    double refine_ms;        /* summed refine kernel time (profile != 0) */
+    int64_t max_chain;       /* most row scans one warp made within a phase
+                                (the length of the longest displacement chain
+                                plus lost bids: the refine's critical path) */
+    int64_t phase_scans[LA_STATS_PHASES];  /* row scans of each phase */
+    double phase_ms[LA_STATS_PHASES];      /* refine time of each phase
+                                              (profile != 0) */
+} la_stats;
+
+/*
+ * la_solve -- exact minimum-cost perfect matching of a dense n x n matrix.
+ *   cost      device const int32[n*n], row-major, read only.
+ *   n         0 <= n <= LA_MAX_N. n = 0 writes *cost_out = 0.
+ *   stream    cudaStream_t as void*.
+ *   match_out device int32[n] or NULL: match_out[x] = column matched to x.
+ *   cost_out  device int64[1]: the optimal total cost sum_x C[x][match[x]].
+ * Returns LA_OK, or an error code with outputs unspecified.
+ */
+la_status la_solve(const int32_t *cost, int32_t n, void *stream,
+                   int32_t *match_out, int64_t *cost_out);
+
+/* la_solve with options (opt may be NULL) and counters (stats_out may be
+ * NULL; it is host memory). */
+la_status la_solve_ex(const int32_t *cost, int32_t n, const la_options *opt,
+                      void *stream, int32_t *match_out, int64_t *cost_out,
+                      la_stats *stats_out);
+
+/* Human-readable name of a status code (static storage). */
+const char *la_status_string(la_status s);
+
+/* Frees the calling device's workspace (the next solve reallocates it). */
+la_status la_release_workspace(void);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int32_t la_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LA_H */

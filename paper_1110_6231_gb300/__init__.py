@@ -1,0 +1,198 @@
+"""GB300 dense assignment solver: Python binding of ``libla.so``.
+
+The binding only marshals arguments: tensors become raw device pointers,
+the current torch stream becomes the ``cudaStream_t``, and every step of the
+solve runs in the library's CUDA kernels. There is no CPU fallback: if
+``libla.so`` has not been built (``__graft_entry__.build()`` or
+``python -m paper_1110_6231_gb300.build``), every call raises.
+
+Low-level functions keep the C names and argument order of ``include/la.h``
+(``la_solve``, ``la_solve_ex``, ``la_status_string``, ...). ``solve`` is the
+convenience wrapper most callers want.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libla.so")
+
+LA_OK = 0
+LA_ERR_INVALID = 1
+LA_ERR_CUDA = 2
+LA_ERR_OVERFLOW = 3
+LA_ERR_ITER_LIMIT = 4
+LA_ERR_NOMEM = 5
+LA_ERR_INTERNAL = 6
+LA_MAX_N = (1 << 20) - 1
+
+
+class la_options(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_int32),
+        ("eps0", ctypes.c_int64),
+        ("init_prices", ctypes.c_void_p),
+        ("prices_out", ctypes.c_void_p),
+        ("scan_budget", ctypes.c_int64),
+        ("profile", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+    ]
+
+
+class la_stats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("phases", ctypes.c_int64),
+        ("scans", ctypes.c_int64),
+        ("wins", ctypes.c_int64),
+        ("displaced", ctypes.c_int64),
+        ("eps_first", ctypes.c_int64),
+        ("scaled_range", ctypes.c_int64),
+        ("wide", ctypes.c_int32),
+        ("vector_loads", ctypes.c_int32),
+        ("launches", ctypes.c_int64),
+        ("refine_launches", ctypes.c_int64),
+        ("refine_ms", ctypes.c_double),
+        ("max_chain", ctypes.c_int64),
+        ("phase_scans", ctypes.c_int64 * 32),
+        ("phase_ms", ctypes.c_double * 32),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            if name.startswith("phase_"):
+                v = list(v)[: max(0, min(32, int(self.phases)))]
+            d[name] = v
+        return d
+
+
+class LaError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        super().__init__(f"{where}: {la_status_string(status)}" if where else la_status_string(status))
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded ``libla.so``; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build the CUDA library first "
+                    "(python -m paper_1110_6231_gb300.build)")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            L.la_solve.argtypes = [P, i32, P, P, P]
+            L.la_solve_ex.argtypes = [P, i32, P, P, P, P, P]
+            L.la_status_string.argtypes = [ctypes.c_int]
+            L.la_status_string.restype = ctypes.c_char_p
+            L.la_release_workspace.argtypes = []
+            L.la_version.argtypes = []
+            L.la_version.restype = i32
+            for f in (L.la_solve, L.la_solve_ex, L.la_release_workspace):
+                f.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """A device pointer from a tensor, an int address, or None (NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------- C names
+
+def la_solve(cost, n, stream, match_out, cost_out) -> int:
+    return lib().la_solve(_ptr(cost), int(n), _stream(stream), _ptr(match_out), _ptr(cost_out))
+
+
+def la_solve_ex(cost, n, opt, stream, match_out, cost_out, stats_out) -> int:
+    return lib().la_solve_ex(_ptr(cost), int(n), None if opt is None else ctypes.byref(opt),
+                             _stream(stream), _ptr(match_out), _ptr(cost_out),
+                             None if stats_out is None else ctypes.byref(stats_out))
+
+
+def la_status_string(status: int) -> str:
+    return lib().la_status_string(int(status)).decode()
+
+
+def la_release_workspace() -> int:
+    return lib().la_release_workspace()
+
+
+def la_version() -> int:
+    return lib().la_version()
+
+
+# ------------------------------------------------------------- convenience
+
+@dataclass
+class Solution:
+    cost: int            # exact optimal total cost
+    match: object        # torch.int32 [n] on the device: row x -> column
+    stats: dict          # la_stats counters
+    prices: object = None  # torch.int64 [n] final column prices (if asked)
+
+
+def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bool = False,
+          scan_budget: int = 0, profile: bool = False, block_threads: int = 0,
+          stream=None, check: bool = True) -> Solution:
+    """Exact minimum-cost assignment of a square int32 CUDA tensor ``C``.
+
+    ``init_prices`` (int64 CUDA tensor, paper sign, units of (n+1) C) warm
+    starts the solve. Raises ``LaError`` on a non-OK status when ``check``.
+    """
+    import torch
+    if C.dim() != 2 or C.shape[0] != C.shape[1]:
+        raise ValueError("cost matrix must be square")
+    if C.dtype != torch.int32 or not C.is_cuda:
+        raise ValueError("cost matrix must be an int32 CUDA tensor")
+    C = C.contiguous()
+    n = C.shape[0]
+    dev = C.device
+    match = torch.empty(n, dtype=torch.int32, device=dev)
+    cost = torch.empty(1, dtype=torch.int64, device=dev)
+    prices = torch.empty(n, dtype=torch.int64, device=dev) if want_prices else None
+    opt = la_options()
+    opt.alpha = alpha
+    opt.eps0 = eps0
+    if init_prices is not None:
+        if init_prices.dtype != torch.int64 or init_prices.numel() != n or not init_prices.is_cuda:
+            raise ValueError("init_prices must be an int64 CUDA tensor of length n")
+        init_prices = init_prices.contiguous()
+    opt.init_prices = _ptr(init_prices)
+    opt.prices_out = _ptr(prices)
+    opt.scan_budget = scan_budget
+    opt.profile = int(bool(profile))
+    opt.block_threads = block_threads
+    st = la_stats()
+    with torch.cuda.device(dev):
+        rc = la_solve_ex(C, n, opt, stream, match, cost, st)
+    if rc != LA_OK and check:
+        raise LaError(rc, "la_solve_ex")
+    return Solution(cost=int(cost.item()) if rc == LA_OK else None, match=match,
+                    stats=dict(st.as_dict(), status=rc), prices=prices)

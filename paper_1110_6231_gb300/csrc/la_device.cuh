@@ -1,0 +1,136 @@
+// Device-side building blocks of the refine: the packed column key, the
+// row scan (best / second-best part-reduced cost) and the warp reduction.
+//
+// Notation (Sect. 2 and Sect. 5 of the paper): rows x in X, columns y in Y,
+// scaled cost c~(x,y) = (n+1) C[x][y]. Column prices p(y) are kept as
+// q(y) = -p(y) >= 0 after a per-phase shift (a uniform shift of all prices
+// leaves every reduced cost c_p(x,y) = c(x,y) + p(x) - p(y) unchanged).
+// The part-reduced cost c'_p(x,y) = c~(x,y) - p(y) then reads
+//   v(x,y) = (C[x][y] - min C) * (n+1) + q(y)  >= 0,
+// the same value up to the constant (n+1) min C.
+#pragma once
+
+#include <cstdint>
+#include <climits>
+
+namespace la {
+
+constexpr int kMateBits = 20;
+constexpr unsigned long long kMateMask = (1ull << kMateBits) - 1;
+constexpr uint32_t kNone = (uint32_t)kMateMask;          // "no mate"
+constexpr int kPriceBits = 64 - kMateBits;               // 44
+constexpr unsigned long long kQMax = (1ull << kPriceBits) - 1;
+
+// A column's state in one 64-bit word: (kQMax - q) in the high 44 bits and
+// the mate row in the low 20. A smaller key means a lower price p(y) = -q,
+// and at equal price the lower row index. One atomicMin therefore decides
+// both the new price and the new holder of the column (the double push's
+// push x -> w and relabel of w commit together).
+__host__ __device__ __forceinline__ unsigned long long pack_key(unsigned long long q, uint32_t mate) {
+    return ((kQMax - q) << kMateBits) | (unsigned long long)mate;
+}
+__host__ __device__ __forceinline__ unsigned long long key_q(unsigned long long k) {
+    return kQMax - (k >> kMateBits);
+}
+__host__ __device__ __forceinline__ uint32_t key_mate(unsigned long long k) {
+    return (uint32_t)(k & kMateMask);
+}
+
+// Solver control block in device memory.
+struct Ctrl {
+    unsigned long long scans;       // row scans (all phases)
+    unsigned long long wins;        // successful double pushes
+    unsigned long long displaced;   // wins that displaced a mate
+    int next_row;                   // head of this phase's row queue
+    int status;                     // la_status of the device side, 0 = ok
+    int cmin, cmax;                 // min / max cost
+    unsigned long long qmin[2];     // per-phase rebase, double buffered
+    unsigned long long qspread;     // max q after the warm-start shift
+    long long pmax;                 // max of warm-start prices
+    unsigned long long max_chain;   // most scans by one warp in one phase
+    unsigned long long phase_start_scans[64];
+};
+
+// --- loads ---------------------------------------------------------------
+
+// Cost rows are read once per scan and never written: non-coherent path,
+// no L1 allocation (the row will not be reused by this SM soon), default L2
+// policy (a matrix that fits in L2 stays there across phases).
+__device__ __forceinline__ int4 ld_row4(const int4 *p) {
+    int4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ int ld_row1(const int *p) {
+    int r;
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+
+// Prices are written by other SMs during the scan. Reading them at L2
+// (.cg) keeps the view at most one in-flight update old; an older price is
+// higher (prices only decrease, Lemma 5.2), which can only make a bid lose,
+// never break eps-optimality. L1 must not serve stale lines repeatedly.
+__device__ __forceinline__ uint4 ld_q4(const uint32_t *p) {
+    return __ldcg(reinterpret_cast<const uint4 *>(p));
+}
+__device__ __forceinline__ ulonglong2 ld_q2(const unsigned long long *p) {
+    return __ldcg(reinterpret_cast<const ulonglong2 *>(p));
+}
+
+// --- best / second best ---------------------------------------------------
+
+template <typename V>
+struct Top2 {
+    V b1;        // smallest v
+    V b2;        // second smallest v (over columns other than the argmin)
+    V qb;        // q(w) as read during the scan
+    int w;       // argmin column (lowest index among equal minima)
+};
+
+template <typename V>
+__device__ __forceinline__ void top2_init(Top2<V> &t) {
+    t.b1 = (V)~(V)0;
+    t.b2 = (V)~(V)0;
+    t.qb = 0;
+    t.w = INT_MAX;
+}
+
+template <typename V>
+__device__ __forceinline__ void top2_push(Top2<V> &t, V v, V q, int y) {
+    const V hi = v > t.b1 ? v : t.b1;
+    t.b2 = hi < t.b2 ? hi : t.b2;
+    const bool better = v < t.b1;       // strict: keeps the earliest column
+    t.w = better ? y : t.w;
+    t.qb = better ? q : t.qb;
+    t.b1 = better ? v : t.b1;
+}
+
+template <typename V>
+__device__ __forceinline__ V shfl_xor_v(V v, int m) {
+    return __shfl_xor_sync(0xffffffffu, v, m);
+}
+
+// Butterfly merge of 32 lanes' partial results; every lane ends with the
+// row's (b1, b2, w, qb). Equal minima resolve to the lower column index, so
+// the merge is order independent.
+template <typename V>
+__device__ __forceinline__ void top2_warp_reduce(Top2<V> &t) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const V o1 = shfl_xor_v(t.b1, m);
+        const V o2 = shfl_xor_v(t.b2, m);
+        const V oq = shfl_xor_v(t.qb, m);
+        const int ow = __shfl_xor_sync(0xffffffffu, t.w, m);
+        const V lo2 = o2 < t.b2 ? o2 : t.b2;
+        const V hi1 = o1 > t.b1 ? o1 : t.b1;
+        t.b2 = lo2 < hi1 ? lo2 : hi1;
+        const bool take = (o1 < t.b1) || (o1 == t.b1 && ow < t.w);
+        t.b1 = take ? o1 : t.b1;
+        t.qb = take ? oq : t.qb;
+        t.w = take ? ow : t.w;
+    }
+}
+
+}  // namespace la

@@ -1,0 +1,553 @@
+// la_solve / la_solve_ex: dense assignment by cost scaling with a lock-free
+// parallel refine on one GPU.
+//
+// Outer loop (Sect. 5.1, Algorithm 5.0): eps starts at C~ = (n+1)(max C -
+// min C) and every phase runs refine at eps <- max(1, floor(eps / alpha));
+// the phase at eps = 1 is the last. Costs are scaled by n + 1 so that an
+// eps = 1 optimal assignment is exactly optimal.
+//
+// Refine (Algorithm 5.2's initialisation + Algorithm 5.4's push/relabel as a
+// Goldberg-Kennedy double push), one phase per launch of k_refine:
+//   * f <- 0: every column's mate is cleared, its price is kept; the row
+//     prices are implicit, p(x) = -min_y (c'_p(x,y) + eps).
+//   * each warp of a persistent grid takes a free row x from a device queue
+//     and scans its cost row with 128-bit loads for the best (b1 at w) and
+//     second best (b2) part-reduced cost v(x,y) = c~(x,y) - p(y);
+//   * it bids q(w) <- q_read(w) + (b2 - b1) + eps (that is, p(w) drops by
+//     second - best + eps) with one 64-bit atomicMin on the column key that
+//     packs (price, mate): a win is the push x -> w, the relabel of w and the
+//     push of w's old mate back, all at once. The displaced mate becomes
+//     the warp's next row; a lost bid rescans the same row.
+//   * the phase ends when the queue is empty and every warp's row is
+//     matched (the kernel exits); no host round trip inside a phase.
+// Lemma 5.2 (prices never increase) makes stale price reads safe: they can
+// only make a bid lose, and a row holding a column keeps its
+// eps-complementary slackness while other prices fall.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+#include <vector>
+
+#include "la.h"
+#include "la_device.cuh"
+
+using namespace la;
+
+namespace {
+
+constexpr int kMaxPhases = 64;
+constexpr int kMaxDevices = 64;
+constexpr int kDefaultBlock = 256;
+constexpr unsigned long long kRangeLimit = 1ull << 40;  // C~ limit (LA_ERR_OVERFLOW)
+
+// ---------------------------------------------------------------- kernels
+
+__device__ __forceinline__ void set_status(Ctrl *ctrl, int s) {
+    atomicCAS(&ctrl->status, 0, s);
+}
+
+// min / max of the cost matrix (one pass).
+__global__ void k_minmax(const int32_t *__restrict__ C, long long total, Ctrl *ctrl) {
+    int lo = INT_MAX, hi = INT_MIN;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if ((reinterpret_cast<uintptr_t>(C) & 15) == 0) {
+        const long long nv = total >> 2;
+        const int4 *C4 = reinterpret_cast<const int4 *>(C);
+        for (long long i = tid; i < nv; i += stride) {
+            const int4 c = ld_row4(C4 + i);
+            lo = min(lo, min(min(c.x, c.y), min(c.z, c.w)));
+            hi = max(hi, max(max(c.x, c.y), max(c.z, c.w)));
+        }
+        for (long long i = (nv << 2) + tid; i < total; i += stride) {
+            const int c = C[i];
+            lo = min(lo, c);
+            hi = max(hi, c);
+        }
+    } else {
+        for (long long i = tid; i < total; i += stride) {
+            const int c = C[i];
+            lo = min(lo, c);
+            hi = max(hi, c);
+        }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&ctrl->cmin, lo);
+        atomicMax(&ctrl->cmax, hi);
+    }
+}
+
+// n == 1: the only matching.
+__global__ void k_single(const int32_t *C, int32_t *match, long long *cost, long long *prices) {
+    if (match) match[0] = 0;
+    *cost = C[0];
+    if (prices) prices[0] = 0;
+}
+
+// Warm start, step 1: max of the given prices.
+__global__ void k_warm_pmax(const long long *__restrict__ p, int n, Ctrl *ctrl) {
+    long long m = LLONG_MIN;
+    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x)
+        m = max(m, p[y]);
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&ctrl->pmax, m);
+}
+
+// Warm start, step 2: q(y) = max p - p(y) >= 0 (a uniform shift), keys with
+// no mate, and the spread max q for the range check.
+__global__ void k_warm_init(const long long *__restrict__ p, int n, unsigned long long *key, Ctrl *ctrl) {
+    unsigned long long spread = 0;
+    const long long pm = ctrl->pmax;
+    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
+        unsigned long long q = (unsigned long long)(pm - p[y]);
+        if (pm - p[y] < 0) q = kQMax;       // wrapped difference: far out of range
+        spread = max(spread, q);
+        key[y] = pack_key(min(q, kQMax - 1), kNone);
+    }
+    for (int o = 16; o; o >>= 1) spread = max(spread, __shfl_xor_sync(0xffffffffu, spread, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&ctrl->qspread, spread);
+}
+
+// Smallest q over the columns (for the per-phase shift).
+__global__ void k_qmin(const unsigned long long *__restrict__ key, int n, Ctrl *ctrl, int slot) {
+    unsigned long long m = ~0ull;
+    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x)
+        m = min(m, key_q(__ldcg(key + y)));
+    for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(&ctrl->qmin[slot], m);
+}
+
+// Phase initialisation (Algorithm 5.2, refine initialisation): clear every
+// mate (f <- 0), keep prices shifted so that min q = 0, refresh the price
+// mirror and reset the row queue.
+template <bool WIDE>
+__global__ void k_reset(unsigned long long *__restrict__ key, void *__restrict__ qmv, int n,
+                        unsigned long long qlim, Ctrl *ctrl, int slot, int phase) {
+    const unsigned long long qmin = ctrl->qmin[slot];
+    bool bad = false;
+    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
+        const unsigned long long q = key_q(key[y]) - qmin;
+        bad |= q > qlim;
+        key[y] = pack_key(q, kNone);
+        if (WIDE) static_cast<unsigned long long *>(qmv)[y] = q;
+        else static_cast<uint32_t *>(qmv)[y] = (uint32_t)q;
+    }
+    if (bad) set_status(ctrl, LA_ERR_OVERFLOW);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->next_row = 0;
+        ctrl->qmin[slot ^ 1] = ~0ull;
+        ctrl->phase_start_scans[phase & 63] = ctrl->scans;
+    }
+}
+
+// One row scan: best / second best of v(x,y) = (C[x][y] - cmin)(n+1) + q(y).
+template <bool WIDE, bool VEC>
+__device__ __forceinline__ auto scan_row(const int32_t *__restrict__ crow, int n, int cmin,
+                                         uint32_t np1, const void *__restrict__ qmv, int lane) {
+    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    Top2<V> t;
+    top2_init(t);
+    if (VEC) {
+        const int4 *r4 = reinterpret_cast<const int4 *>(crow);
+        const int nv = n >> 2;
+#pragma unroll 4
+        for (int j = lane; j < nv; j += 32) {
+            const int4 c = ld_row4(r4 + j);
+            const int y = j << 2;
+            if (WIDE) {
+                const unsigned long long *q = static_cast<const unsigned long long *>(qmv) + y;
+                const ulonglong2 qa = ld_q2(q), qb = ld_q2(q + 2);
+                top2_push<V>(t, (V)(uint32_t)(c.x - cmin) * np1 + qa.x, qa.x, y);
+                top2_push<V>(t, (V)(uint32_t)(c.y - cmin) * np1 + qa.y, qa.y, y + 1);
+                top2_push<V>(t, (V)(uint32_t)(c.z - cmin) * np1 + qb.x, qb.x, y + 2);
+                top2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + qb.y, qb.y, y + 3);
+            } else {
+                const uint4 q = ld_q4(static_cast<const uint32_t *>(qmv) + y);
+                top2_push<V>(t, (uint32_t)(c.x - cmin) * np1 + q.x, q.x, y);
+                top2_push<V>(t, (uint32_t)(c.y - cmin) * np1 + q.y, q.y, y + 1);
+                top2_push<V>(t, (uint32_t)(c.z - cmin) * np1 + q.z, q.z, y + 2);
+                top2_push<V>(t, (uint32_t)(c.w - cmin) * np1 + q.w, q.w, y + 3);
+            }
+        }
+    } else {
+        for (int y = lane; y < n; y += 32) {
+            const int c = ld_row1(crow + y);
+            const V q = WIDE ? (V)__ldcg(static_cast<const unsigned long long *>(qmv) + y)
+                             : (V)__ldcg(static_cast<const uint32_t *>(qmv) + y);
+            top2_push<V>(t, (V)(uint32_t)(c - cmin) * np1 + q, q, y);
+        }
+    }
+    top2_warp_reduce(t);
+    return t;
+}
+
+// The refine phase: persistent grid, one warp per free row.
+template <bool WIDE, bool VEC>
+__global__ void __launch_bounds__(256)
+k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
+         unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
+         Ctrl *__restrict__ ctrl, unsigned long long budget) {
+    const int lane = threadIdx.x & 31;
+    int row = -1;
+    unsigned long long wins = 0, displaced = 0, scans = 0;
+    for (;;) {
+        if (row < 0) {
+            int r = 0;
+            if (lane == 0) r = atomicAdd(&ctrl->next_row, 1);
+            row = __shfl_sync(0xffffffffu, r, 0);
+            if (row >= n) break;
+        }
+        unsigned long long s = 0;
+        int st = 0;
+        if (lane == 0) {
+            s = atomicAdd(&ctrl->scans, 1ull);
+            st = *reinterpret_cast<volatile int *>(&ctrl->status);
+        }
+        s = __shfl_sync(0xffffffffu, s, 0);
+        st = __shfl_sync(0xffffffffu, st, 0);
+        if (st != 0) break;
+        if (s >= budget) {
+            if (lane == 0) set_status(ctrl, LA_ERR_ITER_LIMIT);
+            break;
+        }
+        ++scans;
+        const auto t = scan_row<WIDE, VEC>(C + (size_t)row * n, n, cmin, np1, qmv, lane);
+        // double push: x -> w, relabel w, w's old mate becomes free
+        const unsigned long long nq = (unsigned long long)t.qb + (t.b2 - t.b1) + eps;
+        if (t.w >= n || nq > qlim) {
+            if (lane == 0) set_status(ctrl, t.w >= n ? LA_ERR_INTERNAL : LA_ERR_OVERFLOW);
+            break;
+        }
+        const unsigned long long nk = pack_key(nq, (uint32_t)row);
+        unsigned long long old = 0;
+        if (lane == 0) {
+            old = atomicMin(key + t.w, nk);
+            const unsigned long long qnow = old > nk ? nq : key_q(old);
+            if (WIDE) atomicMax(static_cast<unsigned long long *>(qmv) + t.w, qnow);
+            else atomicMax(static_cast<uint32_t *>(qmv) + t.w, (uint32_t)qnow);
+        }
+        old = __shfl_sync(0xffffffffu, old, 0);
+        if (old > nk) {
+            ++wins;
+            const uint32_t m = key_mate(old);
+            if (m != kNone) {
+                ++displaced;
+                row = (int)m;
+            } else {
+                row = -1;
+            }
+        }
+        // else: a lower price got there first; rescan this row
+    }
+    if (lane == 0 && scans) {
+        atomicAdd(&ctrl->wins, wins);
+        atomicAdd(&ctrl->displaced, displaced);
+        atomicMax(&ctrl->max_chain, scans);
+    }
+}
+
+// Read the matching out of the column keys; exact int64 cost.
+__global__ void k_finalize(const int32_t *__restrict__ C, int n, const unsigned long long *__restrict__ key,
+                           int32_t *match, long long *cost, long long *prices, Ctrl *ctrl, int slot) {
+    long long sum = 0;
+    const unsigned long long qmin = prices ? ctrl->qmin[slot] : 0;
+    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
+        const unsigned long long k = key[y];
+        const uint32_t m = key_mate(k);
+        if (m >= (uint32_t)n) {
+            set_status(ctrl, LA_ERR_INTERNAL);
+            continue;
+        }
+        if (match) match[m] = y;
+        sum += C[(size_t)m * n + y];
+        if (prices) prices[y] = -(long long)(key_q(k) - qmin);
+    }
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0 && sum != 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(cost), (unsigned long long)sum);
+}
+
+// ---------------------------------------------------------------- host side
+
+struct Workspace {
+    int64_t cap = 0;
+    unsigned long long *key = nullptr;
+    void *qm = nullptr;
+    Ctrl *ctrl = nullptr;
+    Ctrl *h_ctrl = nullptr;
+    int num_sms = 0;
+    bool events = false;
+    cudaEvent_t ev[2 * kMaxPhases];
+};
+
+std::mutex g_mu;
+Workspace g_ws[kMaxDevices];
+
+void free_ws(Workspace &ws) {
+    cudaFree(ws.key);
+    cudaFree(ws.qm);
+    cudaFree(ws.ctrl);
+    cudaFreeHost(ws.h_ctrl);
+    if (ws.events)
+        for (auto &e : ws.ev) cudaEventDestroy(e);
+    ws = Workspace();
+}
+
+la_status ensure_ws(Workspace &ws, int64_t n) {
+    if (!ws.ctrl) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return LA_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&ws.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return LA_ERR_CUDA;
+        if (cudaMalloc(&ws.ctrl, sizeof(Ctrl)) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMallocHost(&ws.h_ctrl, sizeof(Ctrl)) != cudaSuccess) return LA_ERR_NOMEM;
+        for (auto &e : ws.ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return LA_ERR_CUDA;
+        ws.events = true;
+    }
+    if (ws.cap < n) {
+        cudaFree(ws.key);
+        cudaFree(ws.qm);
+        ws.key = nullptr;
+        ws.qm = nullptr;
+        ws.cap = 0;
+        const int64_t cap = std::max<int64_t>(n, 1024);
+        if (cudaMalloc(&ws.key, sizeof(unsigned long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.qm, sizeof(unsigned long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        ws.cap = cap;
+    }
+    return LA_OK;
+}
+
+template <bool WIDE, bool VEC>
+int refine_grid(int num_sms, int block, int n) {
+    static int occ[5] = {0, 0, 0, 0, 0};   // per block size / 64 (cached)
+    const int slot = std::min(4, block / 64);
+    if (!occ[slot]) {
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_refine<WIDE, VEC>, block, 0);
+        occ[slot] = std::max(1, o);
+    }
+    const int warps_per_block = block / 32;
+    const int need = (n + warps_per_block - 1) / warps_per_block;
+    return std::max(1, std::min(num_sms * occ[slot], need));
+}
+
+template <bool WIDE, bool VEC>
+void launch_refine(cudaStream_t s, int grid, int block, const int32_t *C, int n, int cmin, uint32_t np1,
+                   unsigned long long eps, unsigned long long qlim, Workspace &ws,
+                   unsigned long long budget) {
+    k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget);
+}
+
+inline int small_grid(int n, int block, int num_sms) {
+    return std::max(1, std::min((n + block - 1) / block, 4 * num_sms));
+}
+
+}  // namespace
+
+#define LA_CK(call)                                   \
+    do {                                              \
+        if ((call) != cudaSuccess) return LA_ERR_CUDA; \
+    } while (0)
+
+static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *opt, cudaStream_t s,
+                              int32_t *match_out, int64_t *cost_out, la_stats *st) {
+    const int alpha = (opt && opt->alpha) ? opt->alpha : 10;
+    const int64_t eps0 = opt ? opt->eps0 : 0;
+    const int block = (opt && opt->block_threads) ? opt->block_threads : kDefaultBlock;
+    const int64_t *init_prices = opt ? opt->init_prices : nullptr;
+    int64_t *prices_out = opt ? opt->prices_out : nullptr;
+    const bool profile = opt && opt->profile;
+    if (alpha < 2 || eps0 < 0 || block < 32 || block > 256 || block % 32) return LA_ERR_INVALID;
+    if (opt && opt->scan_budget < 0) return LA_ERR_INVALID;
+
+    la_stats stats;
+    std::memset(&stats, 0, sizeof(stats));
+    stats.n = n;
+    if (n == 0) {
+        LA_CK(cudaMemsetAsync(cost_out, 0, sizeof(int64_t), s));
+        LA_CK(cudaStreamSynchronize(s));
+        if (st) *st = stats;
+        return LA_OK;
+    }
+    int dev = 0;
+    LA_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return LA_ERR_INVALID;
+    Workspace &ws = g_ws[dev];
+    if (la_status e = ensure_ws(ws, n)) return e;
+
+    Ctrl init;
+    std::memset(&init, 0, sizeof(init));
+    init.cmin = INT_MAX;
+    init.cmax = INT_MIN;
+    init.qmin[0] = init.qmin[1] = ~0ull;
+    init.pmax = LLONG_MIN;
+    *ws.h_ctrl = init;
+    LA_CK(cudaMemcpyAsync(ws.ctrl, ws.h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+    int64_t launches = 0;
+
+    const long long total = (long long)n * n;
+    const int mm_grid = (int)std::max<long long>(1, std::min<long long>((total / 4 + 255) / 256, 8LL * ws.num_sms));
+    k_minmax<<<mm_grid, 256, 0, s>>>(cost, total, ws.ctrl);
+    ++launches;
+    if (n == 1) {
+        k_single<<<1, 1, 0, s>>>(cost, match_out, reinterpret_cast<long long *>(cost_out),
+                                 reinterpret_cast<long long *>(prices_out));
+        ++launches;
+        LA_CK(cudaGetLastError());
+        LA_CK(cudaStreamSynchronize(s));
+        stats.launches = launches;
+        if (st) *st = stats;
+        return LA_OK;
+    }
+    const int sg = small_grid(n, 256, ws.num_sms);
+    if (init_prices) {
+        k_warm_pmax<<<sg, 256, 0, s>>>(reinterpret_cast<const long long *>(init_prices), n, ws.ctrl);
+        k_warm_init<<<sg, 256, 0, s>>>(reinterpret_cast<const long long *>(init_prices), n, ws.key, ws.ctrl);
+        launches += 2;
+    } else {
+        LA_CK(cudaMemsetAsync(ws.key, 0xff, sizeof(unsigned long long) * n, s));  // q = 0, no mate
+    }
+    LA_CK(cudaGetLastError());
+    LA_CK(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    LA_CK(cudaStreamSynchronize(s));
+    const Ctrl c0 = *ws.h_ctrl;
+
+    const unsigned long long np1 = (unsigned long long)n + 1;
+    const unsigned long long range = (unsigned long long)((long long)c0.cmax - (long long)c0.cmin);
+    const unsigned long long Ct = np1 * range;
+    const unsigned long long S = init_prices ? c0.qspread : 0;
+    stats.scaled_range = (int64_t)Ct;
+    if (Ct >= kRangeLimit || S >= (1ull << 42)) return LA_ERR_OVERFLOW;
+
+    // epsilon schedule (Algorithm 5.0): eps <- max(1, eps / alpha) until 1
+    std::vector<unsigned long long> sched;
+    {
+        unsigned long long e = eps0 > 0 ? (unsigned long long)eps0 : Ct;
+        do {
+            e = std::max<unsigned long long>(1, e / (unsigned long long)alpha);
+            sched.push_back(e);
+        } while (e > 1 && (int)sched.size() < kMaxPhases);
+        if (sched.back() != 1) return LA_ERR_INVALID;
+    }
+    stats.eps_first = (int64_t)sched[0];
+    // 32-bit reduced costs when every v = c~ + q provably fits (q stays below
+    // S + 3 C~ + 2 eps during a phase; see the range argument in DESIGN).
+    const unsigned long long need32 = S + 4 * Ct + 2 * sched[0] + 16;
+    const bool wide = need32 >= (1ull << 32);
+    const unsigned long long qlim = wide ? (kQMax - 1) : ((1ull << 32) - 2 - Ct);
+    const bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(cost) & 15) == 0);
+    stats.wide = wide;
+    stats.vector_loads = vec;
+
+    unsigned long long budget = opt && opt->scan_budget ? (unsigned long long)opt->scan_budget
+                                                        : 256ull * n * sched.size() + (1ull << 22);
+    int grid = 0;
+    if (wide) grid = vec ? refine_grid<true, true>(ws.num_sms, block, n) : refine_grid<true, false>(ws.num_sms, block, n);
+    else grid = vec ? refine_grid<false, true>(ws.num_sms, block, n) : refine_grid<false, false>(ws.num_sms, block, n);
+
+    const int cmin = c0.cmin;
+    int ph = 0;
+    for (; ph < (int)sched.size(); ++ph) {
+        const int slot = ph & 1;
+        k_qmin<<<sg, 256, 0, s>>>(ws.key, n, ws.ctrl, slot);
+        if (wide) k_reset<true><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph);
+        else k_reset<false><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph);
+        launches += 2;
+        if (profile) LA_CK(cudaEventRecord(ws.ev[2 * ph], s));
+        if (wide) {
+            if (vec) launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget);
+            else launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget);
+        } else {
+            if (vec) launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget);
+            else launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget);
+        }
+        ++launches;
+        if (profile) LA_CK(cudaEventRecord(ws.ev[2 * ph + 1], s));
+    }
+    const int fslot = ph & 1;
+    if (prices_out) {
+        k_qmin<<<sg, 256, 0, s>>>(ws.key, n, ws.ctrl, fslot);
+        ++launches;
+    }
+    LA_CK(cudaMemsetAsync(cost_out, 0, sizeof(int64_t), s));
+    k_finalize<<<sg, 256, 0, s>>>(cost, n, ws.key, match_out, reinterpret_cast<long long *>(cost_out),
+                                  reinterpret_cast<long long *>(prices_out), ws.ctrl, fslot);
+    ++launches;
+    LA_CK(cudaGetLastError());
+    LA_CK(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    LA_CK(cudaStreamSynchronize(s));
+    const Ctrl c1 = *ws.h_ctrl;
+
+    stats.phases = (int64_t)sched.size();
+    stats.scans = (int64_t)c1.scans;
+    stats.wins = (int64_t)c1.wins;
+    stats.displaced = (int64_t)c1.displaced;
+    stats.launches = launches;
+    stats.refine_launches = (int64_t)sched.size();
+    stats.max_chain = (int64_t)c1.max_chain;
+    for (int k = 0; k < ph && k < LA_STATS_PHASES; ++k) {
+        const unsigned long long end = (k + 1 < ph) ? c1.phase_start_scans[k + 1] : c1.scans;
+        stats.phase_scans[k] = (int64_t)(end - c1.phase_start_scans[k]);
+    }
+    if (profile) {
+        double ms = 0;
+        for (int k = 0; k < ph; ++k) {
+            float t = 0;
+            LA_CK(cudaEventElapsedTime(&t, ws.ev[2 * k], ws.ev[2 * k + 1]));
+            ms += t;
+            if (k < LA_STATS_PHASES) stats.phase_ms[k] = t;
+        }
+        stats.refine_ms = ms;
+    }
+    if (st) *st = stats;
+    return (la_status)c1.status;
+}
+
+extern "C" {
+
+la_status la_solve_ex(const int32_t *cost, int32_t n, const la_options *opt, void *stream,
+                      int32_t *match_out, int64_t *cost_out, la_stats *stats_out) {
+    if (n < 0 || n > LA_MAX_N || !cost_out || (n > 0 && !cost)) return LA_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(g_mu);
+    return solve_locked(cost, n, opt, static_cast<cudaStream_t>(stream), match_out, cost_out, stats_out);
+}
+
+la_status la_solve(const int32_t *cost, int32_t n, void *stream, int32_t *match_out, int64_t *cost_out) {
+    return la_solve_ex(cost, n, nullptr, stream, match_out, cost_out, nullptr);
+}
+
+const char *la_status_string(la_status s) {
+    switch (s) {
+    case LA_OK: return "LA_OK";
+    case LA_ERR_INVALID: return "LA_ERR_INVALID: invalid argument";
+    case LA_ERR_CUDA: return "LA_ERR_CUDA: a CUDA runtime call failed";
+    case LA_ERR_OVERFLOW: return "LA_ERR_OVERFLOW: cost range too large for the exact price field";
+    case LA_ERR_ITER_LIMIT: return "LA_ERR_ITER_LIMIT: row-scan budget exhausted";
+    case LA_ERR_NOMEM: return "LA_ERR_NOMEM: device workspace allocation failed";
+    case LA_ERR_INTERNAL: return "LA_ERR_INTERNAL: device consistency check failed";
+    }
+    return "unknown la_status";
+}
+
+la_status la_release_workspace(void) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LA_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return LA_ERR_INVALID;
+    if (cudaDeviceSynchronize() != cudaSuccess) return LA_ERR_CUDA;
+    free_ws(g_ws[dev]);
+    return LA_OK;
+}
+
+int32_t la_version(void) { return 100; }
+
+}  // extern "C"

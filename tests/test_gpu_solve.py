@@ -1,0 +1,215 @@
+"""GPU parity of la_solve / la_solve_ex against the CPU oracle.
+
+Every case compares the exact optimal total cost bit for bit (all arithmetic
+is integer) and checks the returned matching with the oracle's certificate:
+it is a permutation, its cost is the claimed cost, and with the returned
+prices every row is 1-optimal on costs scaled by n + 1, which forces
+optimality (Sect. 5.1; the eps-optimality bound of Lemma 5.6 with eps = 1).
+The matching itself may differ from the oracle's among ties.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_6231_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def la():
+    import torch
+    from paper_1110_6231_gb300 import build
+    build.build()
+    import paper_1110_6231_gb300 as la
+    assert torch.cuda.is_available()
+    return la
+
+
+def gpu_solve(la, C, **kw):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(C, dtype=np.int32)).cuda()
+    sol = la.solve(t, want_prices=True, **kw)
+    return sol.cost, sol.match.cpu().numpy(), sol.prices.cpu().numpy(), sol.stats
+
+
+def check(la, C, expected=None, **kw):
+    cost, match, prices, st = gpu_solve(la, C, **kw)
+    if expected is None:
+        expected = oracle.hungarian(C)[0] if C.shape[0] <= 2048 else oracle.cost_scaling(C)[0]
+    assert cost == expected
+    assert oracle.check_matching(C, match, cost) == 0
+    assert oracle.check_eps_cs(C, match, prices, 1) == 0
+    return st
+
+
+def fixture(path):
+    lines = [l for l in open(path) if l.strip() and not l.startswith("#")]
+    cost = int(lines[0].split()[1])
+    C = np.array([[int(t) for t in l.split()] for l in lines[3:]], dtype=np.int32)
+    return C, cost
+
+
+@pytest.mark.parametrize("name", sorted(f for f in os.listdir(GOLDEN) if f.endswith(".txt")))
+def test_golden_fixtures(la, name):
+    C, cost = fixture(os.path.join(GOLDEN, name))
+    check(la, C, cost)
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 31, 32, 33, 127, 130, 255, 257, 511, 1000])
+def test_ragged_sizes_uniform(la, n):
+    for seed in range(3):
+        st = check(la, synth.uniform_costs(n, 0, 1000, seed))
+        assert st["vector_loads"] == (n % 4 == 0)
+
+
+@pytest.mark.parametrize("n", [64, 200, 512, 1023])
+def test_geometric(la, n):
+    for seed in range(2):
+        check(la, synth.geometric_costs(n, seed))
+
+
+def test_stored_optimal_costs_n256(la):
+    cases = [c for c in json.load(open(os.path.join(GOLDEN, "optimal_costs.json")))["cases"]
+             if c["workload"] == "uniform-n256-c1000"]
+    for c in cases[:40]:
+        C = synth.instance(c["workload"], c["seed"])
+        cost, match, prices, st = gpu_solve(la, C)
+        assert cost == c["cost"], c
+        assert oracle.check_matching(C, match, cost) == 0
+        assert st["phases"] == 6 and st["wide"] == 0
+
+
+def test_full_size_uniform_n4096(la):
+    """The n = 4096, costs in [0, 2^20) workload: 64-bit reduced costs."""
+    cases = [c for c in json.load(open(os.path.join(GOLDEN, "optimal_costs.json")))["cases"]
+             if c["workload"] == "uniform-n4096-c2^20"]
+    for c in cases[:3]:
+        C = synth.instance(c["workload"], c["seed"])
+        cost, match, prices, st = gpu_solve(la, C)
+        assert cost == c["cost"], c
+        assert oracle.check_matching(C, match, cost) == 0
+        assert oracle.check_eps_cs(C, match, prices, 1) == 0
+        assert st["wide"] == 1 and st["phases"] == 10
+
+
+def test_full_size_geometric_n8192(la):
+    """The n = 8192 geometric workload against the oracle's cost scaling."""
+    C = synth.instance("geometric-n8192", 0)
+    cost, match, prices, st = gpu_solve(la, C)
+    ref = oracle.cost_scaling(C)[0]
+    assert cost == ref
+    assert oracle.check_matching(C, match, cost) == 0
+    assert st["wide"] == 0
+
+
+def test_degenerate_and_extreme(la):
+    import torch
+    # n = 0
+    C0 = torch.zeros((0, 0), dtype=torch.int32, device="cuda")
+    assert la.solve(C0).cost == 0
+    # n = 1, most negative cost
+    check(la, np.array([[-(2**31)]], np.int32), -(2**31))
+    # all costs equal: one phase at eps = 1
+    st = check(la, np.full((40, 40), 123456, np.int32), 40 * 123456)
+    assert st["phases"] == 1
+    # full int32 range at small n: (n+1) * (2^32 - 1) < 2^40
+    rng = np.random.default_rng(1)
+    C = rng.choice([-(2**31), 2**31 - 1, 0, 7], size=(60, 60)).astype(np.int32)
+    check(la, C)
+    C = rng.integers(-(2**31), 2**31 - 1, size=(100, 100), dtype=np.int64).astype(np.int32)
+    check(la, C)
+    # ties everywhere
+    check(la, rng.integers(0, 2, size=(300, 300)).astype(np.int32))
+
+
+def test_overflow_reported(la):
+    """(n+1)(max C - min C) >= 2^40 is refused with LA_ERR_OVERFLOW."""
+    import torch
+    n = 400
+    C = np.zeros((n, n), np.int32)
+    C[0, 0] = 2**31 - 1
+    C[1, 1] = -(2**31)
+    sol = la.solve(torch.from_numpy(C).cuda(), check=False)
+    assert sol.stats["status"] == la.LA_ERR_OVERFLOW
+
+
+def test_scan_budget_returns_iter_limit_then_recovers(la):
+    """A tiny row-scan budget ends the refine with LA_ERR_ITER_LIMIT (no hang),
+    and the next call on the same workspace solves normally."""
+    import torch
+    C = synth.uniform_costs(256, 0, 1000, 3)
+    t = torch.from_numpy(C).cuda()
+    sol = la.solve(t, scan_budget=100, check=False)
+    assert sol.stats["status"] == la.LA_ERR_ITER_LIMIT
+    assert la.solve(t).cost == oracle.hungarian(C)[0]
+
+
+def test_alpha_and_eps0_options(la):
+    C = synth.geometric_costs(300, 5)
+    ref = oracle.hungarian(C)[0]
+    for alpha in (2, 4, 16):
+        check(la, C, ref, alpha=alpha)
+    check(la, C, ref, eps0=1)
+    check(la, C, ref, eps0=301 * 7)
+
+
+def test_warm_start_prices(la):
+    """Any start prices reach the optimum; the oracle's optimal duals do so
+    with about one scan per row (Alg. 5.2's initialisation makes them
+    eps-optimal at once)."""
+    import torch
+    C = synth.uniform_costs(500, 0, 10**5, 8)
+    h, hm, u, v = oracle.hungarian(C)
+    duals = torch.from_numpy(501 * v).cuda()
+    st = check(la, C, h, init_prices=duals, eps0=1)
+    cold = check(la, C, h)
+    assert st["phases"] == 1 and st["scans"] < cold["scans"]
+    rnd = torch.from_numpy(np.random.default_rng(0).integers(-10**9, 10**9, 500)).cuda()
+    check(la, C, h, init_prices=rnd)
+
+
+def test_misaligned_pointer_uses_scalar_path(la):
+    import torch
+    n = 64
+    C = synth.uniform_costs(n, 0, 1000, 2)
+    buf = torch.zeros(n * n + 1, dtype=torch.int32, device="cuda")
+    buf[1:] = torch.from_numpy(C.ravel()).cuda()
+    view = buf[1:].view(n, n)                      # 4-byte offset: no 128-bit loads
+    match = torch.empty(n, dtype=torch.int32, device="cuda")
+    cost = torch.empty(1, dtype=torch.int64, device="cuda")
+    st = la.la_stats()
+    rc = la.la_solve_ex(view.data_ptr(), n, None, None, match, cost, st)
+    assert rc == la.LA_OK
+    assert st.vector_loads == 0
+    assert int(cost.item()) == oracle.hungarian(C)[0]
+    assert oracle.check_matching(C, match.cpu().numpy(), int(cost.item())) == 0
+
+
+def test_la_solve_on_a_side_stream(la):
+    import torch
+    C = synth.uniform_costs(256, 0, 1000, 11)
+    t = torch.from_numpy(C).cuda()
+    s = torch.cuda.Stream()
+    match = torch.empty(256, dtype=torch.int32, device="cuda")
+    cost = torch.empty(1, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(s):
+        rc = la.la_solve(t, 256, s, match, cost)
+    assert rc == la.LA_OK
+    torch.cuda.synchronize()
+    assert int(cost.item()) == oracle.hungarian(C)[0]
+
+
+def test_profile_counts(la):
+    C = synth.uniform_costs(1024, 0, 1000, 1)
+    st = check(la, C, profile=True)
+    assert st["refine_launches"] == st["phases"] == 6
+    assert st["refine_ms"] > 0
+    assert st["scans"] >= 1024 * 6
+    assert st["wins"] == st["displaced"] + 1024 * 6
