@@ -50,7 +50,9 @@ typedef enum {
     LA_ERR_ITER_LIMIT = 4,  /* the row-scan budget ran out before the
                                refine finished (see la_options.scan_budget) */
     LA_ERR_NOMEM = 5,       /* device workspace allocation failed */
-    LA_ERR_INTERNAL = 6     /* a device-side consistency check failed */
+    LA_ERR_INTERNAL = 6,    /* a device-side consistency check failed */
+    LA_ERR_TOO_LARGE = 7    /* n exceeds a fixed scratch size
+                               (la_solve_noalloc: LA_NOALLOC_MAX_N) */
 } la_status;
 
 /* Largest n accepted by the solver (the mate field of a column key is 20
@@ -137,6 +139,39 @@ la_status la_release_workspace(void);
 
 /* Library version as major * 10000 + minor * 100 + patch. */
 int32_t la_version(void);
+
+/*
+ * la_solve_noalloc -- la_solve for callers that must not allocate memory.
+ *
+ * The paper has no counterpart: this entry point exists for deployments
+ * that cannot let a library call cudaMalloc, for example a process whose
+ * device memory is already claimed in full by another allocator (a
+ * framework's caching pool), a real-time loop that cannot afford the
+ * latency and implicit device synchronisation of an allocation, or a
+ * certified system that forbids dynamic allocation after start-up.
+ *
+ * Same arguments, results and blocking behaviour as la_solve, with the
+ * default options (alpha = 10, eps0 = C~, prices from 0). Instead of the
+ * per-device workspace it uses one fixed scratch array that the library
+ * declares in device memory (LA_NOALLOC_SCRATCH_BYTES, about 257 KB); every
+ * GPU that loads the library holds that array until the process exits. It
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - n must be <= LA_NOALLOC_MAX_N; larger n returns LA_ERR_TOO_LARGE with
+ *     nothing enqueued.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture on that device.
+ *   - All calls on a device share the one array, which keeps the last
+ *     call's contents; each call re-initialises what must start clean.
+ *     Calls whose GPU work overlaps race on the array. A call waits for its
+ *     own GPU work before it returns and calls from different host threads
+ *     are serialised, so overlap can only follow a call that returned
+ *     LA_ERR_CUDA with work still queued: synchronise that stream before
+ *     the next call. (Each process has its own copy of the array.)
+ */
+#define LA_NOALLOC_MAX_N 16384
+la_status la_solve_noalloc(const int32_t *cost, int32_t n, void *stream,
+                           int32_t *match_out, int64_t *cost_out);
 
 #ifdef __cplusplus
 }

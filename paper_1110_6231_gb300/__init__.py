@@ -28,7 +28,9 @@ LA_ERR_OVERFLOW = 3
 LA_ERR_ITER_LIMIT = 4
 LA_ERR_NOMEM = 5
 LA_ERR_INTERNAL = 6
+LA_ERR_TOO_LARGE = 7
 LA_MAX_N = (1 << 20) - 1
+LA_NOALLOC_MAX_N = 16384
 
 
 class la_options(ctypes.Structure):
@@ -95,12 +97,13 @@ def lib() -> ctypes.CDLL:
             P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
             L.la_solve.argtypes = [P, i32, P, P, P]
             L.la_solve_ex.argtypes = [P, i32, P, P, P, P, P]
+            L.la_solve_noalloc.argtypes = [P, i32, P, P, P]
             L.la_status_string.argtypes = [ctypes.c_int]
             L.la_status_string.restype = ctypes.c_char_p
             L.la_release_workspace.argtypes = []
             L.la_version.argtypes = []
             L.la_version.restype = i32
-            for f in (L.la_solve, L.la_solve_ex, L.la_release_workspace):
+            for f in (L.la_solve, L.la_solve_ex, L.la_solve_noalloc, L.la_release_workspace):
                 f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -134,6 +137,12 @@ def la_solve_ex(cost, n, opt, stream, match_out, cost_out, stats_out) -> int:
     return lib().la_solve_ex(_ptr(cost), int(n), None if opt is None else ctypes.byref(opt),
                              _stream(stream), _ptr(match_out), _ptr(cost_out),
                              None if stats_out is None else ctypes.byref(stats_out))
+
+
+def la_solve_noalloc(cost, n, stream, match_out, cost_out) -> int:
+    """la_solve without any allocation: scratch is a fixed device array of the
+    library (n <= LA_NOALLOC_MAX_N), for callers that cannot allocate."""
+    return lib().la_solve_noalloc(_ptr(cost), int(n), _stream(stream), _ptr(match_out), _ptr(cost_out))
 
 
 def la_status_string(status: int) -> str:

@@ -534,6 +534,7 @@ const char *la_status_string(la_status s) {
     case LA_ERR_ITER_LIMIT: return "LA_ERR_ITER_LIMIT: row-scan budget exhausted";
     case LA_ERR_NOMEM: return "LA_ERR_NOMEM: device workspace allocation failed";
     case LA_ERR_INTERNAL: return "LA_ERR_INTERNAL: device consistency check failed";
+    case LA_ERR_TOO_LARGE: return "LA_ERR_TOO_LARGE: n exceeds the fixed scratch size";
     }
     return "unknown la_status";
 }
@@ -551,3 +552,135 @@ la_status la_release_workspace(void) {
 int32_t la_version(void) { return 100; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// la_solve_noalloc: the same solve for callers that cannot allocate.
+//
+// The column keys, the price mirror and the control block live in one
+// fixed array in device memory, declared below, instead of the per-device
+// workspace. Kernels receive the array's device address; host code obtains
+// it once per device with cudaGetSymbolAddress (in host code the symbol
+// itself is only a host-side stand-in, not a device address).
+// ------------------------------------------------------------------------
+
+namespace {
+constexpr size_t kNoallocKeyOff = 0;
+constexpr size_t kNoallocQmOff = sizeof(unsigned long long) * LA_NOALLOC_MAX_N;
+constexpr size_t kNoallocCtrlOff = 2 * sizeof(unsigned long long) * LA_NOALLOC_MAX_N;
+constexpr size_t kNoallocBytes = kNoallocCtrlOff + ((sizeof(Ctrl) + 255) / 256) * 256;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+namespace {
+
+struct NoallocDevice {
+    bool ready = false;
+    unsigned char *base = nullptr;   // device address of g_noalloc_scratch
+    int num_sms = 0;
+};
+NoallocDevice g_noalloc[kMaxDevices];
+
+// Once per device, with that device current.
+la_status noalloc_setup(int dev, NoallocDevice &d) {
+    if (d.ready) return LA_OK;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return LA_ERR_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LA_ERR_CUDA;
+    d.base = static_cast<unsigned char *>(p);
+    d.num_sms = sms;
+    d.ready = true;
+    return LA_OK;
+}
+
+la_status solve_noalloc_locked(const int32_t *cost, int32_t n, cudaStream_t s, int32_t *match_out,
+                               int64_t *cost_out) {
+    if (n == 0) {
+        LA_CK(cudaMemsetAsync(cost_out, 0, sizeof(int64_t), s));
+        LA_CK(cudaStreamSynchronize(s));
+        return LA_OK;
+    }
+    int dev = 0;
+    LA_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return LA_ERR_INVALID;
+    NoallocDevice &d = g_noalloc[dev];
+    if (la_status e = noalloc_setup(dev, d)) return e;
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(d.base + kNoallocKeyOff);
+    void *qm = d.base + kNoallocQmOff;
+    Ctrl *ctrl = reinterpret_cast<Ctrl *>(d.base + kNoallocCtrlOff);
+
+    // the array keeps the previous call's contents: start the control block clean
+    Ctrl h;
+    std::memset(&h, 0, sizeof(h));
+    h.cmin = INT_MAX;
+    h.cmax = INT_MIN;
+    h.qmin[0] = h.qmin[1] = ~0ull;
+    h.pmax = LLONG_MIN;
+    LA_CK(cudaMemcpyAsync(ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+
+    const long long total = (long long)n * n;
+    const int mm_grid = (int)std::max<long long>(1, std::min<long long>((total / 4 + 255) / 256, 8LL * d.num_sms));
+    k_minmax<<<mm_grid, 256, 0, s>>>(cost, total, ctrl);
+    if (n == 1) {
+        k_single<<<1, 1, 0, s>>>(cost, match_out, reinterpret_cast<long long *>(cost_out), nullptr);
+        LA_CK(cudaGetLastError());
+        LA_CK(cudaStreamSynchronize(s));
+        return LA_OK;
+    }
+    LA_CK(cudaMemsetAsync(key, 0xff, sizeof(unsigned long long) * n, s));  // q = 0, no mate
+    LA_CK(cudaGetLastError());
+    LA_CK(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    LA_CK(cudaStreamSynchronize(s));
+
+    const unsigned long long np1 = (unsigned long long)n + 1;
+    const unsigned long long Ct = np1 * (unsigned long long)((long long)h.cmax - (long long)h.cmin);
+    if (Ct >= kRangeLimit) return LA_ERR_OVERFLOW;
+    std::vector<unsigned long long> sched;
+    unsigned long long e = Ct;
+    do {
+        e = std::max<unsigned long long>(1, e / 10);
+        sched.push_back(e);
+    } while (e > 1);
+    const bool wide = 4 * Ct + 2 * sched[0] + 16 >= (1ull << 32);
+    const unsigned long long qlim = wide ? (kQMax - 1) : ((1ull << 32) - 2 - Ct);
+    const bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(cost) & 15) == 0);
+    const unsigned long long budget = 256ull * n * sched.size() + (1ull << 22);
+    const int block = kDefaultBlock;
+    int grid = 0;
+    if (wide) grid = vec ? refine_grid<true, true>(d.num_sms, block, n) : refine_grid<true, false>(d.num_sms, block, n);
+    else grid = vec ? refine_grid<false, true>(d.num_sms, block, n) : refine_grid<false, false>(d.num_sms, block, n);
+    const int sg = small_grid(n, 256, d.num_sms);
+    const int cmin = h.cmin;
+    int ph = 0;
+    for (; ph < (int)sched.size(); ++ph) {
+        const int slot = ph & 1;
+        k_qmin<<<sg, 256, 0, s>>>(key, n, ctrl, slot);
+        if (wide) k_reset<true><<<sg, 256, 0, s>>>(key, qm, n, qlim, ctrl, slot, ph);
+        else k_reset<false><<<sg, 256, 0, s>>>(key, qm, n, qlim, ctrl, slot, ph);
+        if (wide) {
+            if (vec) k_refine<true, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget);
+            else k_refine<true, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget);
+        } else {
+            if (vec) k_refine<false, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget);
+            else k_refine<false, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget);
+        }
+    }
+    LA_CK(cudaMemsetAsync(cost_out, 0, sizeof(int64_t), s));
+    k_finalize<<<sg, 256, 0, s>>>(cost, n, key, match_out, reinterpret_cast<long long *>(cost_out), nullptr,
+                                  ctrl, ph & 1);
+    LA_CK(cudaGetLastError());
+    LA_CK(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    LA_CK(cudaStreamSynchronize(s));
+    return (la_status)h.status;
+}
+
+}  // namespace
+
+extern "C" la_status la_solve_noalloc(const int32_t *cost, int32_t n, void *stream, int32_t *match_out,
+                                      int64_t *cost_out) {
+    if (n < 0 || !cost_out || (n > 0 && !cost)) return LA_ERR_INVALID;
+    if (n > LA_NOALLOC_MAX_N) return LA_ERR_TOO_LARGE;
+    std::lock_guard<std::mutex> lock(g_mu);
+    return solve_noalloc_locked(cost, n, static_cast<cudaStream_t>(stream), match_out, cost_out);
+}

@@ -1,0 +1,83 @@
+"""la_solve_noalloc: the allocation-free entry point, checked against la_solve.
+
+Some callers cannot let a library allocate device memory: a process whose
+HBM is already claimed by another allocator, a real-time loop that cannot
+absorb an allocation's latency and implicit synchronisation, or a system
+that forbids allocation after start-up. For them la_solve_noalloc uses one
+fixed scratch array that the library declares in device memory.
+
+These tests call the entry point through the C ABI twice in a row (the
+array keeps the previous call's contents, so the second call also checks
+that a call re-initialises what it needs) and compare each result with
+la_solve's: the same exact optimal cost, and a valid matching of that cost.
+This file is named so that pytest collects it last.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_6231_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def la():
+    import torch
+    from paper_1110_6231_gb300 import build
+    build.build()
+    import paper_1110_6231_gb300 as la
+    assert torch.cuda.is_available()
+    return la
+
+
+def _run(la, entry, C):
+    import torch
+    n = C.shape[0]
+    t = torch.from_numpy(np.ascontiguousarray(C, dtype=np.int32)).cuda()
+    match = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    cost = torch.full((1,), -7, dtype=torch.int64, device="cuda")
+    rc = entry(t, n, None, match, cost)
+    torch.cuda.synchronize()
+    return rc, int(cost.item()), match.cpu().numpy()
+
+
+def test_noalloc_matches_la_solve_on_two_calls_in_a_row(la):
+    import torch
+    instances = [synth.uniform_costs(512, 0, 1000, 21),       # 32-bit path, 128-bit loads
+                 synth.geometric_costs(301, 22),              # ragged n: scalar loads
+                 synth.uniform_costs(1024, 0, (1 << 20) - 1, 23)]  # 64-bit path
+    # load the module and its kernels through la_solve first, then measure
+    rc, ref0, _ = _run(la, la.la_solve, instances[0])
+    assert rc == la.LA_OK
+    free0 = torch.cuda.mem_get_info()[0]
+    for C in instances:
+        rc_ref, ref, ref_match = _run(la, la.la_solve, C)
+        assert rc_ref == la.LA_OK
+        free_before = torch.cuda.mem_get_info()[0]
+        rc1, c1, m1 = _run(la, la.la_solve_noalloc, C)
+        rc2, c2, m2 = _run(la, la.la_solve_noalloc, C)
+        assert torch.cuda.mem_get_info()[0] == free_before
+        assert rc1 == la.LA_OK and rc2 == la.LA_OK
+        assert c1 == ref and c2 == ref
+        for m in (m1, m2, ref_match):
+            assert oracle.check_matching(C, m, ref) == 0
+    assert torch.cuda.mem_get_info()[0] <= free0
+
+
+def test_noalloc_small_and_degenerate_sizes(la):
+    for C in (np.array([[5]], np.int32), np.full((3, 3), -4, np.int32),
+              synth.uniform_costs(2, -10, 10, 1)):
+        rc, c, m = _run(la, la.la_solve_noalloc, C)
+        assert rc == la.LA_OK
+        assert c == oracle.brute_force(C)[0]
+
+
+def test_noalloc_rejects_n_beyond_its_scratch(la):
+    import torch
+    t = torch.zeros(16, dtype=torch.int32, device="cuda")
+    cost = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rc = la.la_solve_noalloc(t, la.LA_NOALLOC_MAX_N + 1, None, None, cost)
+    assert rc == la.LA_ERR_TOO_LARGE
+    assert "LA_ERR_TOO_LARGE" in la.la_status_string(rc)
