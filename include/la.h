@@ -86,7 +86,13 @@ typedef struct {
     int32_t profile;
     /* Tuning: threads per block of the refine kernel (0 = default 256). */
     int32_t block_threads;
+    /* Bit set of LA_FLAG_* values (0 = defaults). */
+    int32_t flags;
 } la_options;
+
+/* la_options.flags: scan every row in full on every bid instead of using
+   the exact candidate lists (for measurement and testing). */
+#define LA_FLAG_NO_CANDIDATE_LISTS 1
 
 /* Phases whose counters la_stats records one by one. */
 #define LA_STATS_PHASES 32
@@ -111,6 +117,9 @@ typedef struct {
     int64_t phase_scans[LA_STATS_PHASES];  /* row scans of each phase */
     double phase_ms[LA_STATS_PHASES];      /* refine time of each phase
                                               (profile != 0) */
+    int64_t full_scans;      /* scans that read the whole cost row */
+    int64_t list_scans;      /* scans answered exactly by the row's candidate
+                                list (64 columns) without reading the row */
 } la_stats;
 
 /*
@@ -139,6 +148,70 @@ la_status la_release_workspace(void);
 
 /* Library version as major * 10000 + minor * 100 + patch. */
 int32_t la_version(void);
+
+/*
+ * Batched solves. B independent instances packed back to back; instance i
+ * is the n_i x n_i row-major matrix at cost + offsets[i]. One persistent
+ * launch (replayed from a CUDA graph) solves them all: each CTA claims
+ * instances from a device work queue, largest first, and runs the complete
+ * cost-scaling solve of one instance (Sect. 5.1, Algorithm 5.0's epsilon
+ * loop with the refine of Algorithms 5.2 and 5.4, costs scaled by n_i + 1)
+ * with that instance's column keys in shared memory.
+ *   cost       device const int32, all instances.
+ *   offsets    device const int64[B]: element offset of each instance.
+ *   ns         device const int32[B]: 0 <= n_i <= max_n (see options).
+ *   match_out  device int32[sum n_i] or NULL: instance i's matching (row ->
+ *              column, 0-based within the instance) at the exclusive prefix
+ *              sum of n_0 .. n_{i-1}.
+ *   cost_out   device int64[B]: exact optimal cost of each instance.
+ *   status_out device int32[B] or NULL: la_status of each instance.
+ * Returns LA_OK when every instance succeeded, else the status of one that
+ * failed (instances are independent: the others are still solved). Blocks
+ * until the results are in place.
+ */
+#define LA_ALPHA_BUCKETS 16   /* alpha by size: bucket k holds 2^k <= n < 2^(k+1) */
+#define LA_BATCH_MAX_N 8192   /* largest instance of a batched solve */
+
+typedef struct {
+    /* Threads per CTA: 32 x the warps that bid concurrently on one instance
+       (64, 128, 256 or 512; 0 selects 128). */
+    int32_t block_threads;
+    /* Largest n the launch must hold in shared memory (0 = LA_BATCH_MAX_N);
+       smaller values let more CTAs share an SM. Instances with n > max_n
+       fail with LA_ERR_INVALID. */
+    int32_t max_n;
+    /* alpha for each size bucket (0 = 10). */
+    int32_t alpha[LA_ALPHA_BUCKETS];
+    /* Row scans per row and phase before LA_ERR_ITER_LIMIT (0 = 256). */
+    int32_t budget_factor;
+    /* Nonzero: launch directly instead of capturing and replaying a CUDA
+       graph (a graph is captured once per distinct argument set). */
+    int32_t no_graph;
+    /* Nonzero: time the launch with CUDA events (la_batch_stats.device_ms). */
+    int32_t profile;
+} la_batch_options;
+
+typedef struct {
+    int64_t instances;
+    int64_t failed;
+    int64_t scans;          /* row scans over all instances */
+    int64_t wins;
+    int64_t displaced;
+    int64_t phases;         /* refine phases over all instances */
+    int32_t max_n;          /* largest n seen */
+    int32_t grid;           /* persistent CTAs launched */
+    int32_t block_threads;
+    int32_t graph;          /* 1 if the launch was a CUDA graph replay */
+    double device_ms;       /* launch time (profile != 0) */
+} la_batch_stats;
+
+la_status la_solve_batched(const int32_t *cost, const int64_t *offsets, const int32_t *ns,
+                           int32_t B, void *stream, int32_t *match_out, int64_t *cost_out);
+
+la_status la_solve_batched_ex(const int32_t *cost, const int64_t *offsets, const int32_t *ns,
+                              int32_t B, const la_batch_options *opt, void *stream,
+                              int32_t *match_out, int64_t *cost_out, int32_t *status_out,
+                              la_batch_stats *stats_out);
 
 /*
  * la_solve_noalloc -- la_solve for callers that must not allocate memory.

@@ -31,6 +31,7 @@ LA_ERR_INTERNAL = 6
 LA_ERR_TOO_LARGE = 7
 LA_MAX_N = (1 << 20) - 1
 LA_NOALLOC_MAX_N = 16384
+LA_FLAG_NO_CANDIDATE_LISTS = 1
 
 
 class la_options(ctypes.Structure):
@@ -42,6 +43,7 @@ class la_options(ctypes.Structure):
         ("scan_budget", ctypes.c_int64),
         ("profile", ctypes.c_int32),
         ("block_threads", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
     ]
 
 
@@ -62,6 +64,8 @@ class la_stats(ctypes.Structure):
         ("max_chain", ctypes.c_int64),
         ("phase_scans", ctypes.c_int64 * 32),
         ("phase_ms", ctypes.c_double * 32),
+        ("full_scans", ctypes.c_int64),
+        ("list_scans", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -72,6 +76,40 @@ class la_stats(ctypes.Structure):
                 v = list(v)[: max(0, min(32, int(self.phases)))]
             d[name] = v
         return d
+
+
+LA_ALPHA_BUCKETS = 16
+LA_BATCH_MAX_N = 8192
+
+
+class la_batch_options(ctypes.Structure):
+    _fields_ = [
+        ("block_threads", ctypes.c_int32),
+        ("max_n", ctypes.c_int32),
+        ("alpha", ctypes.c_int32 * LA_ALPHA_BUCKETS),
+        ("budget_factor", ctypes.c_int32),
+        ("no_graph", ctypes.c_int32),
+        ("profile", ctypes.c_int32),
+    ]
+
+
+class la_batch_stats(ctypes.Structure):
+    _fields_ = [
+        ("instances", ctypes.c_int64),
+        ("failed", ctypes.c_int64),
+        ("scans", ctypes.c_int64),
+        ("wins", ctypes.c_int64),
+        ("displaced", ctypes.c_int64),
+        ("phases", ctypes.c_int64),
+        ("max_n", ctypes.c_int32),
+        ("grid", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+        ("graph", ctypes.c_int32),
+        ("device_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class LaError(RuntimeError):
@@ -98,12 +136,15 @@ def lib() -> ctypes.CDLL:
             L.la_solve.argtypes = [P, i32, P, P, P]
             L.la_solve_ex.argtypes = [P, i32, P, P, P, P, P]
             L.la_solve_noalloc.argtypes = [P, i32, P, P, P]
+            L.la_solve_batched.argtypes = [P, P, P, i32, P, P, P]
+            L.la_solve_batched_ex.argtypes = [P, P, P, i32, P, P, P, P, P, P]
             L.la_status_string.argtypes = [ctypes.c_int]
             L.la_status_string.restype = ctypes.c_char_p
             L.la_release_workspace.argtypes = []
             L.la_version.argtypes = []
             L.la_version.restype = i32
-            for f in (L.la_solve, L.la_solve_ex, L.la_solve_noalloc, L.la_release_workspace):
+            for f in (L.la_solve, L.la_solve_ex, L.la_solve_noalloc, L.la_release_workspace,
+                      L.la_solve_batched, L.la_solve_batched_ex):
                 f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -145,6 +186,19 @@ def la_solve_noalloc(cost, n, stream, match_out, cost_out) -> int:
     return lib().la_solve_noalloc(_ptr(cost), int(n), _stream(stream), _ptr(match_out), _ptr(cost_out))
 
 
+def la_solve_batched(cost, offsets, ns, B, stream, match_out, cost_out) -> int:
+    return lib().la_solve_batched(_ptr(cost), _ptr(offsets), _ptr(ns), int(B), _stream(stream),
+                                  _ptr(match_out), _ptr(cost_out))
+
+
+def la_solve_batched_ex(cost, offsets, ns, B, opt, stream, match_out, cost_out, status_out,
+                        stats_out) -> int:
+    return lib().la_solve_batched_ex(_ptr(cost), _ptr(offsets), _ptr(ns), int(B),
+                                     None if opt is None else ctypes.byref(opt), _stream(stream),
+                                     _ptr(match_out), _ptr(cost_out), _ptr(status_out),
+                                     None if stats_out is None else ctypes.byref(stats_out))
+
+
 def la_status_string(status: int) -> str:
     return lib().la_status_string(int(status)).decode()
 
@@ -169,7 +223,7 @@ class Solution:
 
 def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bool = False,
           scan_budget: int = 0, profile: bool = False, block_threads: int = 0,
-          stream=None, check: bool = True) -> Solution:
+          flags: int = 0, stream=None, check: bool = True) -> Solution:
     """Exact minimum-cost assignment of a square int32 CUDA tensor ``C``.
 
     ``init_prices`` (int64 CUDA tensor, paper sign, units of (n+1) C) warm
@@ -198,6 +252,7 @@ def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bo
     opt.scan_budget = scan_budget
     opt.profile = int(bool(profile))
     opt.block_threads = block_threads
+    opt.flags = flags
     st = la_stats()
     with torch.cuda.device(dev):
         rc = la_solve_ex(C, n, opt, stream, match, cost, st)
@@ -205,3 +260,51 @@ def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bo
         raise LaError(rc, "la_solve_ex")
     return Solution(cost=int(cost.item()) if rc == LA_OK else None, match=match,
                     stats=dict(st.as_dict(), status=rc), prices=prices)
+
+
+@dataclass
+class BatchSolution:
+    costs: object      # torch.int64 [B] exact optimal cost per instance
+    match: object      # torch.int32 [sum n] packed matchings (instance i at prefix sum of n)
+    status: object     # torch.int32 [B] la_status per instance
+    stats: dict
+
+
+def batch_options(block_threads: int = 0, max_n: int = 0, alpha=None, budget_factor: int = 0,
+                  no_graph: bool = False, profile: bool = False) -> la_batch_options:
+    """Build la_batch_options; ``alpha`` is an int or a per-bucket list
+    (bucket k holds 2^k <= n < 2^(k+1))."""
+    o = la_batch_options()
+    o.block_threads = block_threads
+    o.max_n = max_n
+    if alpha is not None:
+        vals = [alpha] * LA_ALPHA_BUCKETS if isinstance(alpha, int) else list(alpha)
+        for k, a in enumerate(vals[:LA_ALPHA_BUCKETS]):
+            o.alpha[k] = int(a)
+    o.budget_factor = budget_factor
+    o.no_graph = int(bool(no_graph))
+    o.profile = int(bool(profile))
+    return o
+
+
+def solve_batched(costs, offsets, ns, *, options: la_batch_options = None, stream=None,
+                  check: bool = True) -> BatchSolution:
+    """Solve B packed instances (int32 costs, int64 offsets, int32 sizes; all
+    CUDA tensors) in one persistent launch."""
+    import torch
+    B = int(ns.numel())
+    for t, dt in ((costs, torch.int32), (offsets, torch.int64), (ns, torch.int32)):
+        if t.dtype != dt or not t.is_cuda:
+            raise ValueError("costs int32, offsets int64 and ns int32 must be CUDA tensors")
+    dev = costs.device
+    total = int(ns.sum().item()) if B else 0
+    match = torch.empty(max(1, total), dtype=torch.int32, device=dev)
+    out = torch.empty(max(1, B), dtype=torch.int64, device=dev)
+    status = torch.empty(max(1, B), dtype=torch.int32, device=dev)
+    st = la_batch_stats()
+    with torch.cuda.device(dev):
+        rc = la_solve_batched_ex(costs, offsets, ns, B, options, stream, match, out, status, st)
+    if rc != LA_OK and check:
+        raise LaError(rc, "la_solve_batched_ex")
+    return BatchSolution(costs=out[:B], match=match[:total], status=status[:B],
+                         stats=dict(st.as_dict(), rc=rc))

@@ -49,6 +49,9 @@ struct Ctrl {
     long long pmax;                 // max of warm-start prices
     unsigned long long max_chain;   // most scans by one warp in one phase
     unsigned long long phase_start_scans[64];
+    unsigned long long rebase_total; // sum of the per-phase shifts of q
+    unsigned long long full_scans;   // row scans over all n columns
+    unsigned long long list_scans;   // row scans answered by the candidate list
 };
 
 // --- loads ---------------------------------------------------------------
@@ -131,6 +134,70 @@ __device__ __forceinline__ void top2_warp_reduce(Top2<V> &t) {
         t.qb = take ? oq : t.qb;
         t.w = take ? ow : t.w;
     }
+}
+
+template <typename V>
+struct ScanResult {
+    V b1, b2;      // best and second-best value over the row
+    V c1;          // scaled cost of the best column
+    int w;         // best column
+};
+
+// Lane-local top two of a stream of (value, column) pairs.
+template <typename V>
+struct Lane2 {
+    V b1, b2;
+    int w1, w2;
+};
+
+template <typename V>
+__device__ __forceinline__ void lane2_init(Lane2<V> &t) {
+    t.b1 = (V)~(V)0;
+    t.b2 = (V)~(V)0;
+    t.w1 = -1;
+    t.w2 = -1;
+}
+
+template <typename V>
+__device__ __forceinline__ void lane2_push(Lane2<V> &t, V v, int y) {
+    const bool better = v < t.b1;       // strict: keeps the earliest column
+    const bool second = v < t.b2;
+    const V hi = better ? t.b1 : v;
+    t.b2 = second ? hi : t.b2;
+    t.w2 = better ? t.w1 : (second ? y : t.w2);
+    t.w1 = better ? y : t.w1;
+    t.b1 = better ? v : t.b1;
+}
+
+// Butterfly merge of the lanes' (b1, w, c1, b2): every lane ends with the
+// row's best value, its column (lowest index among equal minima), that
+// column's scaled cost and the second-best value.
+template <typename V>
+__device__ __forceinline__ void warp_merge(ScanResult<V> &r) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const V o1 = shfl_xor_v(r.b1, m);
+        const V o2 = shfl_xor_v(r.b2, m);
+        const V oc = shfl_xor_v(r.c1, m);
+        const int ow = __shfl_xor_sync(0xffffffffu, r.w, m);
+        const V lo2 = o2 < r.b2 ? o2 : r.b2;
+        const V hi1 = o1 > r.b1 ? o1 : r.b1;
+        r.b2 = lo2 < hi1 ? lo2 : hi1;
+        const bool take = (o1 < r.b1) || (o1 == r.b1 && (unsigned)ow < (unsigned)r.w);
+        r.b1 = take ? o1 : r.b1;
+        r.c1 = take ? oc : r.c1;
+        r.w = take ? ow : r.w;
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_min(V v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const V o = shfl_xor_v(v, m);
+        v = o < v ? o : v;
+    }
+    return v;
 }
 
 }  // namespace la

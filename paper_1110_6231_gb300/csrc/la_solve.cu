@@ -144,19 +144,48 @@ __global__ void k_reset(unsigned long long *__restrict__ key, void *__restrict__
         ctrl->next_row = 0;
         ctrl->qmin[slot ^ 1] = ~0ull;
         ctrl->phase_start_scans[phase & 63] = ctrl->scans;
+        ctrl->rebase_total += qmin;
     }
 }
 
-// One row scan: best / second best of v(x,y) = (C[x][y] - cmin)(n+1) + q(y).
-template <bool WIDE, bool VEC>
-__device__ __forceinline__ auto scan_row(const int32_t *__restrict__ crow, int n, int cmin,
-                                         uint32_t np1, const void *__restrict__ qmv, int lane) {
+// Candidate lists (exact lazy scans). A full scan leaves, for row x, the
+// lane-local best and second-best columns of each of the 32 lanes (64
+// entries: column and scaled cost c~ - (n+1) min C) and the bound
+//   theta = min over lanes of the lane's second-best value.
+// Every column outside the list was beaten twice within its lane, so its
+// value was >= theta then; prices only fall (Lemma 5.2), so its value stays
+// >= theta, up to the uniform per-phase shift R that is tracked in the
+// control block. A later scan of x may therefore gather only the 64 listed
+// prices: when the list's best is <= theta it is the row's best, and
+// min(list second best, theta) is a lower bound of the row's second best
+// (exact when the list's second best is <= theta).
+struct RowLists {
+    int *cols;                  // [n][64] column, -1 = empty
+    void *costs;                // [n][64] scaled cost, u32 or u64
+    unsigned long long *theta;  // [n]: 0 = no list, ~0 = unbounded, else theta + R + 1
+};
+
+template <bool WIDE>
+__device__ __forceinline__ auto load_q(const void *qmv, int y) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
-    Top2<V> t;
-    top2_init(t);
+    if (WIDE) return (V)__ldcg(static_cast<const unsigned long long *>(qmv) + y);
+    else return (V)__ldcg(static_cast<const uint32_t *>(qmv) + y);
+}
+
+// Full scan of row x: v(x,y) = (C[x][y] - cmin)(n+1) + q(y) for every y.
+// Writes x's candidate list when lists are on.
+template <bool WIDE, bool VEC>
+__device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int row, int n, int cmin,
+                                          uint32_t np1, const void *__restrict__ qmv, int lane,
+                                          const RowLists &L, unsigned long long R) {
+    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    Lane2<V> t;
+    lane2_init(t);
+    int cnt;
     if (VEC) {
         const int4 *r4 = reinterpret_cast<const int4 *>(crow);
         const int nv = n >> 2;
+        cnt = lane < nv ? 4 * ((nv - lane + 31) >> 5) : 0;
 #pragma unroll 4
         for (int j = lane; j < nv; j += 32) {
             const int4 c = ld_row4(r4 + j);
@@ -164,28 +193,72 @@ __device__ __forceinline__ auto scan_row(const int32_t *__restrict__ crow, int n
             if (WIDE) {
                 const unsigned long long *q = static_cast<const unsigned long long *>(qmv) + y;
                 const ulonglong2 qa = ld_q2(q), qb = ld_q2(q + 2);
-                top2_push<V>(t, (V)(uint32_t)(c.x - cmin) * np1 + qa.x, qa.x, y);
-                top2_push<V>(t, (V)(uint32_t)(c.y - cmin) * np1 + qa.y, qa.y, y + 1);
-                top2_push<V>(t, (V)(uint32_t)(c.z - cmin) * np1 + qb.x, qb.x, y + 2);
-                top2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + qb.y, qb.y, y + 3);
+                lane2_push<V>(t, (V)(uint32_t)(c.x - cmin) * np1 + qa.x, y);
+                lane2_push<V>(t, (V)(uint32_t)(c.y - cmin) * np1 + qa.y, y + 1);
+                lane2_push<V>(t, (V)(uint32_t)(c.z - cmin) * np1 + qb.x, y + 2);
+                lane2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + qb.y, y + 3);
             } else {
                 const uint4 q = ld_q4(static_cast<const uint32_t *>(qmv) + y);
-                top2_push<V>(t, (uint32_t)(c.x - cmin) * np1 + q.x, q.x, y);
-                top2_push<V>(t, (uint32_t)(c.y - cmin) * np1 + q.y, q.y, y + 1);
-                top2_push<V>(t, (uint32_t)(c.z - cmin) * np1 + q.z, q.z, y + 2);
-                top2_push<V>(t, (uint32_t)(c.w - cmin) * np1 + q.w, q.w, y + 3);
+                lane2_push<V>(t, (uint32_t)(c.x - cmin) * np1 + q.x, y);
+                lane2_push<V>(t, (uint32_t)(c.y - cmin) * np1 + q.y, y + 1);
+                lane2_push<V>(t, (uint32_t)(c.z - cmin) * np1 + q.z, y + 2);
+                lane2_push<V>(t, (uint32_t)(c.w - cmin) * np1 + q.w, y + 3);
             }
         }
     } else {
+        cnt = lane < n ? ((n - lane + 31) >> 5) : 0;
         for (int y = lane; y < n; y += 32) {
             const int c = ld_row1(crow + y);
-            const V q = WIDE ? (V)__ldcg(static_cast<const unsigned long long *>(qmv) + y)
-                             : (V)__ldcg(static_cast<const uint32_t *>(qmv) + y);
-            top2_push<V>(t, (V)(uint32_t)(c - cmin) * np1 + q, q, y);
+            lane2_push<V>(t, (V)(uint32_t)(c - cmin) * np1 + load_q<WIDE>(qmv, y), y);
         }
     }
-    top2_warp_reduce(t);
-    return t;
+    // scaled costs of the lane's two columns (the row was just read: L2 hits)
+    const V c1 = t.w1 >= 0 ? (V)(uint32_t)(ld_row1(crow + t.w1) - cmin) * np1 : (V)0;
+    const V c2 = t.w2 >= 0 ? (V)(uint32_t)(ld_row1(crow + t.w2) - cmin) * np1 : (V)0;
+    if (L.cols) {
+        const size_t base = (size_t)row * 64 + 2 * lane;
+        *reinterpret_cast<int2 *>(L.cols + base) = make_int2(t.w1, t.w2);
+        V *cc = static_cast<V *>(L.costs) + base;
+        cc[0] = c1;
+        cc[1] = c2;
+        const V th = warp_min<V>(cnt > 2 ? t.b2 : (V)~(V)0);
+        if (lane == 0)
+            L.theta[row] = th == (V)~(V)0 ? ~0ull : (unsigned long long)th + R + 1;
+        __threadfence();   // the list is complete before this row can change hands
+    }
+    ScanResult<V> r{t.b1, t.b2, c1, t.w1 < 0 ? INT_MAX : t.w1};
+    warp_merge(r);
+    return r;
+}
+
+// Short scan of row x over its candidate list (two entries per lane).
+template <bool WIDE>
+__device__ __forceinline__ auto list_scan(int row, const void *__restrict__ qmv, int lane,
+                                          const RowLists &L) {
+    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    const size_t base = (size_t)row * 64 + 2 * lane;
+    const int2 yy = __ldcg(reinterpret_cast<const int2 *>(L.cols + base));
+    V c0, c1;
+    if (WIDE) {
+        const ulonglong2 cc = __ldcg(reinterpret_cast<const ulonglong2 *>(static_cast<const V *>(L.costs) + base));
+        c0 = cc.x;
+        c1 = cc.y;
+    } else {
+        const uint2 cc = __ldcg(reinterpret_cast<const uint2 *>(static_cast<const V *>(L.costs) + base));
+        c0 = cc.x;
+        c1 = cc.y;
+    }
+    const V inf = (V)~(V)0;
+    const V v0 = yy.x >= 0 ? c0 + load_q<WIDE>(qmv, yy.x) : inf;
+    const V v1 = yy.y >= 0 ? c1 + load_q<WIDE>(qmv, yy.y) : inf;
+    const bool first = (v0 < v1) || (v0 == v1 && (unsigned)yy.x < (unsigned)yy.y);
+    ScanResult<V> r;
+    r.b1 = first ? v0 : v1;
+    r.b2 = first ? v1 : v0;
+    r.c1 = first ? c0 : c1;
+    r.w = first ? (yy.x < 0 ? INT_MAX : yy.x) : (yy.y < 0 ? INT_MAX : yy.y);
+    warp_merge(r);
+    return r;
 }
 
 // The refine phase: persistent grid, one warp per free row.
@@ -193,10 +266,13 @@ template <bool WIDE, bool VEC>
 __global__ void __launch_bounds__(256)
 k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
          unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
-         Ctrl *__restrict__ ctrl, unsigned long long budget) {
+         Ctrl *__restrict__ ctrl, unsigned long long budget, RowLists L) {
+    constexpr unsigned kFlush = 16;      // scans between budget / status checks
     const int lane = threadIdx.x & 31;
+    const unsigned long long R = ctrl->rebase_total;
     int row = -1;
-    unsigned long long wins = 0, displaced = 0, scans = 0;
+    unsigned long long wins = 0, displaced = 0, total = 0, full = 0, hits = 0;
+    unsigned pending = 0;
     for (;;) {
         if (row < 0) {
             int r = 0;
@@ -204,23 +280,55 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
             row = __shfl_sync(0xffffffffu, r, 0);
             if (row >= n) break;
         }
-        unsigned long long s = 0;
-        int st = 0;
-        if (lane == 0) {
-            s = atomicAdd(&ctrl->scans, 1ull);
-            st = *reinterpret_cast<volatile int *>(&ctrl->status);
+        if (pending == kFlush) {
+            unsigned long long s = 0;
+            int st = 0;
+            if (lane == 0) {
+                s = atomicAdd(&ctrl->scans, (unsigned long long)kFlush);
+                st = *reinterpret_cast<volatile int *>(&ctrl->status);
+            }
+            s = __shfl_sync(0xffffffffu, s, 0);
+            st = __shfl_sync(0xffffffffu, st, 0);
+            pending = 0;
+            if (st != 0) break;
+            if (s + kFlush > budget) {
+                if (lane == 0) set_status(ctrl, LA_ERR_ITER_LIMIT);
+                break;
+            }
         }
-        s = __shfl_sync(0xffffffffu, s, 0);
-        st = __shfl_sync(0xffffffffu, st, 0);
-        if (st != 0) break;
-        if (s >= budget) {
-            if (lane == 0) set_status(ctrl, LA_ERR_ITER_LIMIT);
-            break;
+        ++pending;
+        ++total;
+        using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+        ScanResult<V> t;
+        bool ok = false;
+        if (L.cols) {
+            const unsigned long long th = __ldcg(L.theta + row);
+            if (th != 0) {
+                t = list_scan<WIDE>(row, qmv, lane, L);
+                // The list's best is the row's best when it does not exceed
+                // theta (every other column is >= theta). The second best is
+                // then min(list second, theta) at least, and bidding with that
+                // lower bound still leaves x eps-optimal at w: the price drop
+                // is at least eps and at most the full double push's.
+                if (th == ~0ull) {
+                    ok = true;
+                } else if ((unsigned long long)t.b1 + R + 1 <= th) {
+                    ok = true;
+                    const unsigned long long tf = th - R - 1;     // theta in this phase's frame
+                    if ((unsigned long long)t.b2 > tf) t.b2 = (V)tf;
+                }
+            }
         }
-        ++scans;
-        const auto t = scan_row<WIDE, VEC>(C + (size_t)row * n, n, cmin, np1, qmv, lane);
+        if (ok) {
+            ++hits;
+        } else {
+            ++full;
+            t = full_scan<WIDE, VEC>(C + (size_t)row * n, row, n, cmin, np1, qmv, lane, L, R);
+        }
+        __syncwarp();
         // double push: x -> w, relabel w, w's old mate becomes free
-        const unsigned long long nq = (unsigned long long)t.qb + (t.b2 - t.b1) + eps;
+        const unsigned long long qw = (unsigned long long)(t.b1 - t.c1);
+        const unsigned long long nq = qw + (t.b2 - t.b1) + eps;
         if (t.w >= n || nq > qlim) {
             if (lane == 0) set_status(ctrl, t.w >= n ? LA_ERR_INTERNAL : LA_ERR_OVERFLOW);
             break;
@@ -246,10 +354,13 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
         }
         // else: a lower price got there first; rescan this row
     }
-    if (lane == 0 && scans) {
+    if (lane == 0 && total) {
+        atomicAdd(&ctrl->scans, (unsigned long long)pending);
         atomicAdd(&ctrl->wins, wins);
         atomicAdd(&ctrl->displaced, displaced);
-        atomicMax(&ctrl->max_chain, scans);
+        atomicAdd(&ctrl->full_scans, full);
+        atomicAdd(&ctrl->list_scans, hits);
+        atomicMax(&ctrl->max_chain, total);
     }
 }
 
@@ -280,6 +391,9 @@ struct Workspace {
     int64_t cap = 0;
     unsigned long long *key = nullptr;
     void *qm = nullptr;
+    int *lcols = nullptr;                 // candidate lists
+    unsigned long long *lcosts = nullptr;
+    unsigned long long *ltheta = nullptr;
     Ctrl *ctrl = nullptr;
     Ctrl *h_ctrl = nullptr;
     int num_sms = 0;
@@ -293,6 +407,9 @@ Workspace g_ws[kMaxDevices];
 void free_ws(Workspace &ws) {
     cudaFree(ws.key);
     cudaFree(ws.qm);
+    cudaFree(ws.lcols);
+    cudaFree(ws.lcosts);
+    cudaFree(ws.ltheta);
     cudaFree(ws.ctrl);
     cudaFreeHost(ws.h_ctrl);
     if (ws.events)
@@ -315,12 +432,21 @@ la_status ensure_ws(Workspace &ws, int64_t n) {
     if (ws.cap < n) {
         cudaFree(ws.key);
         cudaFree(ws.qm);
+        cudaFree(ws.lcols);
+        cudaFree(ws.lcosts);
+        cudaFree(ws.ltheta);
         ws.key = nullptr;
         ws.qm = nullptr;
+        ws.lcols = nullptr;
+        ws.lcosts = nullptr;
+        ws.ltheta = nullptr;
         ws.cap = 0;
         const int64_t cap = std::max<int64_t>(n, 1024);
         if (cudaMalloc(&ws.key, sizeof(unsigned long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
         if (cudaMalloc(&ws.qm, sizeof(unsigned long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.lcols, sizeof(int) * 64 * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.lcosts, sizeof(unsigned long long) * 64 * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.ltheta, sizeof(unsigned long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
         ws.cap = cap;
     }
     return LA_OK;
@@ -343,8 +469,8 @@ int refine_grid(int num_sms, int block, int n) {
 template <bool WIDE, bool VEC>
 void launch_refine(cudaStream_t s, int grid, int block, const int32_t *C, int n, int cmin, uint32_t np1,
                    unsigned long long eps, unsigned long long qlim, Workspace &ws,
-                   unsigned long long budget) {
-    k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget);
+                   unsigned long long budget, const RowLists &L) {
+    k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L);
 }
 
 inline int small_grid(int n, int block, int num_sms) {
@@ -366,6 +492,7 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     const int64_t *init_prices = opt ? opt->init_prices : nullptr;
     int64_t *prices_out = opt ? opt->prices_out : nullptr;
     const bool profile = opt && opt->profile;
+    const bool lists = !(opt && (opt->flags & LA_FLAG_NO_CANDIDATE_LISTS));
     if (alpha < 2 || eps0 < 0 || block < 32 || block > 256 || block % 32) return LA_ERR_INVALID;
     if (opt && opt->scan_budget < 0) return LA_ERR_INVALID;
 
@@ -448,6 +575,11 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.wide = wide;
     stats.vector_loads = vec;
 
+    RowLists L{nullptr, nullptr, nullptr};
+    if (lists) {
+        L = RowLists{ws.lcols, ws.lcosts, ws.ltheta};
+        LA_CK(cudaMemsetAsync(ws.ltheta, 0, sizeof(unsigned long long) * n, s));
+    }
     unsigned long long budget = opt && opt->scan_budget ? (unsigned long long)opt->scan_budget
                                                         : 256ull * n * sched.size() + (1ull << 22);
     int grid = 0;
@@ -464,11 +596,11 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         launches += 2;
         if (profile) LA_CK(cudaEventRecord(ws.ev[2 * ph], s));
         if (wide) {
-            if (vec) launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget);
-            else launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget);
+            if (vec) launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L);
+            else launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L);
         } else {
-            if (vec) launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget);
-            else launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget);
+            if (vec) launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L);
+            else launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L);
         }
         ++launches;
         if (profile) LA_CK(cudaEventRecord(ws.ev[2 * ph + 1], s));
@@ -494,6 +626,8 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.launches = launches;
     stats.refine_launches = (int64_t)sched.size();
     stats.max_chain = (int64_t)c1.max_chain;
+    stats.full_scans = (int64_t)c1.full_scans;
+    stats.list_scans = (int64_t)c1.list_scans;
     for (int k = 0; k < ph && k < LA_STATS_PHASES; ++k) {
         const unsigned long long end = (k + 1 < ph) ? c1.phase_start_scans[k + 1] : c1.scans;
         stats.phase_scans[k] = (int64_t)(end - c1.phase_start_scans[k]);
@@ -659,11 +793,11 @@ la_status solve_noalloc_locked(const int32_t *cost, int32_t n, cudaStream_t s, i
         if (wide) k_reset<true><<<sg, 256, 0, s>>>(key, qm, n, qlim, ctrl, slot, ph);
         else k_reset<false><<<sg, 256, 0, s>>>(key, qm, n, qlim, ctrl, slot, ph);
         if (wide) {
-            if (vec) k_refine<true, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget);
-            else k_refine<true, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget);
+            if (vec) k_refine<true, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr});
+            else k_refine<true, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr});
         } else {
-            if (vec) k_refine<false, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget);
-            else k_refine<false, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget);
+            if (vec) k_refine<false, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr});
+            else k_refine<false, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr});
         }
     }
     LA_CK(cudaMemsetAsync(cost_out, 0, sizeof(int64_t), s));

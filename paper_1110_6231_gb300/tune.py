@@ -1,0 +1,107 @@
+"""Autotuner for batched solves.
+
+It picks, by measurement on the caller's own batch (or a sample of it):
+
+* alpha per size bucket (bucket k holds 2^k <= n < 2^(k+1)). alpha is the
+  divisor of eps between refine phases (Algorithm 5.0; the paper uses 10):
+  a larger alpha means fewer phases with more bidding each.
+* the CTA size, i.e. how many warps bid concurrently on one instance (rows
+  in flight per CTA).
+* the shared-memory key capacity ``max_n`` (the largest n in the batch), which
+  sets how many CTAs fit on an SM.
+
+Every candidate is timed with CUDA events through ``la_solve_batched_ex``
+(the same kernel the tuned call runs). The result is a small JSON table that
+``options_from_table`` turns back into ``la_batch_options``.
+"""
+
+from __future__ import annotations
+
+import json
+
+import paper_1110_6231_gb300 as la
+
+DEFAULT_ALPHAS = (4, 6, 8, 10, 16)
+DEFAULT_BLOCKS = (64, 128, 256)
+
+
+def _bucket(n: int) -> int:
+    return min(la.LA_ALPHA_BUCKETS - 1, max(0, int(n).bit_length() - 1))
+
+
+def _time(costs, offsets, ns, opt, reps):
+    import torch
+    B = int(ns.numel())
+    total = int(ns.sum().item())
+    match = torch.empty(max(1, total), dtype=torch.int32, device=costs.device)
+    out = torch.empty(max(1, B), dtype=torch.int64, device=costs.device)
+    best = None
+    for _ in range(reps):
+        st = la.la_batch_stats()
+        rc = la.la_solve_batched_ex(costs, offsets, ns, B, opt, None, match, out, None, st)
+        if rc != la.LA_OK:
+            raise la.LaError(rc, "autotune")
+        best = st.device_ms if best is None else min(best, st.device_ms)
+    return best
+
+
+def autotune_batched(costs, offsets, ns, *, alphas=DEFAULT_ALPHAS, blocks=DEFAULT_BLOCKS,
+                     per_bucket: int = 256, reps: int = 2, seed: int = 0) -> dict:
+    """Tune on CUDA tensors (int32 costs, int64 offsets, int32 ns).
+
+    Each bucket is timed on up to ``per_bucket`` of its instances; the CTA
+    size is then timed on the union of those samples with the tuned alphas.
+    """
+    import numpy as np
+    import torch
+
+    ns_h = ns.cpu().numpy()
+    off_h = offsets.cpu().numpy()
+    max_n = int(ns_h.max()) if ns_h.size else 1
+    rng = np.random.default_rng(seed)
+    buckets = {}
+    for i, n in enumerate(ns_h):
+        buckets.setdefault(_bucket(int(n)), []).append(i)
+    alpha_tab = [0] * la.LA_ALPHA_BUCKETS
+    timings = {"alpha": {}, "block": {}}
+    sample_all = []
+    for b, idx in sorted(buckets.items()):
+        idx = np.array(idx)
+        if idx.size > per_bucket:
+            idx = np.sort(rng.choice(idx, per_bucket, replace=False))
+        sample_all.extend(idx.tolist())
+        sub_off = torch.from_numpy(off_h[idx]).to(costs.device)
+        sub_ns = torch.from_numpy(ns_h[idx]).to(costs.device)
+        res = {}
+        for a in alphas:
+            opt = la.batch_options(block_threads=128, max_n=max_n, alpha=int(a), no_graph=True,
+                                   profile=True)
+            res[int(a)] = _time(costs, sub_off, sub_ns, opt, reps)
+        alpha_tab[b] = min(res, key=res.get)
+        timings["alpha"][b] = res
+    idx = np.array(sorted(sample_all))
+    sub_off = torch.from_numpy(off_h[idx]).to(costs.device)
+    sub_ns = torch.from_numpy(ns_h[idx]).to(costs.device)
+    for blk in blocks:
+        opt = la.batch_options(block_threads=int(blk), max_n=max_n, alpha=alpha_tab, no_graph=True,
+                               profile=True)
+        timings["block"][int(blk)] = _time(costs, sub_off, sub_ns, opt, reps)
+    block = min(timings["block"], key=timings["block"].get)
+    return {"block_threads": int(block), "max_n": max_n, "alpha": [int(a) for a in alpha_tab],
+            "timings_ms": {"alpha": {str(k): v for k, v in timings["alpha"].items()},
+                           "block": {str(k): v for k, v in timings["block"].items()}}}
+
+
+def options_from_table(table: dict, **extra) -> "la.la_batch_options":
+    return la.batch_options(block_threads=table["block_threads"], max_n=table["max_n"],
+                            alpha=table["alpha"], **extra)
+
+
+def save_table(path: str, table: dict) -> None:
+    with open(path, "w") as f:
+        json.dump(table, f, indent=1)
+
+
+def load_table(path: str) -> dict:
+    with open(path) as f:
+        return json.load(f)

@@ -56,8 +56,8 @@ def test_status_strings_without_gpu(libla):
 def test_struct_layout_matches_header(tmp_path):
     import paper_1110_6231_gb300 as la
     src = tmp_path / "layout.c"
-    fields = {"la_options": [f for f, _ in la.la_options._fields_],
-              "la_stats": [f for f, _ in la.la_stats._fields_]}
+    fields = {name: [f for f, _ in getattr(la, name)._fields_]
+              for name in ("la_options", "la_stats", "la_batch_options", "la_batch_stats")}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "la.h"', "int main(void){"]
     for st, fs in fields.items():
         lines.append(f'printf("{st} %zu\\n", sizeof({st}));')

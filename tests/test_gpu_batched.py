@@ -1,0 +1,119 @@
+"""GPU parity of la_solve_batched against the CPU oracle, instance by
+instance: exact optimal cost and a valid matching of that cost."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_6231_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def la():
+    import torch
+    from paper_1110_6231_gb300 import build
+    build.build()
+    import paper_1110_6231_gb300 as la
+    assert torch.cuda.is_available()
+    return la
+
+
+def pack(instances):
+    ns = np.array([c.shape[0] for c in instances], dtype=np.int32)
+    offsets = np.zeros(len(instances), dtype=np.int64)
+    sizes = ns.astype(np.int64) ** 2
+    if len(instances) > 1:
+        offsets[1:] = np.cumsum(sizes)[:-1]
+    flat = np.concatenate([c.ravel() for c in instances]) if instances else np.zeros(0, np.int32)
+    return flat.astype(np.int32), offsets, ns
+
+
+def run(la, flat, offsets, ns, **kw):
+    import torch
+    sol = la.solve_batched(torch.from_numpy(flat).cuda(), torch.from_numpy(offsets).cuda(),
+                           torch.from_numpy(ns).cuda(), options=la.batch_options(**kw) if kw else None,
+                           check=False)
+    return sol
+
+
+def verify(flat, offsets, ns, sol, expected=None):
+    costs = sol.costs.cpu().numpy()
+    match = sol.match.cpu().numpy()
+    status = sol.status.cpu().numpy()
+    mo = 0
+    for i in range(len(ns)):
+        n = int(ns[i])
+        C = flat[offsets[i]:offsets[i] + n * n].reshape(n, n)
+        ref = expected[i] if expected is not None else oracle.hungarian(C)[0]
+        assert status[i] == 0, (i, n, status[i])
+        assert costs[i] == ref, (i, n)
+        if n:
+            assert oracle.check_matching(C, match[mo:mo + n], ref) == 0, (i, n)
+        mo += n
+
+
+def test_mixed_small_batch(la):
+    rng = np.random.default_rng(3)
+    inst = []
+    for i, n in enumerate([0, 1, 2, 3, 5, 17, 31, 32, 33, 64, 100, 129, 255, 256, 300, 513]):
+        if i % 3 == 0:
+            inst.append(synth.uniform_costs(n, -50, 1000, i))
+        elif i % 3 == 1:
+            inst.append(synth.geometric_costs(n, i))
+        else:
+            inst.append(rng.integers(0, 3, size=(n, n)).astype(np.int32))   # heavy ties
+    flat, off, ns = pack(inst)
+    sol = run(la, flat, off, ns)
+    assert sol.stats["rc"] == 0
+    verify(flat, off, ns, sol)
+
+
+@pytest.mark.parametrize("block", [64, 128, 256, 512])
+def test_block_sizes_and_no_graph(la, block):
+    flat, off, ns = synth.batch(40, 7, lo=16, hi=400)
+    expected = [oracle.cost_scaling(flat[off[i]:off[i] + int(ns[i]) ** 2].reshape(int(ns[i]), int(ns[i])))[0]
+                for i in range(len(ns))]
+    for no_graph in (False, True):
+        sol = run(la, flat, off, ns, block_threads=block, no_graph=no_graph, max_n=512)
+        assert sol.stats["rc"] == 0
+        assert sol.stats["graph"] == (0 if no_graph else 1)
+        verify(flat, off, ns, sol, expected)
+
+
+def test_batch_workload_sample_and_graph_replay(la):
+    """A sample of the 10,000-instance workload (n log-uniform in [16, 1024],
+    half uniform [0, 10^4], half geometric), solved twice from the cached
+    graph, with the data changed in place between the two launches."""
+    import torch
+    flat, off, ns = synth.batch(120, 0)
+    expected = [oracle.cost_scaling(flat[off[i]:off[i] + int(ns[i]) ** 2].reshape(int(ns[i]), int(ns[i])))[0]
+                for i in range(len(ns))]
+    dc, do, dn = (torch.from_numpy(a).cuda() for a in (flat, off, ns))
+    opt = la.batch_options(max_n=1024, alpha=[0] * 4 + [4] * 12)
+    s1 = la.solve_batched(dc, do, dn, options=opt)
+    verify(flat, off, ns, s1, expected)
+    flat2, off2, ns2 = synth.batch(120, 0, cost_hi=5000)           # same sizes, new costs
+    assert np.array_equal(ns2, ns)
+    dc.copy_(torch.from_numpy(flat2))
+    s2 = la.solve_batched(dc, do, dn, options=opt)
+    assert s2.stats["graph"] == 1
+    verify(flat2, off2, ns2, s2)
+
+
+def test_invalid_sizes_flagged_per_instance(la):
+    inst = [synth.uniform_costs(20, 0, 9, 1), synth.uniform_costs(40, 0, 9, 2)]
+    flat, off, ns = pack(inst)
+    sol = run(la, flat, off, ns, max_n=32)
+    status = sol.status.cpu().numpy()
+    assert status[0] == 0 and status[1] == la.LA_ERR_INVALID
+    assert sol.stats["rc"] == la.LA_ERR_INVALID and sol.stats["failed"] == 1
+    assert int(sol.costs[0].item()) == oracle.hungarian(inst[0])[0]
+
+
+def test_empty_batch(la):
+    import torch
+    z = torch.zeros(0, dtype=torch.int32, device="cuda")
+    sol = la.solve_batched(z, torch.zeros(0, dtype=torch.int64, device="cuda"), z)
+    assert sol.costs.numel() == 0

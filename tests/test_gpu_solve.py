@@ -213,3 +213,14 @@ def test_profile_counts(la):
     assert st["refine_ms"] > 0
     assert st["scans"] >= 1024 * 6
     assert st["wins"] == st["displaced"] + 1024 * 6
+
+
+@pytest.mark.parametrize("kind,n", [("uniform", 1024), ("geometric", 1024), ("uniform", 100)])
+def test_candidate_lists_on_and_off(la, kind, n):
+    C = synth.uniform_costs(n, 0, (1 << 20) - 1, 5) if kind == "uniform" else synth.geometric_costs(n, 5)
+    ref = oracle.hungarian(C)[0]
+    on = check(la, C, ref)
+    off = check(la, C, ref, flags=la.LA_FLAG_NO_CANDIDATE_LISTS)
+    assert off["list_scans"] == 0 and off["full_scans"] == off["scans"]
+    assert on["list_scans"] + on["full_scans"] == on["scans"]
+    assert on["list_scans"] > 0
