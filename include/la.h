@@ -88,6 +88,10 @@ typedef struct {
     int32_t block_threads;
     /* Bit set of LA_FLAG_* values (0 = defaults). */
     int32_t flags;
+    /* When a phase is down to this many free rows, the refine hands them to
+       a one-CTA kernel that finishes the phase with the column keys in
+       shared memory (n <= 16384). 0 selects 32; negative disables it. */
+    int32_t tail_threshold;
 } la_options;
 
 /* la_options.flags: scan every row in full on every bid instead of using
@@ -120,6 +124,8 @@ typedef struct {
     int64_t full_scans;      /* scans that read the whole cost row */
     int64_t list_scans;      /* scans answered exactly by the row's candidate
                                 list (64 columns) without reading the row */
+    int64_t tail_scans;      /* scans made by the one-CTA tail kernel */
+    int32_t tail_phases;     /* phases that handed their last rows to it */
 } la_stats;
 
 /*
@@ -195,6 +201,7 @@ typedef struct {
     int64_t instances;
     int64_t failed;
     int64_t scans;          /* row scans over all instances */
+    int64_t scan_bytes;     /* cost bytes those scans read (4 n_i per scan) */
     int64_t wins;
     int64_t displaced;
     int64_t phases;         /* refine phases over all instances */

@@ -44,6 +44,7 @@ class la_options(ctypes.Structure):
         ("profile", ctypes.c_int32),
         ("block_threads", ctypes.c_int32),
         ("flags", ctypes.c_int32),
+        ("tail_threshold", ctypes.c_int32),
     ]
 
 
@@ -66,6 +67,8 @@ class la_stats(ctypes.Structure):
         ("phase_ms", ctypes.c_double * 32),
         ("full_scans", ctypes.c_int64),
         ("list_scans", ctypes.c_int64),
+        ("tail_scans", ctypes.c_int64),
+        ("tail_phases", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -98,6 +101,7 @@ class la_batch_stats(ctypes.Structure):
         ("instances", ctypes.c_int64),
         ("failed", ctypes.c_int64),
         ("scans", ctypes.c_int64),
+        ("scan_bytes", ctypes.c_int64),
         ("wins", ctypes.c_int64),
         ("displaced", ctypes.c_int64),
         ("phases", ctypes.c_int64),
@@ -223,7 +227,7 @@ class Solution:
 
 def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bool = False,
           scan_budget: int = 0, profile: bool = False, block_threads: int = 0,
-          flags: int = 0, stream=None, check: bool = True) -> Solution:
+          flags: int = 0, tail_threshold: int = 0, stream=None, check: bool = True) -> Solution:
     """Exact minimum-cost assignment of a square int32 CUDA tensor ``C``.
 
     ``init_prices`` (int64 CUDA tensor, paper sign, units of (n+1) C) warm
@@ -253,6 +257,7 @@ def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bo
     opt.profile = int(bool(profile))
     opt.block_threads = block_threads
     opt.flags = flags
+    opt.tail_threshold = tail_threshold
     st = la_stats()
     with torch.cuda.device(dev):
         rc = la_solve_ex(C, n, opt, stream, match, cost, st)

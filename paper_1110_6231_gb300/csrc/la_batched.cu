@@ -36,6 +36,7 @@ constexpr int kPrepThreads = 1024;
 constexpr int kMaxDevices = 64;
 
 struct BatchCtrl {
+    unsigned long long scan_bytes;   // 4 n bytes of cost per row scan
     unsigned long long scans;
     unsigned long long wins;
     unsigned long long displaced;
@@ -341,6 +342,7 @@ k_batch_solve(const int32_t *__restrict__ C, const long long *__restrict__ offse
             if (cost_out) cost_out[i] = (long long)s_cost;
             if (inst_status) inst_status[i] = st;
             atomicAdd(&ctrl->scans, s_scans);
+            atomicAdd(&ctrl->scan_bytes, s_scans * 4ull * (unsigned long long)n);
             if (st) {
                 atomicAdd(&ctrl->failed, 1);
                 atomicCAS(&ctrl->status, 0, st);
@@ -559,6 +561,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
         st->instances = B;
         st->failed = c.failed;
         st->scans = (int64_t)c.scans;
+        st->scan_bytes = (int64_t)c.scan_bytes;
         st->wins = (int64_t)c.wins;
         st->displaced = (int64_t)c.displaced;
         st->phases = (int64_t)c.phases;

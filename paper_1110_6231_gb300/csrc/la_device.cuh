@@ -52,6 +52,11 @@ struct Ctrl {
     unsigned long long rebase_total; // sum of the per-phase shifts of q
     unsigned long long full_scans;   // row scans over all n columns
     unsigned long long list_scans;   // row scans answered by the candidate list
+    unsigned long long tail_scans;   // row scans made by the tail kernel
+    int free_rows;                   // rows still unmatched in this phase
+    int handoff;                     // 1: the refine handed its rows to the tail kernel
+    int tail_count;                  // rows the refine handed over
+    int tail_phases;                 // phases that used the tail kernel
 };
 
 // --- loads ---------------------------------------------------------------

@@ -44,6 +44,9 @@ constexpr int kMaxPhases = 64;
 constexpr int kMaxDevices = 64;
 constexpr int kDefaultBlock = 256;
 constexpr unsigned long long kRangeLimit = 1ull << 40;  // C~ limit (LA_ERR_OVERFLOW)
+constexpr int kTailMaxN = 16384;      // shared-memory keys of the tail kernel (128 KB)
+constexpr int kTailThreads = 1024;
+constexpr int kDefaultTailRows = 32;
 
 // ---------------------------------------------------------------- kernels
 
@@ -145,6 +148,9 @@ __global__ void k_reset(unsigned long long *__restrict__ key, void *__restrict__
         ctrl->qmin[slot ^ 1] = ~0ull;
         ctrl->phase_start_scans[phase & 63] = ctrl->scans;
         ctrl->rebase_total += qmin;
+        ctrl->free_rows = n;
+        ctrl->handoff = 0;
+        ctrl->tail_count = 0;
     }
 }
 
@@ -172,11 +178,40 @@ __device__ __forceinline__ auto load_q(const void *qmv, int y) {
     else return (V)__ldcg(static_cast<const uint32_t *>(qmv) + y);
 }
 
+// Where a scan reads the column prices q(y) from.
+// The global mirror of the refine kernel (read at L2, see ld_q4).
+template <bool WIDE>
+struct MirrorPrices {
+    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    const void *qm;
+    __device__ __forceinline__ V q(int y) const { return load_q<WIDE>(qm, y); }
+    __device__ __forceinline__ void q4(int y, V &a, V &b, V &c, V &d) const {
+        if (WIDE) {
+            const unsigned long long *p = static_cast<const unsigned long long *>(qm) + y;
+            const ulonglong2 u = ld_q2(p), w = ld_q2(p + 2);
+            a = (V)u.x; b = (V)u.y; c = (V)w.x; d = (V)w.y;
+        } else {
+            const uint4 u = ld_q4(static_cast<const uint32_t *>(qm) + y);
+            a = (V)u.x; b = (V)u.y; c = (V)u.z; d = (V)u.w;
+        }
+    }
+};
+// The column keys held in shared memory by the tail kernel.
+template <bool WIDE>
+struct SharedKeyPrices {
+    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    const volatile unsigned long long *k;
+    __device__ __forceinline__ V q(int y) const { return (V)key_q(k[y]); }
+    __device__ __forceinline__ void q4(int y, V &a, V &b, V &c, V &d) const {
+        a = (V)key_q(k[y]); b = (V)key_q(k[y + 1]); c = (V)key_q(k[y + 2]); d = (V)key_q(k[y + 3]);
+    }
+};
+
 // Full scan of row x: v(x,y) = (C[x][y] - cmin)(n+1) + q(y) for every y.
 // Writes x's candidate list when lists are on.
-template <bool WIDE, bool VEC>
+template <bool WIDE, bool VEC, class P>
 __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int row, int n, int cmin,
-                                          uint32_t np1, const void *__restrict__ qmv, int lane,
+                                          uint32_t np1, const P &prices, int lane,
                                           const RowLists &L, unsigned long long R) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
     Lane2<V> t;
@@ -190,26 +225,18 @@ __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int 
         for (int j = lane; j < nv; j += 32) {
             const int4 c = ld_row4(r4 + j);
             const int y = j << 2;
-            if (WIDE) {
-                const unsigned long long *q = static_cast<const unsigned long long *>(qmv) + y;
-                const ulonglong2 qa = ld_q2(q), qb = ld_q2(q + 2);
-                lane2_push<V>(t, (V)(uint32_t)(c.x - cmin) * np1 + qa.x, y);
-                lane2_push<V>(t, (V)(uint32_t)(c.y - cmin) * np1 + qa.y, y + 1);
-                lane2_push<V>(t, (V)(uint32_t)(c.z - cmin) * np1 + qb.x, y + 2);
-                lane2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + qb.y, y + 3);
-            } else {
-                const uint4 q = ld_q4(static_cast<const uint32_t *>(qmv) + y);
-                lane2_push<V>(t, (uint32_t)(c.x - cmin) * np1 + q.x, y);
-                lane2_push<V>(t, (uint32_t)(c.y - cmin) * np1 + q.y, y + 1);
-                lane2_push<V>(t, (uint32_t)(c.z - cmin) * np1 + q.z, y + 2);
-                lane2_push<V>(t, (uint32_t)(c.w - cmin) * np1 + q.w, y + 3);
-            }
+            V qa, qb, qc, qd;
+            prices.q4(y, qa, qb, qc, qd);
+            lane2_push<V>(t, (V)(uint32_t)(c.x - cmin) * np1 + qa, y);
+            lane2_push<V>(t, (V)(uint32_t)(c.y - cmin) * np1 + qb, y + 1);
+            lane2_push<V>(t, (V)(uint32_t)(c.z - cmin) * np1 + qc, y + 2);
+            lane2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + qd, y + 3);
         }
     } else {
         cnt = lane < n ? ((n - lane + 31) >> 5) : 0;
         for (int y = lane; y < n; y += 32) {
             const int c = ld_row1(crow + y);
-            lane2_push<V>(t, (V)(uint32_t)(c - cmin) * np1 + load_q<WIDE>(qmv, y), y);
+            lane2_push<V>(t, (V)(uint32_t)(c - cmin) * np1 + prices.q(y), y);
         }
     }
     // scaled costs of the lane's two columns (the row was just read: L2 hits)
@@ -232,9 +259,8 @@ __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int 
 }
 
 // Short scan of row x over its candidate list (two entries per lane).
-template <bool WIDE>
-__device__ __forceinline__ auto list_scan(int row, const void *__restrict__ qmv, int lane,
-                                          const RowLists &L) {
+template <bool WIDE, class P>
+__device__ __forceinline__ auto list_scan(int row, const P &prices, int lane, const RowLists &L) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
     const size_t base = (size_t)row * 64 + 2 * lane;
     const int2 yy = __ldcg(reinterpret_cast<const int2 *>(L.cols + base));
@@ -249,8 +275,8 @@ __device__ __forceinline__ auto list_scan(int row, const void *__restrict__ qmv,
         c1 = cc.y;
     }
     const V inf = (V)~(V)0;
-    const V v0 = yy.x >= 0 ? c0 + load_q<WIDE>(qmv, yy.x) : inf;
-    const V v1 = yy.y >= 0 ? c1 + load_q<WIDE>(qmv, yy.y) : inf;
+    const V v0 = yy.x >= 0 ? c0 + prices.q(yy.x) : inf;
+    const V v1 = yy.y >= 0 ? c1 + prices.q(yy.y) : inf;
     const bool first = (v0 < v1) || (v0 == v1 && (unsigned)yy.x < (unsigned)yy.y);
     ScanResult<V> r;
     r.b1 = first ? v0 : v1;
@@ -261,13 +287,47 @@ __device__ __forceinline__ auto list_scan(int row, const void *__restrict__ qmv,
     return r;
 }
 
+// Best and second best of row x for its next bid: from the candidate list
+// when it decides the row (see RowLists), else from a full scan that also
+// rebuilds the list. The second best may be the lower bound theta.
+template <bool WIDE, bool VEC, class P>
+__device__ __forceinline__ auto scan_for_bid(const int32_t *__restrict__ C, int row, int n, int cmin,
+                                             uint32_t np1, const P &prices, int lane,
+                                             const RowLists &L, unsigned long long R, bool &full) {
+    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    ScanResult<V> t;
+    bool ok = false;
+    if (L.cols) {
+        const unsigned long long th = __ldcg(L.theta + row);
+        if (th != 0) {
+            t = list_scan<WIDE>(row, prices, lane, L);
+            // The list's best is the row's best when it does not exceed
+            // theta (every other column is >= theta). The second best is
+            // then min(list second, theta) at least, and bidding with that
+            // lower bound still leaves x eps-optimal at w: the price drop is
+            // at least eps and at most the full double push's.
+            if (th == ~0ull) {
+                ok = true;
+            } else if ((unsigned long long)t.b1 + R + 1 <= th) {
+                ok = true;
+                const unsigned long long tf = th - R - 1;     // theta in this phase's frame
+                if ((unsigned long long)t.b2 > tf) t.b2 = (V)tf;
+            }
+        }
+    }
+    full = !ok;
+    if (!ok) t = full_scan<WIDE, VEC>(C + (size_t)row * n, row, n, cmin, np1, prices, lane, L, R);
+    return t;
+}
+
 // The refine phase: persistent grid, one warp per free row.
 template <bool WIDE, bool VEC>
 __global__ void __launch_bounds__(256)
 k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
          unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
-         Ctrl *__restrict__ ctrl, unsigned long long budget, RowLists L) {
-    constexpr unsigned kFlush = 16;      // scans between budget / status checks
+         Ctrl *__restrict__ ctrl, unsigned long long budget, RowLists L, int tail_T,
+         int *__restrict__ tail_rows) {
+    constexpr unsigned kFlush = 8;       // scans between budget / status / hand-off checks
     const int lane = threadIdx.x & 31;
     const unsigned long long R = ctrl->rebase_total;
     int row = -1;
@@ -282,49 +342,32 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
         }
         if (pending == kFlush) {
             unsigned long long s = 0;
-            int st = 0;
+            int st = 0, ho = 0;
             if (lane == 0) {
                 s = atomicAdd(&ctrl->scans, (unsigned long long)kFlush);
                 st = *reinterpret_cast<volatile int *>(&ctrl->status);
+                ho = *reinterpret_cast<volatile int *>(&ctrl->handoff);
             }
             s = __shfl_sync(0xffffffffu, s, 0);
             st = __shfl_sync(0xffffffffu, st, 0);
+            ho = __shfl_sync(0xffffffffu, ho, 0);
             pending = 0;
             if (st != 0) break;
             if (s + kFlush > budget) {
                 if (lane == 0) set_status(ctrl, LA_ERR_ITER_LIMIT);
                 break;
             }
+            if (ho) {   // few free rows left: the tail kernel takes this one
+                if (lane == 0) tail_rows[atomicAdd(&ctrl->tail_count, 1)] = row;
+                break;
+            }
         }
         ++pending;
         ++total;
-        using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
-        ScanResult<V> t;
-        bool ok = false;
-        if (L.cols) {
-            const unsigned long long th = __ldcg(L.theta + row);
-            if (th != 0) {
-                t = list_scan<WIDE>(row, qmv, lane, L);
-                // The list's best is the row's best when it does not exceed
-                // theta (every other column is >= theta). The second best is
-                // then min(list second, theta) at least, and bidding with that
-                // lower bound still leaves x eps-optimal at w: the price drop
-                // is at least eps and at most the full double push's.
-                if (th == ~0ull) {
-                    ok = true;
-                } else if ((unsigned long long)t.b1 + R + 1 <= th) {
-                    ok = true;
-                    const unsigned long long tf = th - R - 1;     // theta in this phase's frame
-                    if ((unsigned long long)t.b2 > tf) t.b2 = (V)tf;
-                }
-            }
-        }
-        if (ok) {
-            ++hits;
-        } else {
-            ++full;
-            t = full_scan<WIDE, VEC>(C + (size_t)row * n, row, n, cmin, np1, qmv, lane, L, R);
-        }
+        bool was_full = false;
+        const auto t = scan_for_bid<WIDE, VEC>(C, row, n, cmin, np1, MirrorPrices<WIDE>{qmv}, lane, L, R, was_full);
+        if (was_full) ++full;
+        else ++hits;
         __syncwarp();
         // double push: x -> w, relabel w, w's old mate becomes free
         const unsigned long long qw = (unsigned long long)(t.b1 - t.c1);
@@ -350,6 +393,8 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
                 row = (int)m;
             } else {
                 row = -1;
+                if (tail_T > 0 && lane == 0 && atomicSub(&ctrl->free_rows, 1) - 1 <= tail_T)
+                    atomicExch(&ctrl->handoff, 1);
             }
         }
         // else: a lower price got there first; rescan this row
@@ -361,6 +406,102 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
         atomicAdd(&ctrl->full_scans, full);
         atomicAdd(&ctrl->list_scans, hits);
         atomicMax(&ctrl->max_chain, total);
+    }
+}
+
+// The end of a refine phase on one CTA. Once few rows are free (the refine
+// kernel's hand-off), every step of their displacement chains is latency
+// bound; here the column keys live in shared memory, so a step's price reads
+// and its commit (the same packed atomicMin) stay on the SM. The rows handed
+// over, and any still in the queue, are finished by the CTA's 32 warps, then
+// the keys go back to global memory.
+template <bool WIDE, bool VEC>
+__global__ void __launch_bounds__(1024)
+k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
+       unsigned long long qlim, unsigned long long *__restrict__ key, Ctrl *__restrict__ ctrl,
+       unsigned long long budget, RowLists L, const int *__restrict__ tail_rows) {
+    extern __shared__ unsigned long long skey[];
+    __shared__ int s_next, s_tc, s_q0, s_count;
+    if (*reinterpret_cast<volatile int *>(&ctrl->handoff) == 0) return;
+    constexpr unsigned kFlush = 8;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int y = tid; y < n; y += blockDim.x) skey[y] = __ldcg(key + y);
+    if (tid == 0) {
+        s_next = 0;
+        s_tc = ctrl->tail_count;
+        s_q0 = min(ctrl->next_row, n);
+        s_count = s_tc + (n - s_q0);
+    }
+    __syncthreads();
+    const unsigned long long R = ctrl->rebase_total;
+    const SharedKeyPrices<WIDE> prices{skey};
+    int row = -1;
+    unsigned long long wins = 0, displaced = 0, total = 0, full = 0, hits = 0;
+    unsigned pending = 0;
+    for (;;) {
+        if (row < 0) {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(&s_next, 1);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k >= s_count) break;
+            row = k < s_tc ? __ldcg(tail_rows + k) : s_q0 + (k - s_tc);
+        }
+        if (pending == kFlush) {
+            unsigned long long s = 0;
+            int st = 0;
+            if (lane == 0) {
+                s = atomicAdd(&ctrl->scans, (unsigned long long)kFlush);
+                st = *reinterpret_cast<volatile int *>(&ctrl->status);
+            }
+            s = __shfl_sync(0xffffffffu, s, 0);
+            st = __shfl_sync(0xffffffffu, st, 0);
+            pending = 0;
+            if (st != 0) break;
+            if (s + kFlush > budget) {
+                if (lane == 0) set_status(ctrl, LA_ERR_ITER_LIMIT);
+                break;
+            }
+        }
+        ++pending;
+        ++total;
+        bool was_full = false;
+        const auto t = scan_for_bid<WIDE, VEC>(C, row, n, cmin, np1, prices, lane, L, R, was_full);
+        if (was_full) ++full;
+        else ++hits;
+        __syncwarp();
+        const unsigned long long nq = (unsigned long long)(t.b1 - t.c1) + (t.b2 - t.b1) + eps;
+        if (t.w >= n || nq > qlim) {
+            if (lane == 0) set_status(ctrl, t.w >= n ? LA_ERR_INTERNAL : LA_ERR_OVERFLOW);
+            break;
+        }
+        const unsigned long long nk = pack_key(nq, (uint32_t)row);
+        unsigned long long old = 0;
+        if (lane == 0) old = atomicMin(skey + t.w, nk);
+        old = __shfl_sync(0xffffffffu, old, 0);
+        if (old > nk) {
+            ++wins;
+            const uint32_t m = key_mate(old);
+            if (m != kNone) {
+                ++displaced;
+                row = (int)m;
+            } else {
+                row = -1;
+            }
+        }
+    }
+    __syncthreads();
+    for (int y = tid; y < n; y += blockDim.x) key[y] = skey[y];
+    if (lane == 0 && total) {
+        atomicAdd(&ctrl->scans, (unsigned long long)pending);
+        atomicAdd(&ctrl->tail_scans, total);
+        atomicAdd(&ctrl->wins, wins);
+        atomicAdd(&ctrl->displaced, displaced);
+        atomicAdd(&ctrl->full_scans, full);
+        atomicAdd(&ctrl->list_scans, hits);
+    }
+    if (tid == 0) {
+        ctrl->handoff = 0;
+        ctrl->tail_phases += 1;
     }
 }
 
@@ -394,6 +535,7 @@ struct Workspace {
     int *lcols = nullptr;                 // candidate lists
     unsigned long long *lcosts = nullptr;
     unsigned long long *ltheta = nullptr;
+    int *tail_rows = nullptr;             // rows handed to the tail kernel
     Ctrl *ctrl = nullptr;
     Ctrl *h_ctrl = nullptr;
     int num_sms = 0;
@@ -410,6 +552,7 @@ void free_ws(Workspace &ws) {
     cudaFree(ws.lcols);
     cudaFree(ws.lcosts);
     cudaFree(ws.ltheta);
+    cudaFree(ws.tail_rows);
     cudaFree(ws.ctrl);
     cudaFreeHost(ws.h_ctrl);
     if (ws.events)
@@ -435,11 +578,13 @@ la_status ensure_ws(Workspace &ws, int64_t n) {
         cudaFree(ws.lcols);
         cudaFree(ws.lcosts);
         cudaFree(ws.ltheta);
+        cudaFree(ws.tail_rows);
         ws.key = nullptr;
         ws.qm = nullptr;
         ws.lcols = nullptr;
         ws.lcosts = nullptr;
         ws.ltheta = nullptr;
+        ws.tail_rows = nullptr;
         ws.cap = 0;
         const int64_t cap = std::max<int64_t>(n, 1024);
         if (cudaMalloc(&ws.key, sizeof(unsigned long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
@@ -447,6 +592,7 @@ la_status ensure_ws(Workspace &ws, int64_t n) {
         if (cudaMalloc(&ws.lcols, sizeof(int) * 64 * cap) != cudaSuccess) return LA_ERR_NOMEM;
         if (cudaMalloc(&ws.lcosts, sizeof(unsigned long long) * 64 * cap) != cudaSuccess) return LA_ERR_NOMEM;
         if (cudaMalloc(&ws.ltheta, sizeof(unsigned long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.tail_rows, sizeof(int) * cap) != cudaSuccess) return LA_ERR_NOMEM;
         ws.cap = cap;
     }
     return LA_OK;
@@ -469,8 +615,19 @@ int refine_grid(int num_sms, int block, int n) {
 template <bool WIDE, bool VEC>
 void launch_refine(cudaStream_t s, int grid, int block, const int32_t *C, int n, int cmin, uint32_t np1,
                    unsigned long long eps, unsigned long long qlim, Workspace &ws,
-                   unsigned long long budget, const RowLists &L) {
-    k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L);
+                   unsigned long long budget, const RowLists &L, int tail_T) {
+    k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L,
+                                               tail_T, ws.tail_rows);
+    if (tail_T > 0) {
+        static int smem_set = 0;
+        const int smem = (int)(sizeof(unsigned long long) * n);
+        if (smem > 48 * 1024 && smem > smem_set) {
+            cudaFuncSetAttribute(k_tail<WIDE, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            smem_set = smem;
+        }
+        k_tail<WIDE, VEC><<<1, kTailThreads, smem, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.ctrl, budget, L,
+                                                         ws.tail_rows);
+    }
 }
 
 inline int small_grid(int n, int block, int num_sms) {
@@ -493,6 +650,8 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     int64_t *prices_out = opt ? opt->prices_out : nullptr;
     const bool profile = opt && opt->profile;
     const bool lists = !(opt && (opt->flags & LA_FLAG_NO_CANDIDATE_LISTS));
+    int tail_T = (opt && opt->tail_threshold) ? opt->tail_threshold : kDefaultTailRows;
+    if (tail_T < 0 || n > kTailMaxN) tail_T = 0;
     if (alpha < 2 || eps0 < 0 || block < 32 || block > 256 || block % 32) return LA_ERR_INVALID;
     if (opt && opt->scan_budget < 0) return LA_ERR_INVALID;
 
@@ -596,13 +755,13 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         launches += 2;
         if (profile) LA_CK(cudaEventRecord(ws.ev[2 * ph], s));
         if (wide) {
-            if (vec) launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L);
-            else launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L);
+            if (vec) launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T);
+            else launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T);
         } else {
-            if (vec) launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L);
-            else launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L);
+            if (vec) launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T);
+            else launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T);
         }
-        ++launches;
+        launches += tail_T > 0 ? 2 : 1;
         if (profile) LA_CK(cudaEventRecord(ws.ev[2 * ph + 1], s));
     }
     const int fslot = ph & 1;
@@ -628,6 +787,8 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.max_chain = (int64_t)c1.max_chain;
     stats.full_scans = (int64_t)c1.full_scans;
     stats.list_scans = (int64_t)c1.list_scans;
+    stats.tail_scans = (int64_t)c1.tail_scans;
+    stats.tail_phases = c1.tail_phases;
     for (int k = 0; k < ph && k < LA_STATS_PHASES; ++k) {
         const unsigned long long end = (k + 1 < ph) ? c1.phase_start_scans[k + 1] : c1.scans;
         stats.phase_scans[k] = (int64_t)(end - c1.phase_start_scans[k]);
@@ -793,11 +954,11 @@ la_status solve_noalloc_locked(const int32_t *cost, int32_t n, cudaStream_t s, i
         if (wide) k_reset<true><<<sg, 256, 0, s>>>(key, qm, n, qlim, ctrl, slot, ph);
         else k_reset<false><<<sg, 256, 0, s>>>(key, qm, n, qlim, ctrl, slot, ph);
         if (wide) {
-            if (vec) k_refine<true, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr});
-            else k_refine<true, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr});
+            if (vec) k_refine<true, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr);
+            else k_refine<true, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr);
         } else {
-            if (vec) k_refine<false, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr});
-            else k_refine<false, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr});
+            if (vec) k_refine<false, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr);
+            else k_refine<false, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr);
         }
     }
     LA_CK(cudaMemsetAsync(cost_out, 0, sizeof(int64_t), s));

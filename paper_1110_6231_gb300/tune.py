@@ -46,11 +46,13 @@ def _time(costs, offsets, ns, opt, reps):
 
 
 def autotune_batched(costs, offsets, ns, *, alphas=DEFAULT_ALPHAS, blocks=DEFAULT_BLOCKS,
-                     per_bucket: int = 256, reps: int = 2, seed: int = 0) -> dict:
+                     per_bucket: int = 0, reps: int = 2, seed: int = 0) -> dict:
     """Tune on CUDA tensors (int32 costs, int64 offsets, int32 ns).
 
-    Each bucket is timed on up to ``per_bucket`` of its instances; the CTA
-    size is then timed on the union of those samples with the tuned alphas.
+    Each bucket's alpha is timed on that bucket's instances (all of them, or
+    a sample of ``per_bucket`` when it is > 0): a bucket's sub-batch must be
+    large enough to fill the GPU for its timing to reflect throughput. The
+    CTA size is then timed on the union of the samples with the tuned alphas.
     """
     import numpy as np
     import torch
@@ -67,14 +69,14 @@ def autotune_batched(costs, offsets, ns, *, alphas=DEFAULT_ALPHAS, blocks=DEFAUL
     sample_all = []
     for b, idx in sorted(buckets.items()):
         idx = np.array(idx)
-        if idx.size > per_bucket:
+        if per_bucket > 0 and idx.size > per_bucket:
             idx = np.sort(rng.choice(idx, per_bucket, replace=False))
         sample_all.extend(idx.tolist())
         sub_off = torch.from_numpy(off_h[idx]).to(costs.device)
         sub_ns = torch.from_numpy(ns_h[idx]).to(costs.device)
         res = {}
         for a in alphas:
-            opt = la.batch_options(block_threads=128, max_n=max_n, alpha=int(a), no_graph=True,
+            opt = la.batch_options(block_threads=128 if b >= 7 else 64, max_n=max_n, alpha=int(a), no_graph=True,
                                    profile=True)
             res[int(a)] = _time(costs, sub_off, sub_ns, opt, reps)
         alpha_tab[b] = min(res, key=res.get)

@@ -224,3 +224,16 @@ def test_candidate_lists_on_and_off(la, kind, n):
     assert off["list_scans"] == 0 and off["full_scans"] == off["scans"]
     assert on["list_scans"] + on["full_scans"] == on["scans"]
     assert on["list_scans"] > 0
+
+
+@pytest.mark.parametrize("tail", [-1, 8, 32, 100000])
+def test_tail_kernel_thresholds(la, tail):
+    """The one-CTA tail kernel finishes phases exactly: off, at the default
+    and small thresholds, and with a threshold above n (every phase is handed
+    over at its first completed chain)."""
+    for C in (synth.uniform_costs(700, 0, (1 << 20) - 1, 3), synth.geometric_costs(640, 4)):
+        st = check(la, C, tail_threshold=tail)
+        if tail < 0:
+            assert st["tail_phases"] == 0 and st["tail_scans"] == 0
+        else:
+            assert st["tail_phases"] >= 1
