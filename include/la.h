@@ -195,6 +195,10 @@ typedef struct {
     int32_t no_graph;
     /* Nonzero: time the launch with CUDA events (la_batch_stats.device_ms). */
     int32_t profile;
+    /* Device int64[sum n_i] or NULL: final column prices of every instance,
+       packed like match_out (paper sign, units of (n_i+1) C, up to a
+       constant per instance). */
+    int64_t *prices_out;
 } la_batch_options;
 
 typedef struct {
@@ -219,6 +223,89 @@ la_status la_solve_batched_ex(const int32_t *cost, const int64_t *offsets, const
                               int32_t B, const la_batch_options *opt, void *stream,
                               int32_t *match_out, int64_t *cost_out, int32_t *status_out,
                               la_batch_stats *stats_out);
+
+/*
+ * la_dual_certificate -- exact integer LP duals of an optimal assignment.
+ * Given a perfect matching M (device int32[n], row -> column), returns the
+ * duals tight on M: v (device int64[n], cost units) is the largest
+ * potential with v <= 0 and v(y) <= v(M(x)) + C[x][y] - C[x][M(x)] for all
+ * x, y (shortest paths, Bellman-Ford sweeps over the columns), and u
+ * (device int64[n] or NULL) is u(x) = C[x][M(x)] - v(M(x)). Then
+ * u(x) + v(y) <= C[x][y] everywhere, equality holds on M and
+ * sum u + sum v = cost(M), which proves M optimal (LP duality). These are
+ * the paper's prices at eps = 0 (c_p(x,y) = c(x,y) + p(x) - p(y) >= 0 with
+ * p(y) = v(y), p(x) = -u(x); Sect. 2, eps-optimality).
+ * Returns LA_ERR_INVALID if M is not a permutation and LA_ERR_INTERNAL if
+ * M is not optimal (no such duals exist). Blocks until done.
+ */
+la_status la_dual_certificate(const int32_t *cost, int32_t n, const int32_t *match, void *stream,
+                              int64_t *u_out, int64_t *v_out);
+
+/*
+ * Learned warm start. Refine's initialisation makes any price vector
+ * eps-optimal (Sect. 5.2, Algorithm 5.2), so a solve may start from
+ * predicted column prices and a small eps0 instead of p = 0 and eps0 = C~
+ * (Algorithm 5.0) and still returns the exact optimum. A set encoder
+ * predicts the optimal column duals from per-column cost statistics:
+ *   f_j   8 features of column j (LA_PRED_FEATURES, padded to 16): column
+ *         minimum and gap to the second minimum, the same on the row-reduced
+ *         matrix C - rowmin, the number of rows whose minimum is in column j,
+ *         the column mean, log T and log n (location features centred and
+ *         divided by T = 1 + mean column gap);
+ *   h1_j  = relu(W1^T f_j + b1), c = mean_j h1_j,
+ *   h2_j  = relu(W2^T [h1_j ; c] + b2), y_j = W3^T h2_j + b3 (width 128),
+ *   p(j)  = round((n+1) T (y_j - max y)).
+ * Matrix products run on the tensor cores with BF16 operands and FP32
+ * accumulation. The weights are one device float array of LA_PRED_PARAMS
+ * entries: a 16-float header (LA_PRED_MAGIC, version 1, 16, 128, then the
+ * calibrated eps0 factor q: eps0 = ceil((n+1) T q)), followed by W1 [16x128],
+ * b1 [128], W2 [256x128], b2 [128], W3 [128x8] (column 0 used), b3 [8].
+ */
+#define LA_PRED_FEATURES 8
+#define LA_PRED_FEATURES_PADDED 16
+#define LA_PRED_WIDTH 128
+#define LA_PRED_HEADER 16
+#define LA_PRED_PARAMS 36120
+#define LA_PRED_MAGIC 4242.0f
+
+/* Number of floats in a weight array (LA_PRED_PARAMS). */
+int32_t la_predictor_param_count(void);
+
+/* Column features of one n x n matrix: feats_out device float[n][16],
+ * inst_out device float[2] or NULL: (T, mean column minimum). */
+la_status la_features(const int32_t *cost, int32_t n, void *stream, float *feats_out,
+                      float *inst_out);
+
+/* Forward pass over N feature rows forming I instances (seg: device
+ * int32[I+1] row offsets): y_out device float[N]. */
+la_status la_predictor_forward(const float *params, const float *feats, const int32_t *seg,
+                               int32_t I, int32_t N, void *stream, float *y_out);
+
+/* One training step: forward, loss
+ *   L = (1/I) sum_i (1/n_i) sum_j (d_j - mean_i d)^2,  d = y - t
+ * (targets t: device float[N]; the loss ignores a per-instance shift of y or
+ * t, as prices do), backward, and an Adam
+ * update of params with moments adam_m / adam_v (device float[LA_PRED_PARAMS],
+ * zero at step 1; lr <= 0 or NULL moments skip the update). grad_out (device
+ * float[LA_PRED_PARAMS] or NULL) receives dL/dparams; loss_out (host) the loss. */
+la_status la_predictor_train_step(float *params, float *adam_m, float *adam_v, const float *feats,
+                                  const float *targets, const int32_t *seg, int32_t I, int32_t N,
+                                  int32_t step, float lr, float weight_decay, void *stream,
+                                  float *grad_out, float *loss_out);
+
+/* Predicted column prices of one matrix (device int64[n], paper sign, units of
+ * the scaled costs (n+1) C, max = 0). weights: device float[LA_PRED_PARAMS];
+ * a bad header returns LA_ERR_INVALID. _ex also returns the calibrated eps0
+ * (host int64). */
+la_status la_predict_prices(const int32_t *cost, int32_t n, const void *weights, void *stream,
+                            int64_t *prices_out);
+la_status la_predict_prices_ex(const int32_t *cost, int32_t n, const void *weights, void *stream,
+                               int64_t *prices_out, int64_t *eps0_out);
+
+/* Warm-started exact solve: la_predict_prices_ex, then la_solve_ex from the
+ * predicted prices and eps0. Same results as la_solve. */
+la_status la_solve_warm(const int32_t *cost, int32_t n, const void *weights, void *stream,
+                        int32_t *match_out, int64_t *cost_out, la_stats *stats_out);
 
 /*
  * la_solve_noalloc -- la_solve for callers that must not allocate memory.

@@ -83,6 +83,12 @@ class la_stats(ctypes.Structure):
 
 LA_ALPHA_BUCKETS = 16
 LA_BATCH_MAX_N = 8192
+LA_PRED_FEATURES = 8
+LA_PRED_FEATURES_PADDED = 16
+LA_PRED_WIDTH = 128
+LA_PRED_HEADER = 16
+LA_PRED_PARAMS = 36120
+LA_PRED_MAGIC = 4242.0
 
 
 class la_batch_options(ctypes.Structure):
@@ -93,6 +99,7 @@ class la_batch_options(ctypes.Structure):
         ("budget_factor", ctypes.c_int32),
         ("no_graph", ctypes.c_int32),
         ("profile", ctypes.c_int32),
+        ("prices_out", ctypes.c_void_p),
     ]
 
 
@@ -142,6 +149,20 @@ def lib() -> ctypes.CDLL:
             L.la_solve_noalloc.argtypes = [P, i32, P, P, P]
             L.la_solve_batched.argtypes = [P, P, P, i32, P, P, P]
             L.la_solve_batched_ex.argtypes = [P, P, P, i32, P, P, P, P, P, P]
+            L.la_predictor_param_count.argtypes = []
+            L.la_predictor_param_count.restype = i32
+            L.la_features.argtypes = [P, i32, P, P, P]
+            L.la_predictor_forward.argtypes = [P, P, P, i32, i32, P, P]
+            L.la_predictor_train_step.argtypes = [P, P, P, P, P, P, i32, i32, i32, ctypes.c_float,
+                                                  ctypes.c_float, P, P, P]
+            L.la_predict_prices.argtypes = [P, i32, P, P, P]
+            L.la_predict_prices_ex.argtypes = [P, i32, P, P, P, P]
+            L.la_solve_warm.argtypes = [P, i32, P, P, P, P, P]
+            L.la_dual_certificate.argtypes = [P, i32, P, P, P, P]
+            L.la_dual_certificate.restype = ctypes.c_int
+            for f in (L.la_features, L.la_predictor_forward, L.la_predictor_train_step,
+                      L.la_predict_prices, L.la_predict_prices_ex, L.la_solve_warm):
+                f.restype = ctypes.c_int
             L.la_status_string.argtypes = [ctypes.c_int]
             L.la_status_string.restype = ctypes.c_char_p
             L.la_release_workspace.argtypes = []
@@ -201,6 +222,55 @@ def la_solve_batched_ex(cost, offsets, ns, B, opt, stream, match_out, cost_out, 
                                      None if opt is None else ctypes.byref(opt), _stream(stream),
                                      _ptr(match_out), _ptr(cost_out), _ptr(status_out),
                                      None if stats_out is None else ctypes.byref(stats_out))
+
+
+def la_features(cost, n, stream, feats_out, inst_out) -> int:
+    return lib().la_features(_ptr(cost), int(n), _stream(stream), _ptr(feats_out), _ptr(inst_out))
+
+
+def la_predictor_forward(params, feats, seg, I, N, stream, y_out) -> int:
+    return lib().la_predictor_forward(_ptr(params), _ptr(feats), _ptr(seg), int(I), int(N),
+                                      _stream(stream), _ptr(y_out))
+
+
+def la_predictor_train_step(params, adam_m, adam_v, feats, targets, seg, I, N, step, lr,
+                            weight_decay, stream, grad_out, loss_out) -> int:
+    return lib().la_predictor_train_step(_ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(feats),
+                                         _ptr(targets), _ptr(seg), int(I), int(N), int(step),
+                                         float(lr), float(weight_decay), _stream(stream),
+                                         _ptr(grad_out), loss_out)
+
+
+def la_predict_prices(cost, n, weights, stream, prices_out) -> int:
+    return lib().la_predict_prices(_ptr(cost), int(n), _ptr(weights), _stream(stream), _ptr(prices_out))
+
+
+def la_predict_prices_ex(cost, n, weights, stream, prices_out, eps0_out) -> int:
+    return lib().la_predict_prices_ex(_ptr(cost), int(n), _ptr(weights), _stream(stream),
+                                      _ptr(prices_out), eps0_out)
+
+
+def la_solve_warm(cost, n, weights, stream, match_out, cost_out, stats_out) -> int:
+    return lib().la_solve_warm(_ptr(cost), int(n), _ptr(weights), _stream(stream), _ptr(match_out),
+                               _ptr(cost_out), None if stats_out is None else ctypes.byref(stats_out))
+
+
+def la_dual_certificate(cost, n, match, stream, u_out, v_out) -> int:
+    return lib().la_dual_certificate(_ptr(cost), int(n), _ptr(match), _stream(stream), _ptr(u_out),
+                                     _ptr(v_out))
+
+
+def dual_certificate(C, match, *, stream=None):
+    """Exact integer duals (u, v) (int64 CUDA tensors, cost units) proving
+    ``match`` optimal for the int32 CUDA matrix ``C``."""
+    import torch
+    n = C.shape[0]
+    u = torch.empty(max(1, n), dtype=torch.int64, device=C.device)
+    v = torch.empty(max(1, n), dtype=torch.int64, device=C.device)
+    rc = la_dual_certificate(C.contiguous(), n, match.contiguous(), stream, u, v)
+    if rc != LA_OK:
+        raise LaError(rc, "la_dual_certificate")
+    return u[:n], v[:n]
 
 
 def la_status_string(status: int) -> str:
@@ -276,7 +346,7 @@ class BatchSolution:
 
 
 def batch_options(block_threads: int = 0, max_n: int = 0, alpha=None, budget_factor: int = 0,
-                  no_graph: bool = False, profile: bool = False) -> la_batch_options:
+                  no_graph: bool = False, profile: bool = False, prices_out=None) -> la_batch_options:
     """Build la_batch_options; ``alpha`` is an int or a per-bucket list
     (bucket k holds 2^k <= n < 2^(k+1))."""
     o = la_batch_options()
@@ -289,6 +359,7 @@ def batch_options(block_threads: int = 0, max_n: int = 0, alpha=None, budget_fac
     o.budget_factor = budget_factor
     o.no_graph = int(bool(no_graph))
     o.profile = int(bool(profile))
+    o.prices_out = _ptr(prices_out)
     return o
 
 
@@ -313,3 +384,35 @@ def solve_batched(costs, offsets, ns, *, options: la_batch_options = None, strea
         raise LaError(rc, "la_solve_batched_ex")
     return BatchSolution(costs=out[:B], match=match[:total], status=status[:B],
                          stats=dict(st.as_dict(), rc=rc))
+
+
+def solve_warm(C, weights, *, stream=None, check: bool = True) -> Solution:
+    """Exact assignment warm-started from the learned price predictor
+    (``weights``: float32 CUDA tensor of LA_PRED_PARAMS entries)."""
+    import torch
+    if C.dim() != 2 or C.shape[0] != C.shape[1] or C.dtype != torch.int32 or not C.is_cuda:
+        raise ValueError("cost matrix must be a square int32 CUDA tensor")
+    C = C.contiguous()
+    n = C.shape[0]
+    match = torch.empty(n, dtype=torch.int32, device=C.device)
+    cost = torch.empty(1, dtype=torch.int64, device=C.device)
+    st = la_stats()
+    with torch.cuda.device(C.device):
+        rc = la_solve_warm(C, n, weights, stream, match, cost, st)
+    if rc != LA_OK and check:
+        raise LaError(rc, "la_solve_warm")
+    return Solution(cost=int(cost.item()) if rc == LA_OK else None, match=match,
+                    stats=dict(st.as_dict(), status=rc))
+
+
+def predict_prices(C, weights, *, stream=None):
+    """Predicted column prices (int64 CUDA tensor, paper sign, scaled units)
+    and the calibrated starting eps."""
+    import torch
+    n = C.shape[0]
+    prices = torch.empty(max(1, n), dtype=torch.int64, device=C.device)
+    eps0 = ctypes.c_int64(0)
+    rc = la_predict_prices_ex(C.contiguous(), n, weights, stream, prices, ctypes.byref(eps0))
+    if rc != LA_OK:
+        raise LaError(rc, "la_predict_prices_ex")
+    return prices[:n], int(eps0.value)

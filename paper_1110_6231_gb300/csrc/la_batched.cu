@@ -215,7 +215,7 @@ k_batch_solve(const int32_t *__restrict__ C, const long long *__restrict__ offse
               const int *__restrict__ ns, const int *__restrict__ order,
               const long long *__restrict__ moff, int B, int max_n, BatchParams P,
               int32_t *__restrict__ match_out, long long *__restrict__ cost_out,
-              int *__restrict__ inst_status, BatchCtrl *ctrl) {
+              int *__restrict__ inst_status, BatchCtrl *ctrl, long long *__restrict__ prices_out) {
     extern __shared__ unsigned long long skey[];
     __shared__ int s_k, s_next_row, s_cmin, s_cmax, s_status;
     __shared__ unsigned long long s_qmin, s_scans, s_cost;
@@ -330,6 +330,7 @@ k_batch_solve(const int32_t *__restrict__ C, const long long *__restrict__ offse
                         continue;
                     }
                     if (Mi) Mi[mm] = y;
+                    if (prices_out) prices_out[moff[i] + y] = -(long long)key_q(skey[y]);
                     sum += Ci[(size_t)mm * n + y];
                 }
                 for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -360,7 +361,7 @@ k_batch_solve(const int32_t *__restrict__ C, const long long *__restrict__ offse
 // ---------------------------------------------------------------- host side
 
 struct GraphKey {
-    const void *cost, *offsets, *ns, *match, *costout, *status;
+    const void *cost, *offsets, *ns, *match, *costout, *status, *prices;
     int B, block, max_n;
     cudaStream_t stream;
     BatchParams P;
@@ -425,10 +426,11 @@ la_status ensure_bws(BatchWorkspace &w, int64_t B, int max_n) {
 template <int BLOCK>
 cudaError_t launch_solve(cudaStream_t s, int grid, size_t smem, const int32_t *cost, const int64_t *offsets,
                          const int32_t *ns, const BatchWorkspace &w, int B, int max_n, const BatchParams &P,
-                         int32_t *match_out, int64_t *cost_out, int *status) {
+                         int32_t *match_out, int64_t *cost_out, int *status, int64_t *prices) {
     k_batch_solve<BLOCK><<<grid, BLOCK, smem, s>>>(cost, reinterpret_cast<const long long *>(offsets), ns,
                                                    w.order, w.moff, B, max_n, P, match_out,
-                                                   reinterpret_cast<long long *>(cost_out), status, w.ctrl);
+                                                   reinterpret_cast<long long *>(cost_out), status, w.ctrl,
+                                                   reinterpret_cast<long long *>(prices));
     return cudaGetLastError();
 }
 
@@ -450,16 +452,16 @@ int solve_grid(int num_sms, size_t smem) {
 
 cudaError_t enqueue(cudaStream_t s, int block, int grid, size_t smem, const int32_t *cost,
                     const int64_t *offsets, const int32_t *ns, BatchWorkspace &w, int B, int max_n,
-                    const BatchParams &P, int32_t *match_out, int64_t *cost_out, int *status) {
+                    const BatchParams &P, int32_t *match_out, int64_t *cost_out, int *status, int64_t *prices) {
     cudaError_t e = cudaMemsetAsync(w.ctrl, 0, sizeof(BatchCtrl), s);
     if (e != cudaSuccess) return e;
     k_batch_prep<<<1, kPrepThreads, 0, s>>>(ns, B, max_n, w.moff, w.order, w.hist, w.ctrl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     switch (block) {
-    case 64: return launch_solve<64>(s, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status);
-    case 128: return launch_solve<128>(s, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status);
-    case 256: return launch_solve<256>(s, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status);
-    default: return launch_solve<512>(s, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status);
+    case 64: return launch_solve<64>(s, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status, prices);
+    case 128: return launch_solve<128>(s, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status, prices);
+    case 256: return launch_solve<256>(s, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status, prices);
+    default: return launch_solve<512>(s, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status, prices);
     }
 }
 
@@ -476,6 +478,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
     const int block = (opt && opt->block_threads) ? opt->block_threads : 128;
     const int max_n = (opt && opt->max_n) ? opt->max_n : LA_BATCH_MAX_N;
     const bool graph = !(opt && opt->no_graph);
+    int64_t *prices = opt ? opt->prices_out : nullptr;
     if (block != 64 && block != 128 && block != 256 && block != 512) return LA_ERR_INVALID;
     if (max_n < 1 || max_n > LA_BATCH_MAX_N) return LA_ERR_INVALID;
     BatchParams P;
@@ -521,6 +524,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
         key.match = match_out;
         key.costout = cost_out;
         key.status = status;
+        key.prices = prices;
         key.B = B;
         key.block = block;
         key.max_n = max_n;
@@ -534,7 +538,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
             cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (ce == cudaSuccess) {
                 const cudaError_t le = enqueue(cs, block, grid, smem, cost, offsets, ns, w, B, max_n, P,
-                                               match_out, cost_out, status);
+                                               match_out, cost_out, status, prices);
                 ce = cudaStreamEndCapture(cs, &g);
                 if (le != cudaSuccess) ce = le;
             }
@@ -551,7 +555,8 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
         LA_BCK(cudaGraphLaunch(w.exec, s));
         launched_graph = true;
     } else {
-        LA_BCK(enqueue(s, block, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status));
+        LA_BCK(enqueue(s, block, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status,
+                       prices));
     }
     if (profile) LA_BCK(cudaEventRecord(e1, s));
     LA_BCK(cudaMemcpyAsync(w.h_ctrl, w.ctrl, sizeof(BatchCtrl), cudaMemcpyDeviceToHost, s));

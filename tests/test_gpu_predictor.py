@@ -1,0 +1,172 @@
+"""GPU parity of the learned price predictor against its CPU oracle, and the
+exactness of warm-started solves.
+
+Features are compared in FP32 tolerance. The forward pass and the
+gradients are compared with the oracle evaluated with every matrix
+product's operands rounded to BF16, which is what the tensor cores see; what
+remains is FP32 versus FP64 accumulation, so the bound is 5e-3 of a block's
+norm. A second check against the unrounded FP64 oracle bounds the total
+effect of BF16 operands: a few roundings of relative size 2^-8 along the
+backward chain, allowed 6e-2 of a block's norm.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import set_encoder as se
+from paper_1110_6231_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "paper_1110_6231_gb300", "weights", "set_encoder_geometric.f32")
+
+
+@pytest.fixture(scope="module")
+def la():
+    import torch
+    from paper_1110_6231_gb300 import build
+    build.build()
+    import paper_1110_6231_gb300 as la
+    assert torch.cuda.is_available()
+    return la
+
+
+def _dev(a, dtype):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a).astype(dtype)).cuda()
+
+
+@pytest.mark.parametrize("kind,n", [("uniform", 1), ("uniform", 2), ("uniform", 5), ("geometric", 33),
+                                    ("uniform", 257), ("geometric", 1000)])
+def test_features_match_oracle(la, kind, n):
+    import torch
+    C = synth.uniform_costs(n, 0, 5000, n) if kind == "uniform" else synth.geometric_costs(n, n)
+    f = torch.empty((n, 16), dtype=torch.float32, device="cuda")
+    inst = torch.empty(2, dtype=torch.float32, device="cuda")
+    assert la.la_features(_dev(C, np.int32), n, None, f, inst) == la.LA_OK
+    X, T = se.features(C)
+    assert float(inst[0]) == pytest.approx(T, rel=1e-6)
+    np.testing.assert_allclose(f.cpu().numpy(), X, rtol=1e-4, atol=2e-5)
+
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    P = se.init_params(seed)
+    P[se.OFF_B1:se.OFF_W2] += rng.normal(0, 0.1, se.H)
+    P[se.OFF_B2:se.OFF_W3] += rng.normal(0, 0.1, se.H)
+    P[se.OFF_B3] = 0.3
+    return P
+
+
+def _inputs(seed, sizes):
+    rng = np.random.default_rng(seed)
+    seg = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    N = int(seg[-1])
+    X = np.zeros((N, 16))
+    X[:, :8] = rng.normal(0, 1, (N, 8))
+    t = rng.normal(0, 1, N)
+    return X, t, seg
+
+
+def test_forward_matches_oracle(la):
+    import torch
+    P = _params(1)
+    X, t, seg = _inputs(2, [5, 40, 100, 1])
+    N = X.shape[0]
+    y = torch.empty(N, dtype=torch.float32, device="cuda")
+    rc = la.la_predictor_forward(_dev(P, np.float32), _dev(X, np.float32), _dev(seg, np.int32),
+                                 len(seg) - 1, N, None, y)
+    assert rc == la.LA_OK
+    ref = se.forward(P.astype(np.float32).astype(np.float64), X, seg, quant=True)
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(y.cpu().numpy(), ref, atol=5e-3 * scale, rtol=0)
+
+
+def test_gradients_match_oracle(la):
+    import torch
+    P = _params(3)
+    X, t, seg = _inputs(4, [17, 64, 130])
+    N = X.shape[0]
+    g = torch.zeros(la.LA_PRED_PARAMS, dtype=torch.float32, device="cuda")
+    loss = ctypes.c_float(0)
+    Pd = _dev(P, np.float32)
+    rc = la.la_predictor_train_step(Pd, None, None, _dev(X, np.float32), _dev(t, np.float32),
+                                    _dev(seg, np.int32), len(seg) - 1, N, 1, 0.0, 0.0, None, g,
+                                    ctypes.byref(loss))
+    assert rc == la.LA_OK
+    P64 = P.astype(np.float32).astype(np.float64)
+    Lq, gq = se.loss_grad(P64, X, t, seg, quant=True)
+    L, gref = se.loss_grad(P64, X, t, seg)
+    assert loss.value == pytest.approx(Lq, rel=5e-3)
+    assert loss.value == pytest.approx(L, rel=3e-2)
+    g = g.cpu().numpy().astype(np.float64)
+    blocks = {"W1": (se.OFF_W1, se.OFF_B1), "b1": (se.OFF_B1, se.OFF_W2), "W2": (se.OFF_W2, se.OFF_B2),
+              "b2": (se.OFF_B2, se.OFF_W3), "W3": (se.OFF_W3, se.OFF_B3)}
+    for name, (a, b) in blocks.items():
+        ga = g[a:b]
+        for ref, bound in ((gq[a:b], 5e-3), (gref[a:b], 6e-2)):
+            rel = np.linalg.norm(ga - ref) / max(np.linalg.norm(ref), 1e-12)
+            assert rel < bound, (name, bound, rel)
+    assert np.all(g[:se.HEADER] == 0)
+    # Pd unchanged when lr = 0
+    np.testing.assert_array_equal(Pd.cpu().numpy(), P.astype(np.float32))
+
+
+def test_training_fits_a_simple_target(la):
+    import torch
+    X, _, seg = _inputs(5, [50] * 16)
+    t = X[:, 0] - 0.5 * X[:, 2] + 0.25 * X[:, 1] * X[:, 3]
+    from paper_1110_6231_gb300 import learn
+    P = torch.from_numpy(learn.init_params(0)).cuda()
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    Xd, td, sd = _dev(X, np.float32), _dev(t, np.float32), _dev(seg, np.int32)
+    loss = ctypes.c_float(0)
+    first = None
+    for step in range(1, 301):
+        rc = la.la_predictor_train_step(P, m, v, Xd, td, sd, len(seg) - 1, X.shape[0], step, 3e-3, 0.0,
+                                        None, None, ctypes.byref(loss))
+        assert rc == la.LA_OK
+        first = loss.value if first is None else first
+    assert loss.value < 0.1 * first
+
+
+@pytest.mark.parametrize("kind,n", [("geometric", 100), ("uniform", 300), ("geometric", 1000)])
+def test_warm_solve_is_exact_with_any_weights(la, kind, n):
+    import torch
+    P = _dev(se.init_params(7, eps_factor=0.5), np.float32)
+    C = synth.geometric_costs(n, 11) if kind == "geometric" else synth.uniform_costs(n, 0, 10**5, 11)
+    sol = la.solve_warm(_dev(C, np.int32), P)
+    assert sol.cost == oracle.hungarian(C)[0]
+    assert oracle.check_matching(C, sol.match.cpu().numpy(), sol.cost) == 0
+    prices, eps0 = la.predict_prices(_dev(C, np.int32), P)
+    assert int(prices.max()) == 0 and eps0 >= 1
+    bad = P.clone()
+    bad[0] = 1.0
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    assert la.la_predict_prices(_dev(C, np.int32), n, bad, None, out) == la.LA_ERR_INVALID
+
+
+@pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="trained weights not present")
+def test_trained_predictor_gains_over_cold_start(la):
+    """On fresh geometric instances (n = 1024, seeds never used in training),
+    the trained warm start returns the same exact optimum with far fewer row
+    scans than the cold start."""
+    import torch
+    P = torch.from_numpy(np.fromfile(WEIGHTS, dtype=np.float32)).cuda()
+    warm_scans = cold_scans = 0
+    for s in range(8):
+        C = synth.geometric_costs(1024, 2_000_000 + s)
+        Cd = _dev(C, np.int32)
+        cold = la.solve(Cd)
+        warm = la.solve_warm(Cd, P)
+        assert warm.cost == cold.cost
+        assert oracle.check_matching(C, warm.match.cpu().numpy(), warm.cost) == 0
+        cold_scans += cold.stats["scans"]
+        warm_scans += warm.stats["scans"]
+    assert warm_scans < 0.6 * cold_scans, (warm_scans, cold_scans)

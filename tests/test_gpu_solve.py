@@ -237,3 +237,41 @@ def test_tail_kernel_thresholds(la, tail):
             assert st["tail_phases"] == 0 and st["tail_scans"] == 0
         else:
             assert st["tail_phases"] >= 1
+
+
+@pytest.mark.parametrize("kind,n", [("uniform", 2), ("uniform", 257), ("geometric", 500), ("ties", 300)])
+def test_dual_certificate_proves_gpu_optimum(la, kind, n):
+    """The library's own integer duals certify its matching by LP duality,
+    checked by the oracle's certificate checker (no solver involved)."""
+    import torch
+    if kind == "uniform":
+        C = synth.uniform_costs(n, -1000, 10**6, 3)
+    elif kind == "geometric":
+        C = synth.geometric_costs(n, 3)
+    else:
+        C = np.random.default_rng(3).integers(0, 3, size=(n, n)).astype(np.int32)
+    Cd = torch.from_numpy(C).cuda()
+    sol = la.solve(Cd)
+    u, v = la.dual_certificate(Cd, sol.match)
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    m = sol.match.cpu().numpy()
+    assert oracle.check_duals(C, m, u, v) == 0
+    assert int(u.sum() + v.sum()) == sol.cost == oracle.hungarian(C)[0]
+    assert v.max() == 0
+
+
+def test_dual_certificate_rejects_bad_matchings(la):
+    import torch
+    C = synth.uniform_costs(40, 0, 1000, 9)
+    Cd = torch.from_numpy(C).cuda()
+    sol = la.solve(Cd)
+    m = sol.match.clone()
+    m[[0, 1]] = m[[1, 0]]
+    if oracle.check_matching(C, m.cpu().numpy(), sol.cost) != 0:      # strictly worse
+        with pytest.raises(la.LaError) as e:
+            la.dual_certificate(Cd, m)
+        assert e.value.status == la.LA_ERR_INTERNAL
+    m[0] = m[1]
+    with pytest.raises(la.LaError) as e:
+        la.dual_certificate(Cd, m)
+    assert e.value.status == la.LA_ERR_INVALID
