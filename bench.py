@@ -183,6 +183,101 @@ def run_reference(args):
     return 0
 
 
+def bench_batched(args, la, synth, dev, stream):
+    """10,000 instances, n log-uniform in [16, 1024] (half uniform [0, 10^4],
+    half geometric): one persistent launch replayed from a CUDA graph, versus
+    one la_solve call per instance on a sample."""
+    import numpy as np
+    import torch
+    t0 = time.perf_counter()
+    flat, off, ns = synth.batch(args.batch, 0)
+    gen_s = time.perf_counter() - t0
+    dc, do, dn = (torch.from_numpy(a).to(dev) for a in (flat, off, ns))
+    opt = la.batch_options(max_n=1024, profile=True)
+    la.solve_batched(dc, do, dn, options=opt)           # capture the graph
+    times, stats = [], None
+    for _ in range(3):
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        sol = la.solve_batched(dc, do, dn, options=opt)
+        torch.cuda.synchronize(dev)
+        times.append(time.perf_counter() - t1)
+        stats = sol.stats
+    best = min(times)
+    idx = list(range(0, args.batch, max(1, args.batch // 100)))
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    for i in idx:
+        n = int(ns[i])
+        la.solve(dc[int(off[i]):int(off[i]) + n * n].view(n, n))
+    torch.cuda.synchronize(dev)
+    per = len(idx) / (time.perf_counter() - t2)
+    return {"workload": f"{args.batch} instances, n log-uniform [16,1024], half uniform [0,1e4], half geometric",
+            "solves_per_s": args.batch / best, "ms": 1e3 * best, "device_ms": stats["device_ms"],
+            "graph": stats["graph"], "scan_GBps": stats["scan_bytes"] / (stats["device_ms"] * 1e-3) / 1e9,
+            "scans": stats["scans"], "cost_bytes": int(flat.size) * 4,
+            "per_instance_la_solve_per_s": per, "per_instance_sample": len(idx),
+            "speedup_vs_per_instance": (args.batch / best) / per, "generate_s": gen_s}
+
+
+def bench_warm(args, la, synth, dev):
+    """Learned warm start versus plain cold start on fresh geometric
+    instances (seeds never used in training), identical exact costs."""
+    import numpy as np
+    import torch
+    from paper_1110_6231_gb300 import learn
+    if not os.path.exists(learn.DEFAULT_WEIGHTS):
+        return {"unavailable": "no trained weights"}
+    P = torch.from_numpy(np.fromfile(learn.DEFAULT_WEIGHTS, dtype=np.float32)).to(dev)
+    out = {}
+    for n, cnt in ((1024, args.warm_n1024), (8192, args.warm_n8192)):
+        tc = tw = 0.0
+        sc = sw = 0
+        for s in range(cnt):
+            C = torch.from_numpy(synth.geometric_costs(n, 2_000_000 + s)).to(dev)
+            if s == 0:
+                la.solve(C)
+                la.solve_warm(C, P)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            cold = la.solve(C)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            warm = la.solve_warm(C, P)
+            torch.cuda.synchronize(dev)
+            t2 = time.perf_counter()
+            if warm.cost != cold.cost:
+                raise RuntimeError("warm and cold costs differ")
+            tc += t1 - t0
+            tw += t2 - t1
+            sc += cold.stats["scans"]
+            sw += warm.stats["scans"]
+        out[f"n{n}"] = {"instances": cnt, "cold_ms": 1e3 * tc / cnt, "warm_ms": 1e3 * tw / cnt,
+                        "speedup": tc / tw, "cold_scans": sc / cnt, "warm_scans": sw / cnt,
+                        "identical_cost": True, "warm_includes": "features + set encoder + solve"}
+    return out
+
+
+def bench_single(la, synth, dev, name, reps=2):
+    import torch
+    C = torch.from_numpy(synth.instance(name, 0)).to(dev)
+    la.solve(C)
+    best = None
+    st = None
+    for _ in range(reps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sol = la.solve(C, profile=True)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        if best is None or dt < best:
+            best, st = dt, sol.stats
+    n = C.shape[0]
+    return {"ms": 1e3 * best, "scans": st["scans"], "full_scans": st["full_scans"],
+            "arc_scan_GBps": 4.0 * n * st["full_scans"] / (st["refine_ms"] * 1e-3) / 1e9,
+            "phases": st["phases"], "max_chain": st["max_chain"]}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -245,12 +340,19 @@ def run_gpu(args):
     total = args.steps * world
     value = total / elapsed
 
-    # roofline of the dominant kernel (refine): algorithmic bytes / event time
+    # roofline of the dominant kernel (refine): algorithmic bytes / event time.
+    # A full row scan must read the 4n-byte cost row; a candidate-list scan
+    # reads the row's 64 list entries (column + scaled cost).
     scans = sum(s["scans"] for s in stats)
+    full = sum(s["full_scans"] for s in stats)
+    listed = sum(s["list_scans"] for s in stats)
+    wide0 = stats[0]["wide"] if stats else 0
+    list_bytes = 64 * (4 + (8 if wide0 else 4))
     refine_ms = sum(s["refine_ms"] for s in stats)
     refine_launches = sum(s["refine_launches"] for s in stats)
     launches = sum(s["launches"] for s in stats)
-    achieved = 4.0 * n * scans / (refine_ms * 1e-3) / 1e9
+    alg_bytes = 4.0 * n * full + list_bytes * listed
+    achieved = alg_bytes / (refine_ms * 1e-3) / 1e9
     peak, peak_src = peaks()
     traffic = recorded_traffic(WORKLOAD)
 
@@ -277,6 +379,12 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_t = float(t.item())
 
+    extra = {}
+    if not args.no_extra:
+        extra["batched"] = bench_batched(args, la, synth, dev, stream)
+        extra["warm_start"] = bench_warm(args, la, synth, dev)
+        extra["geometric_n8192"] = bench_single(la, synth, dev, "geometric-n8192", reps=2)
+
     line = None
     if rank == 0:
         cpu = None
@@ -296,9 +404,11 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "kernel": "k_refine", "achieved": achieved, "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic,
-                         "algorithmic_bytes_per_launch": 4.0 * n * scans / max(1, refine_launches),
+                         "algorithmic_bytes_per_launch": alg_bytes / max(1, refine_launches),
                          "avg_launch_ms": refine_ms / max(1, refine_launches)},
             "arc_scans_per_solve": scans / max(1, len(stats)),
+            "full_row_scans_per_solve": full / max(1, len(stats)),
+            "list_scans_per_solve": listed / max(1, len(stats)),
             "phases": stats[0]["phases"] if stats else None,
             "max_chain": max(s["max_chain"] for s in stats) if stats else None,
             "e2e": {"value": e2e_steps * world / e2e_t, "unit": UNIT,
@@ -306,6 +416,7 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "extra": extra,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -323,6 +434,10 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched / warm-start / n=8192 lines")
+    ap.add_argument("--batch", type=int, default=10_000)
+    ap.add_argument("--warm-n1024", type=int, default=100)
+    ap.add_argument("--warm-n8192", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
