@@ -231,6 +231,8 @@ def bench_warm(args, la, synth, dev):
     P = torch.from_numpy(np.fromfile(learn.DEFAULT_WEIGHTS, dtype=np.float32)).to(dev)
     out = {}
     for n, cnt in ((1024, args.warm_n1024), (8192, args.warm_n8192)):
+        if cnt <= 0:
+            continue
         tc = tw = 0.0
         sc = sw = 0
         for s in range(cnt):
