@@ -57,6 +57,8 @@ struct Ctrl {
     int handoff;                     // 1: the refine handed its rows to the tail kernel
     int tail_count;                  // rows the refine handed over
     int tail_phases;                 // phases that used the tail kernel
+    unsigned long long ph_full;      // this phase's full scans so far (refine kernel)
+    unsigned long long ph_hits;      // this phase's candidate-list scans so far
 };
 
 // --- loads ---------------------------------------------------------------

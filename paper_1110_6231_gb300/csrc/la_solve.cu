@@ -151,6 +151,8 @@ __global__ void k_reset(unsigned long long *__restrict__ key, void *__restrict__
         ctrl->free_rows = n;
         ctrl->handoff = 0;
         ctrl->tail_count = 0;
+        ctrl->ph_full = 0;
+        ctrl->ph_hits = 0;
     }
 }
 
@@ -221,7 +223,7 @@ __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int 
         const int4 *r4 = reinterpret_cast<const int4 *>(crow);
         const int nv = n >> 2;
         cnt = lane < nv ? 4 * ((nv - lane + 31) >> 5) : 0;
-#pragma unroll 4
+#pragma unroll 8
         for (int j = lane; j < nv; j += 32) {
             const int4 c = ld_row4(r4 + j);
             const int y = j << 2;
@@ -258,11 +260,15 @@ __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int 
     return r;
 }
 
-// Short scan of row x over its candidate list (two entries per lane).
+// Short scan of row x over its candidate list (two entries per lane). The
+// list entries and the row's bound theta are loaded in the same round trip;
+// the prices are gathered only when a list exists (theta != 0).
 template <bool WIDE, class P>
-__device__ __forceinline__ auto list_scan(int row, const P &prices, int lane, const RowLists &L) {
+__device__ __forceinline__ auto list_scan(int row, int n, const P &prices, int lane, const RowLists &L,
+                                          unsigned long long &theta) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
     const size_t base = (size_t)row * 64 + 2 * lane;
+    theta = __ldcg(L.theta + row);
     const int2 yy = __ldcg(reinterpret_cast<const int2 *>(L.cols + base));
     V c0, c1;
     if (WIDE) {
@@ -275,14 +281,16 @@ __device__ __forceinline__ auto list_scan(int row, const P &prices, int lane, co
         c1 = cc.y;
     }
     const V inf = (V)~(V)0;
-    const V v0 = yy.x >= 0 ? c0 + prices.q(yy.x) : inf;
-    const V v1 = yy.y >= 0 ? c1 + prices.q(yy.y) : inf;
+    ScanResult<V> r{inf, inf, 0, INT_MAX};
+    if (theta == 0) return r;            // no list for this row yet (uniform across the warp)
+    const bool ok0 = yy.x >= 0 && yy.x < n, ok1 = yy.y >= 0 && yy.y < n;
+    const V v0 = ok0 ? c0 + prices.q(yy.x) : inf;
+    const V v1 = ok1 ? c1 + prices.q(yy.y) : inf;
     const bool first = (v0 < v1) || (v0 == v1 && (unsigned)yy.x < (unsigned)yy.y);
-    ScanResult<V> r;
     r.b1 = first ? v0 : v1;
     r.b2 = first ? v1 : v0;
     r.c1 = first ? c0 : c1;
-    r.w = first ? (yy.x < 0 ? INT_MAX : yy.x) : (yy.y < 0 ? INT_MAX : yy.y);
+    r.w = first ? (ok0 ? yy.x : INT_MAX) : (ok1 ? yy.y : INT_MAX);
     warp_merge(r);
     return r;
 }
@@ -298,9 +306,9 @@ __device__ __forceinline__ auto scan_for_bid(const int32_t *__restrict__ C, int 
     ScanResult<V> t;
     bool ok = false;
     if (L.cols) {
-        const unsigned long long th = __ldcg(L.theta + row);
+        unsigned long long th = 0;
+        t = list_scan<WIDE>(row, n, prices, lane, L, th);
         if (th != 0) {
-            t = list_scan<WIDE>(row, prices, lane, L);
             // The list's best is the row's best when it does not exceed
             // theta (every other column is >= theta). The second best is
             // then min(list second, theta) at least, and bidding with that
@@ -332,6 +340,7 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
     const unsigned long long R = ctrl->rebase_total;
     int row = -1;
     unsigned long long wins = 0, displaced = 0, total = 0, full = 0, hits = 0;
+    unsigned long long full_pub = 0, hits_pub = 0;   // already added to the phase counters
     unsigned pending = 0;
     for (;;) {
         if (row < 0) {
@@ -347,7 +356,13 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
                 s = atomicAdd(&ctrl->scans, (unsigned long long)kFlush);
                 st = *reinterpret_cast<volatile int *>(&ctrl->status);
                 ho = *reinterpret_cast<volatile int *>(&ctrl->handoff);
+                if (tail_T > 0) {
+                    atomicAdd(&ctrl->ph_full, full - full_pub);
+                    atomicAdd(&ctrl->ph_hits, hits - hits_pub);
+                }
             }
+            full_pub = full;
+            hits_pub = hits;
             s = __shfl_sync(0xffffffffu, s, 0);
             st = __shfl_sync(0xffffffffu, st, 0);
             ho = __shfl_sync(0xffffffffu, ho, 0);
@@ -393,8 +408,14 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
                 row = (int)m;
             } else {
                 row = -1;
-                if (tail_T > 0 && lane == 0 && atomicSub(&ctrl->free_rows, 1) - 1 <= tail_T)
-                    atomicExch(&ctrl->handoff, 1);
+                // Hand the last rows to the one-CTA tail kernel only while
+                // the candidate lists answer most scans (>= 3 of 4): its
+                // single SM is then spent on cheap list scans, not rescans.
+                if (tail_T > 0 && lane == 0 && atomicSub(&ctrl->free_rows, 1) - 1 <= tail_T) {
+                    const unsigned long long pf = *reinterpret_cast<volatile unsigned long long *>(&ctrl->ph_full);
+                    const unsigned long long ph = *reinterpret_cast<volatile unsigned long long *>(&ctrl->ph_hits);
+                    if (ph >= 3 * pf) atomicExch(&ctrl->handoff, 1);
+                }
             }
         }
         // else: a lower price got there first; rescan this row
