@@ -45,6 +45,28 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def rank_seeds(rank, count):
+    """Seeds of the instances a replica solves: disjoint across ranks."""
+    return [10_000 * rank + i for i in range(count)]
+
+
+def max_over_ranks(value, device=None):
+    """The slowest rank's time (every rank gets it); identity without a
+    process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(steps, world, elapsed):
+    """Whole-job solves per second: every rank's steps over the slowest rank's time."""
+    return steps * world / elapsed
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -296,7 +318,7 @@ def run_gpu(args):
     la.lib()
 
     n = synth.WORKLOADS[WORKLOAD]["n"]
-    host = [synth.instance(WORKLOAD, 10_000 * rank + i) for i in range(ROTATE)]
+    host = [synth.instance(WORKLOAD, s) for s in rank_seeds(rank, ROTATE)]
     dmats = [torch.from_numpy(h).to(dev) for h in host]
     stream = torch.cuda.current_stream(dev)
     match = torch.empty(n, dtype=torch.int32, device=dev)
@@ -333,14 +355,8 @@ def run_gpu(args):
         barrier()
         wall = time.perf_counter() - t0
     dev_ms = ev0.elapsed_time(ev1)
-    elapsed = max(wall, dev_ms / 1e3)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    total = args.steps * world
-    value = total / elapsed
+    elapsed = max_over_ranks(max(wall, dev_ms / 1e3), dev)
+    value = replica_throughput(args.steps, world, elapsed)
 
     # roofline of the dominant kernel (refine): algorithmic bytes / event time.
     # A full row scan must read the 4n-byte cost row; a candidate-list scan
@@ -374,12 +390,7 @@ def run_gpu(args):
     for i in range(e2e_steps):
         e2e_step(i)
     barrier()
-    e2e_t = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t = max_over_ranks(time.perf_counter() - t0, dev)
 
     extra = {}
     if not args.no_extra:
