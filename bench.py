@@ -215,7 +215,11 @@ def bench_batched(args, la, synth, dev, stream):
     flat, off, ns = synth.batch(args.batch, 0)
     gen_s = time.perf_counter() - t0
     dc, do, dn = (torch.from_numpy(a).to(dev) for a in (flat, off, ns))
-    opt = la.batch_options(max_n=1024, profile=True)
+    from paper_1110_6231_gb300 import tune
+    t_tune = time.perf_counter()
+    table = tune.autotune_batched(dc, do, dn, reps=1)   # CTA size and alpha per size bucket
+    t_tune = time.perf_counter() - t_tune
+    opt = tune.options_from_table(table, profile=True)
     la.solve_batched(dc, do, dn, options=opt)           # capture the graph
     times, stats = [], None
     for _ in range(3):
@@ -239,7 +243,9 @@ def bench_batched(args, la, synth, dev, stream):
             "graph": stats["graph"], "scan_GBps": stats["scan_bytes"] / (stats["device_ms"] * 1e-3) / 1e9,
             "scans": stats["scans"], "cost_bytes": int(flat.size) * 4,
             "per_instance_la_solve_per_s": per, "per_instance_sample": len(idx),
-            "speedup_vs_per_instance": (args.batch / best) / per, "generate_s": gen_s}
+            "speedup_vs_per_instance": (args.batch / best) / per, "generate_s": gen_s,
+            "autotuned": {"block_threads": table["block_threads"], "max_n": table["max_n"],
+                          "alpha_by_log2n": table["alpha"], "tune_s": t_tune}}
 
 
 def bench_warm(args, la, synth, dev):

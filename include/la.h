@@ -92,6 +92,19 @@ typedef struct {
        a one-CTA kernel that finishes the phase with the column keys in
        shared memory (n <= 16384). 0 selects 32; negative disables it. */
     int32_t tail_threshold;
+    /* Global price updates (Sect. 5.2, Algorithm 5.3) per phase, each run
+       when the phase is down to max(16, n/128) free rows after a stretch of
+       bidding. 0 or negative: none (the default; on the measured workloads
+       their sweeps cost about what they save). */
+    int32_t price_updates;
+    /* Intermediate phases (all but the last, eps = 1) stop once this many
+       rows or fewer are free; 0 selects max(1, min(8, n/512)), a negative
+       value runs every phase to a complete assignment (Algorithm 5.2 as
+       written). Only the last phase must end with an eps-optimal flow: the
+       next phase's initialisation makes any prices eps-optimal, so the
+       optimum is unchanged. Large values make the next phase pay for the
+       unresolved conflicts (small eps, long price wars); keep it small. */
+    int32_t phase_cutoff;
 } la_options;
 
 /* la_options.flags: scan every row in full on every bid instead of using
@@ -126,6 +139,9 @@ typedef struct {
                                 list (64 columns) without reading the row */
     int64_t tail_scans;      /* scans made by the one-CTA tail kernel */
     int32_t tail_phases;     /* phases that handed their last rows to it */
+    int64_t price_updates;   /* global price updates applied */
+    int64_t price_update_sweeps;  /* relaxation sweeps they took */
+    int64_t price_update_levels;  /* sum of their truncation levels */
 } la_stats;
 
 /*

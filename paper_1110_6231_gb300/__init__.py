@@ -45,6 +45,8 @@ class la_options(ctypes.Structure):
         ("block_threads", ctypes.c_int32),
         ("flags", ctypes.c_int32),
         ("tail_threshold", ctypes.c_int32),
+        ("price_updates", ctypes.c_int32),
+        ("phase_cutoff", ctypes.c_int32),
     ]
 
 
@@ -69,6 +71,9 @@ class la_stats(ctypes.Structure):
         ("list_scans", ctypes.c_int64),
         ("tail_scans", ctypes.c_int64),
         ("tail_phases", ctypes.c_int32),
+        ("price_updates", ctypes.c_int64),
+        ("price_update_sweeps", ctypes.c_int64),
+        ("price_update_levels", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -297,7 +302,8 @@ class Solution:
 
 def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bool = False,
           scan_budget: int = 0, profile: bool = False, block_threads: int = 0,
-          flags: int = 0, tail_threshold: int = 0, stream=None, check: bool = True) -> Solution:
+          flags: int = 0, tail_threshold: int = 0, price_updates: int = 0, phase_cutoff: int = 0,
+          stream=None, check: bool = True) -> Solution:
     """Exact minimum-cost assignment of a square int32 CUDA tensor ``C``.
 
     ``init_prices`` (int64 CUDA tensor, paper sign, units of (n+1) C) warm
@@ -328,6 +334,8 @@ def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bo
     opt.block_threads = block_threads
     opt.flags = flags
     opt.tail_threshold = tail_threshold
+    opt.price_updates = price_updates
+    opt.phase_cutoff = phase_cutoff
     st = la_stats()
     with torch.cuda.device(dev):
         rc = la_solve_ex(C, n, opt, stream, match, cost, st)

@@ -59,6 +59,18 @@ struct Ctrl {
     int tail_phases;                 // phases that used the tail kernel
     unsigned long long ph_full;      // this phase's full scans so far (refine kernel)
     unsigned long long ph_hits;      // this phase's candidate-list scans so far
+    // row queue: qmode 0 = rows 0..n-1 by index, 1 = rows qlist[qsel][0..qlen)
+    int qmode, qlen, qsel;
+    int pu_left;                     // price updates still allowed in this phase
+    unsigned long long pu_mark;      // scans at the phase start or the last update
+    unsigned long long pu_updates;   // price updates applied (all phases)
+    unsigned long long pu_iters;     // relaxation sweeps they took
+    unsigned long long pu_levels;    // sum of their truncation levels
+    unsigned long long pu_qmax;      // largest q before an update
+    unsigned pu_bar[2];              // grid barrier: arrivals, generation
+    int pu_changed[3];               // a label fell in this sweep (triple buffered)
+    unsigned pu_last;                // largest label of a free row
+    int pu_abort;                    // sweeps did not settle: no update
 };
 
 // --- loads ---------------------------------------------------------------

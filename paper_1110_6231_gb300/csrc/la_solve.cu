@@ -47,6 +47,7 @@ constexpr unsigned long long kRangeLimit = 1ull << 40;  // C~ limit (LA_ERR_OVER
 constexpr int kTailMaxN = 16384;      // shared-memory keys of the tail kernel (128 KB)
 constexpr int kTailThreads = 1024;
 constexpr int kDefaultTailRows = 32;
+constexpr int kDefaultPuRounds = 0;   // global price updates per phase (off unless asked)
 
 // ---------------------------------------------------------------- kernels
 
@@ -132,7 +133,7 @@ __global__ void k_qmin(const unsigned long long *__restrict__ key, int n, Ctrl *
 // mirror and reset the row queue.
 template <bool WIDE>
 __global__ void k_reset(unsigned long long *__restrict__ key, void *__restrict__ qmv, int n,
-                        unsigned long long qlim, Ctrl *ctrl, int slot, int phase) {
+                        unsigned long long qlim, Ctrl *ctrl, int slot, int phase, int pu_rounds) {
     const unsigned long long qmin = ctrl->qmin[slot];
     bool bad = false;
     for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
@@ -153,6 +154,10 @@ __global__ void k_reset(unsigned long long *__restrict__ key, void *__restrict__
         ctrl->tail_count = 0;
         ctrl->ph_full = 0;
         ctrl->ph_hits = 0;
+        ctrl->qmode = 0;
+        ctrl->qlen = n;
+        ctrl->pu_left = pu_rounds;
+        ctrl->pu_mark = ctrl->scans;
     }
 }
 
@@ -334,10 +339,14 @@ __global__ void __launch_bounds__(256)
 k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
          unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
          Ctrl *__restrict__ ctrl, unsigned long long budget, RowLists L, int tail_T,
-         int *__restrict__ tail_rows) {
+         int *__restrict__ tail_rows, int pu_T, const int *__restrict__ qlist0,
+         const int *__restrict__ qlist1, int stop_free) {
     constexpr unsigned kFlush = 8;       // scans between budget / status / hand-off checks
     const int lane = threadIdx.x & 31;
     const unsigned long long R = ctrl->rebase_total;
+    const int qmode = ctrl->qmode, qlen = ctrl->qlen;
+    const int *qlist = ctrl->qsel ? qlist1 : qlist0;
+    const bool pu_on = pu_T > 0 && ctrl->pu_left > 0;
     int row = -1;
     unsigned long long wins = 0, displaced = 0, total = 0, full = 0, hits = 0;
     unsigned long long full_pub = 0, hits_pub = 0;   // already added to the phase counters
@@ -345,7 +354,10 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
     for (;;) {
         if (row < 0) {
             int r = 0;
-            if (lane == 0) r = atomicAdd(&ctrl->next_row, 1);
+            if (lane == 0) {
+                r = atomicAdd(&ctrl->next_row, 1);
+                if (qmode) r = r < qlen ? __ldcg(qlist + r) : n;
+            }
             row = __shfl_sync(0xffffffffu, r, 0);
             if (row >= n) break;
         }
@@ -360,6 +372,16 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
                     atomicAdd(&ctrl->ph_full, full - full_pub);
                     atomicAdd(&ctrl->ph_hits, hits - hits_pub);
                 }
+                // Few free rows and a stretch of bidding since the last update:
+                // stop here for a global price update (Alg. 5.3).
+                if (!ho && pu_on) {
+                    const int fr = *reinterpret_cast<volatile int *>(&ctrl->free_rows);
+                    const unsigned long long mark = *reinterpret_cast<volatile unsigned long long *>(&ctrl->pu_mark);
+                    if (fr <= pu_T && s >= mark + 8ull * (unsigned long long)pu_T + 256ull) {
+                        atomicCAS(&ctrl->handoff, 0, 2);
+                        ho = 2;
+                    }
+                }
             }
             full_pub = full;
             hits_pub = hits;
@@ -372,6 +394,7 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
                 if (lane == 0) set_status(ctrl, LA_ERR_ITER_LIMIT);
                 break;
             }
+            if (ho == 3) break;   // the phase was cut short: its last rows stay free
             if (ho) {   // few free rows left: the tail kernel takes this one
                 if (lane == 0) tail_rows[atomicAdd(&ctrl->tail_count, 1)] = row;
                 break;
@@ -411,10 +434,17 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
                 // Hand the last rows to the one-CTA tail kernel only while
                 // the candidate lists answer most scans (>= 3 of 4): its
                 // single SM is then spent on cheap list scans, not rescans.
-                if (tail_T > 0 && lane == 0 && atomicSub(&ctrl->free_rows, 1) - 1 <= tail_T) {
-                    const unsigned long long pf = *reinterpret_cast<volatile unsigned long long *>(&ctrl->ph_full);
-                    const unsigned long long ph = *reinterpret_cast<volatile unsigned long long *>(&ctrl->ph_hits);
-                    if (ph >= 3 * pf) atomicExch(&ctrl->handoff, 1);
+                if (lane == 0 && (tail_T > 0 || pu_on || stop_free > 0)) {
+                    const int fr = atomicSub(&ctrl->free_rows, 1) - 1;
+                    // An intermediate phase only prepares prices for the next
+                    // one, whose initialisation makes any prices eps-optimal
+                    // (Alg. 5.2): it may stop with a few rows still free.
+                    if (stop_free > 0 && fr <= stop_free) atomicCAS(&ctrl->handoff, 0, 3);
+                    if (!pu_on && tail_T > 0 && fr <= tail_T) {
+                        const unsigned long long pf = *reinterpret_cast<volatile unsigned long long *>(&ctrl->ph_full);
+                        const unsigned long long ph = *reinterpret_cast<volatile unsigned long long *>(&ctrl->ph_hits);
+                        if (ph >= 3 * pf) atomicCAS(&ctrl->handoff, 0, 1);
+                    }
                 }
             }
         }
@@ -440,18 +470,22 @@ template <bool WIDE, bool VEC>
 __global__ void __launch_bounds__(1024)
 k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
        unsigned long long qlim, unsigned long long *__restrict__ key, Ctrl *__restrict__ ctrl,
-       unsigned long long budget, RowLists L, const int *__restrict__ tail_rows) {
+       unsigned long long budget, RowLists L, const int *__restrict__ tail_rows,
+       const int *__restrict__ qlist0, const int *__restrict__ qlist1) {
     extern __shared__ unsigned long long skey[];
     __shared__ int s_next, s_tc, s_q0, s_count;
-    if (*reinterpret_cast<volatile int *>(&ctrl->handoff) == 0) return;
+    if (*reinterpret_cast<volatile int *>(&ctrl->handoff) != 1) return;
+    const int qmode = ctrl->qmode, qlen = ctrl->qlen;
+    const int *qlist = ctrl->qsel ? qlist1 : qlist0;
     constexpr unsigned kFlush = 8;
     const int tid = threadIdx.x, lane = tid & 31;
     for (int y = tid; y < n; y += blockDim.x) skey[y] = __ldcg(key + y);
     if (tid == 0) {
+        const int qend = qmode ? qlen : n;
         s_next = 0;
         s_tc = ctrl->tail_count;
-        s_q0 = min(ctrl->next_row, n);
-        s_count = s_tc + (n - s_q0);
+        s_q0 = min(ctrl->next_row, qend);
+        s_count = s_tc + (qend - s_q0);
     }
     __syncthreads();
     const unsigned long long R = ctrl->rebase_total;
@@ -465,7 +499,8 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
             if (lane == 0) k = atomicAdd(&s_next, 1);
             k = __shfl_sync(0xffffffffu, k, 0);
             if (k >= s_count) break;
-            row = k < s_tc ? __ldcg(tail_rows + k) : s_q0 + (k - s_tc);
+            if (k < s_tc) row = __ldcg(tail_rows + k);
+            else row = qmode ? __ldcg(qlist + s_q0 + (k - s_tc)) : s_q0 + (k - s_tc);
         }
         if (pending == kFlush) {
             unsigned long long s = 0;
@@ -526,6 +561,248 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
     }
 }
 
+// ------------------------------------------------------------------------
+// Global price update (Sect. 5.2, Algorithm 5.3), run when a phase is down
+// to a few free rows. It labels every node with its distance, in units of
+// eps, to the nearest free column (a node with negative excess) over the
+// residual graph, then lowers p(y) by eps * label (q grows), which keeps
+// every matched row eps-optimal and lines up admissible paths from the free
+// rows to the free columns, so their displacement chains become short.
+//
+// Arc lengths keep the version-2 eps-optimality (Sect. 5.1): with the row
+// price p(x) = eps - v(x, M(x)) of a matched row x (v = c~ - p), the arc
+// x -> y (y != M(x)) has length floor((v(x,y) - v(x,M(x)) + eps) / eps) and
+// the matched arc M(x) -> x has length 0, so the label of a matched column
+// is that of its row. Only the 64 arcs of x's candidate list are relaxed;
+// every other column has v >= theta (see RowLists), so the row's label is
+// also capped at floor((theta - v(x,M(x)) + eps) / eps), which keeps the
+// required inequality label(x) <= label(y) + length(x,y) on those arcs
+// (labels are >= 0). Labels are truncated at one more than the largest label
+// of a free row, as Algorithm 5.3 does for unscanned nodes (the whole last
+// bucket is included). Bellman-Ford sweeps run to a fixed point between grid
+// barriers of a cooperatively launched (co-resident) grid; if they do not
+// settle within the sweep limit, no price changes.
+constexpr unsigned kLabelInf = 0x7fffffffu;
+constexpr unsigned kMaxPuLevel = 2048;
+
+__device__ __forceinline__ unsigned long long global_timer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Barrier of a co-resident grid. A wait longer than 2 s sets
+// LA_ERR_INTERNAL and returns false instead of spinning on.
+__device__ bool pu_grid_sync(Ctrl *ctrl, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &ctrl->pu_bar[1];
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(&ctrl->pu_bar[0], 1u) + 1 == gridDim.x) {
+            atomicExch(&ctrl->pu_bar[0], 0u);
+            __threadfence();
+            atomicAdd(&ctrl->pu_bar[1], 1u);
+        } else {
+            const unsigned long long t0 = global_timer();
+            while (*gen == g) {
+                __nanosleep(64);
+                if (global_timer() - t0 > 2000000000ull) {
+                    atomicCAS(&ctrl->status, 0, (int)LA_ERR_INTERNAL);
+                    *s_ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(256)
+k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
+     unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
+     Ctrl *__restrict__ ctrl, RowLists L, const int *__restrict__ tail_rows, int *__restrict__ qlist0,
+     int *__restrict__ qlist1, unsigned *__restrict__ lab, unsigned long long *__restrict__ vref,
+     unsigned *__restrict__ cap, int *__restrict__ rowcol, int max_sweeps) {
+    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    __shared__ int s_ok;
+    if (*reinterpret_cast<volatile int *>(&ctrl->handoff) != 2) return;
+    if (threadIdx.x == 0) s_ok = 1;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int gtid = blockIdx.x * blockDim.x + tid, gthreads = gridDim.x * blockDim.x;
+    const int gwarp = gtid >> 5, nwarps = gthreads >> 5;
+    const unsigned long long R = ctrl->rebase_total;
+    // A0: clear the row -> column map and the sweep flags
+    for (int x = gtid; x < n; x += gthreads) rowcol[x] = -1;
+    if (gtid == 0) {
+        ctrl->pu_changed[0] = 0;
+        ctrl->pu_changed[1] = 0;
+        ctrl->pu_changed[2] = 0;
+    }
+    if (!pu_grid_sync(ctrl, &s_ok)) return;
+    // A1: matched columns, start labels, largest q
+    unsigned long long qmx = 0;
+    for (int y = gtid; y < n; y += gthreads) {
+        const unsigned long long k = key[y];
+        const uint32_t m = key_mate(k);
+        if (m != kNone && m < (uint32_t)n) rowcol[m] = y;
+        lab[y] = m == kNone ? 0u : kLabelInf;
+        qmx = max(qmx, key_q(k));
+    }
+    for (int o = 16; o; o >>= 1) qmx = max(qmx, __shfl_xor_sync(0xffffffffu, qmx, o));
+    if (lane == 0) atomicMax(&ctrl->pu_qmax, qmx);
+    if (!pu_grid_sync(ctrl, &s_ok)) return;
+    // A2: per row, v(x, M(x)) (or a lower bound of min_y v(x,y) for a free row)
+    // and the cap from theta
+    for (int x = gwarp; x < n; x += nwarps) {
+        const int w = rowcol[x];
+        const unsigned long long th = L.cols ? __ldcg(L.theta + x) : 0ull;
+        unsigned long long vr = 0;
+        if (w >= 0) {
+            vr = (unsigned long long)(uint32_t)(ld_row1(C + (size_t)x * n + w) - cmin) * np1 + key_q(__ldcg(key + w));
+        } else if (th != 0) {
+            // free row: min over the list and theta is <= min_y v(x,y)
+            const size_t base = (size_t)x * 64 + 2 * lane;
+            const int2 yy = __ldcg(reinterpret_cast<const int2 *>(L.cols + base));
+            const V *cc = static_cast<const V *>(L.costs) + base;
+            unsigned long long m = ~0ull;
+            if (yy.x >= 0 && yy.x < n) m = min(m, (unsigned long long)__ldcg(cc) + key_q(__ldcg(key + yy.x)));
+            if (yy.y >= 0 && yy.y < n) m = min(m, (unsigned long long)__ldcg(cc + 1) + key_q(__ldcg(key + yy.y)));
+            for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+            vr = th == ~0ull ? m : min(m, th - R - 1);
+        }
+        if (lane == 0) {
+            vref[x] = vr;
+            unsigned c;
+            if (th == 0) {
+                c = 0;                                   // no list: label 0 is always safe
+            } else if (th == ~0ull) {
+                c = kLabelInf;                           // every column is listed
+            } else {
+                const unsigned long long tf = th - R - 1, add = w >= 0 ? eps : 0;
+                const unsigned long long len = tf + add >= vr ? (tf + add - vr) / eps : 0;
+                c = (unsigned)min(len, (unsigned long long)kLabelInf);
+            }
+            cap[x] = c;
+            if (w >= 0 && c < kLabelInf) lab[w] = c;
+        }
+    }
+    if (!pu_grid_sync(ctrl, &s_ok)) return;
+    // B: Bellman-Ford sweeps over the matched rows until no label falls
+    int it = 0;
+    bool settled = false;
+    for (; it < max_sweeps; ++it) {
+        // Flag of this sweep; the next sweep's flag was last read after the
+        // barrier two sweeps ago, which every block has passed, so it can be
+        // cleared now.
+        const int par = it % 3;
+        bool changed = false;
+        for (int x = gwarp; x < n; x += nwarps) {
+            const int w = rowcol[x];
+            if (w < 0) continue;
+            const unsigned long long th = L.cols ? __ldcg(L.theta + x) : 0ull;
+            if (th == 0) continue;
+            const unsigned long long vr = vref[x];
+            const size_t base = (size_t)x * 64 + 2 * lane;
+            const int2 yy = __ldcg(reinterpret_cast<const int2 *>(L.cols + base));
+            const V *cc = static_cast<const V *>(L.costs) + base;
+            unsigned long long best = cap[x];
+            const int ys[2] = {yy.x, yy.y};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int y = ys[e];
+                if (y < 0 || y >= n || y == w) continue;
+                const unsigned long long vy = (unsigned long long)__ldcg(cc + e) + key_q(__ldcg(key + y));
+                const unsigned long long len = vy + eps >= vr ? (vy + eps - vr) / eps : 0;
+                best = min(best, (unsigned long long)__ldcg(lab + y) + len);
+            }
+            for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+            const unsigned b = (unsigned)min(best, (unsigned long long)kLabelInf);
+            if (lane == 0 && b < __ldcg(lab + w)) {
+                lab[w] = b;
+                changed = true;
+            }
+        }
+        if (changed) ctrl->pu_changed[par] = 1;
+        if (gtid == 0) ctrl->pu_changed[(it + 1) % 3] = 0;
+        if (!pu_grid_sync(ctrl, &s_ok)) return;
+        if (*reinterpret_cast<volatile int *>(&ctrl->pu_changed[par]) == 0) {
+            settled = true;
+            break;
+        }
+    }
+    // C: the free rows' labels set the truncation level
+    unsigned mx = 0;
+    for (int x = gwarp; x < n; x += nwarps) {
+        if (rowcol[x] >= 0) continue;
+        const unsigned long long th = L.cols ? __ldcg(L.theta + x) : 0ull;
+        unsigned long long best = cap[x];
+        if (th != 0) {
+            const unsigned long long vr = vref[x];
+            const size_t base = (size_t)x * 64 + 2 * lane;
+            const int2 yy = __ldcg(reinterpret_cast<const int2 *>(L.cols + base));
+            const V *cc = static_cast<const V *>(L.costs) + base;
+            const int ys[2] = {yy.x, yy.y};
+            for (int e = 0; e < 2; ++e) {
+                const int y = ys[e];
+                if (y < 0 || y >= n) continue;
+                const unsigned long long vy = (unsigned long long)__ldcg(cc + e) + key_q(__ldcg(key + y));
+                const unsigned long long len = vy >= vr ? (vy - vr) / eps : 0;
+                best = min(best, (unsigned long long)__ldcg(lab + y) + len);
+            }
+            for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+        }
+        mx = max(mx, (unsigned)min(best, (unsigned long long)kLabelInf));
+    }
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) atomicMax(&ctrl->pu_last, mx);
+    if (!pu_grid_sync(ctrl, &s_ok)) return;
+    // D: lower the prices, q += eps * min(label, K), and queue the free rows
+    const unsigned long long qmax = ctrl->pu_qmax;
+    unsigned long long K = settled ? (unsigned long long)ctrl->pu_last + 1 : 0;
+    K = min(K, (unsigned long long)kMaxPuLevel);   // keeps the price spread near its usual bound
+    K = min(K, qlim > qmax ? (qlim - qmax) / eps : 0ull);
+    for (int y = gtid; y < n && K > 0; y += gthreads) {
+        const unsigned long long lb = min((unsigned long long)lab[y], K);
+        if (lb == 0) continue;
+        const unsigned long long k = key[y];
+        const unsigned long long q = key_q(k) + eps * lb;
+        key[y] = pack_key(q, key_mate(k));
+        if (WIDE) static_cast<unsigned long long *>(qmv)[y] = q;
+        else static_cast<uint32_t *>(qmv)[y] = (uint32_t)q;
+    }
+    const int qmode = ctrl->qmode, qlen = ctrl->qlen, qsel = ctrl->qsel, tc = ctrl->tail_count;
+    const int *qold = qsel ? qlist1 : qlist0;
+    int *qnew = qsel ? qlist0 : qlist1;
+    const int qend = qmode ? qlen : n;
+    const int q0 = min(ctrl->next_row, qend);
+    const int total = tc + (qend - q0);
+    for (int k = gtid; k < total; k += gthreads)
+        qnew[k] = k < tc ? tail_rows[k] : (qmode ? qold[q0 + (k - tc)] : q0 + (k - tc));
+    if (!pu_grid_sync(ctrl, &s_ok)) return;
+    if (gtid == 0) {
+        ctrl->qsel = qsel ^ 1;
+        ctrl->qmode = 1;
+        ctrl->qlen = total;
+        ctrl->next_row = 0;
+        ctrl->tail_count = 0;
+        ctrl->pu_left -= 1;
+        ctrl->pu_mark = ctrl->scans;
+        ctrl->pu_iters += (unsigned long long)(it + 1);
+        if (K > 0) {
+            ctrl->pu_updates += 1;
+            ctrl->pu_levels += K;
+        }
+        ctrl->pu_qmax = 0;
+        ctrl->pu_last = 0;
+        __threadfence();
+        ctrl->handoff = 0;
+    }
+}
+
 // Read the matching out of the column keys; exact int64 cost.
 __global__ void k_finalize(const int32_t *__restrict__ C, int n, const unsigned long long *__restrict__ key,
                            int32_t *match, long long *cost, long long *prices, Ctrl *ctrl, int slot) {
@@ -556,7 +833,13 @@ struct Workspace {
     int *lcols = nullptr;                 // candidate lists
     unsigned long long *lcosts = nullptr;
     unsigned long long *ltheta = nullptr;
-    int *tail_rows = nullptr;             // rows handed to the tail kernel
+    int *tail_rows = nullptr;             // rows handed to the tail kernel / price update
+    int *qlist[2] = {nullptr, nullptr};   // row queues after a price update
+    unsigned *pu_lab = nullptr;           // price-update labels, caps, row data
+    unsigned *pu_cap = nullptr;
+    unsigned long long *pu_vref = nullptr;
+    int *pu_rowcol = nullptr;
+    int pu_grid = 0;
     Ctrl *ctrl = nullptr;
     Ctrl *h_ctrl = nullptr;
     int num_sms = 0;
@@ -574,6 +857,12 @@ void free_ws(Workspace &ws) {
     cudaFree(ws.lcosts);
     cudaFree(ws.ltheta);
     cudaFree(ws.tail_rows);
+    cudaFree(ws.qlist[0]);
+    cudaFree(ws.qlist[1]);
+    cudaFree(ws.pu_lab);
+    cudaFree(ws.pu_cap);
+    cudaFree(ws.pu_vref);
+    cudaFree(ws.pu_rowcol);
     cudaFree(ws.ctrl);
     cudaFreeHost(ws.h_ctrl);
     if (ws.events)
@@ -600,6 +889,16 @@ la_status ensure_ws(Workspace &ws, int64_t n) {
         cudaFree(ws.lcosts);
         cudaFree(ws.ltheta);
         cudaFree(ws.tail_rows);
+        cudaFree(ws.qlist[0]);
+        cudaFree(ws.qlist[1]);
+        cudaFree(ws.pu_lab);
+        cudaFree(ws.pu_cap);
+        cudaFree(ws.pu_vref);
+        cudaFree(ws.pu_rowcol);
+        ws.qlist[0] = ws.qlist[1] = nullptr;
+        ws.pu_lab = ws.pu_cap = nullptr;
+        ws.pu_vref = nullptr;
+        ws.pu_rowcol = nullptr;
         ws.key = nullptr;
         ws.qm = nullptr;
         ws.lcols = nullptr;
@@ -614,6 +913,12 @@ la_status ensure_ws(Workspace &ws, int64_t n) {
         if (cudaMalloc(&ws.lcosts, sizeof(unsigned long long) * 64 * cap) != cudaSuccess) return LA_ERR_NOMEM;
         if (cudaMalloc(&ws.ltheta, sizeof(unsigned long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
         if (cudaMalloc(&ws.tail_rows, sizeof(int) * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.qlist[0], sizeof(int) * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.qlist[1], sizeof(int) * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.pu_lab, sizeof(unsigned) * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.pu_cap, sizeof(unsigned) * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.pu_vref, sizeof(unsigned long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.pu_rowcol, sizeof(int) * cap) != cudaSuccess) return LA_ERR_NOMEM;
         ws.cap = cap;
     }
     return LA_OK;
@@ -633,13 +938,41 @@ int refine_grid(int num_sms, int block, int n) {
     return std::max(1, std::min(num_sms * occ[slot], need));
 }
 
+template <bool WIDE>
+cudaError_t launch_pu(cudaStream_t s, const int32_t *C, int n, int cmin, uint32_t np1, unsigned long long eps,
+                      unsigned long long qlim, Workspace &ws, const RowLists &L) {
+    if (!ws.pu_grid) {
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_pu<WIDE>, 256, 0);
+        ws.pu_grid = std::max(1, o) * ws.num_sms;
+    }
+    int max_sweeps = 256;
+    void *args[] = {(void *)&C, (void *)&n, (void *)&cmin, (void *)&np1, (void *)&eps, (void *)&qlim,
+                    (void *)&ws.key, (void *)&ws.qm, (void *)&ws.ctrl, (void *)&L, (void *)&ws.tail_rows,
+                    (void *)&ws.qlist[0], (void *)&ws.qlist[1], (void *)&ws.pu_lab, (void *)&ws.pu_vref,
+                    (void *)&ws.pu_cap, (void *)&ws.pu_rowcol, (void *)&max_sweeps};
+    return cudaLaunchCooperativeKernel((const void *)k_pu<WIDE>, dim3(ws.pu_grid), dim3(256), args, 0, s);
+}
+
 template <bool WIDE, bool VEC>
-void launch_refine(cudaStream_t s, int grid, int block, const int32_t *C, int n, int cmin, uint32_t np1,
-                   unsigned long long eps, unsigned long long qlim, Workspace &ws,
-                   unsigned long long budget, const RowLists &L, int tail_T) {
-    k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L,
-                                               tail_T, ws.tail_rows);
+cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C, int n, int cmin, uint32_t np1,
+                          unsigned long long eps, unsigned long long qlim, Workspace &ws,
+                          unsigned long long budget, const RowLists &L, int tail_T, int pu_T, int pu_rounds,
+                          int64_t &launches, int stop_free) {
+    for (int r = 0; r <= pu_rounds; ++r) {
+        if (r > 0) {
+            cudaError_t e = launch_pu<WIDE>(s, C, n, cmin, np1, eps, qlim, ws, L);
+            if (e != cudaSuccess) return e;
+            ++launches;
+        }
+        // the last refine of a phase never stops for a price update
+        k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L,
+                                                   tail_T, ws.tail_rows, r < pu_rounds ? pu_T : 0,
+                                                   ws.qlist[0], ws.qlist[1], stop_free);
+        ++launches;
+    }
     if (tail_T > 0) {
+        ++launches;
         static int smem_set = 0;
         const int smem = (int)(sizeof(unsigned long long) * n);
         if (smem > 48 * 1024 && smem > smem_set) {
@@ -647,8 +980,9 @@ void launch_refine(cudaStream_t s, int grid, int block, const int32_t *C, int n,
             smem_set = smem;
         }
         k_tail<WIDE, VEC><<<1, kTailThreads, smem, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.ctrl, budget, L,
-                                                         ws.tail_rows);
+                                                         ws.tail_rows, ws.qlist[0], ws.qlist[1]);
     }
+    return cudaGetLastError();
 }
 
 inline int small_grid(int n, int block, int num_sms) {
@@ -673,6 +1007,13 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     const bool lists = !(opt && (opt->flags & LA_FLAG_NO_CANDIDATE_LISTS));
     int tail_T = (opt && opt->tail_threshold) ? opt->tail_threshold : kDefaultTailRows;
     if (tail_T < 0 || n > kTailMaxN) tail_T = 0;
+    int pu_rounds = (opt && opt->price_updates) ? opt->price_updates : kDefaultPuRounds;
+    if (pu_rounds < 0 || !lists) pu_rounds = 0;
+    const int pu_T = std::max(16, n / 128);
+    // intermediate phases stop at this many free rows (the last phase never does)
+    // (default max(1, min(8, n / 512)); a negative value runs every phase to the end)
+    const int stop_free = (opt && opt->phase_cutoff) ? std::max(0, opt->phase_cutoff)
+                                                      : std::max(1, std::min(8, n / 512));
     if (alpha < 2 || eps0 < 0 || block < 32 || block > 256 || block % 32) return LA_ERR_INVALID;
     if (opt && opt->scan_budget < 0) return LA_ERR_INVALID;
 
@@ -771,18 +1112,17 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     for (; ph < (int)sched.size(); ++ph) {
         const int slot = ph & 1;
         k_qmin<<<sg, 256, 0, s>>>(ws.key, n, ws.ctrl, slot);
-        if (wide) k_reset<true><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph);
-        else k_reset<false><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph);
+        if (wide) k_reset<true><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds);
+        else k_reset<false><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds);
         launches += 2;
         if (profile) LA_CK(cudaEventRecord(ws.ev[2 * ph], s));
         if (wide) {
-            if (vec) launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T);
-            else launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T);
+            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, ph + 1 < (int)sched.size() ? stop_free : 0)));
+            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, ph + 1 < (int)sched.size() ? stop_free : 0)));
         } else {
-            if (vec) launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T);
-            else launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T);
+            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, ph + 1 < (int)sched.size() ? stop_free : 0)));
+            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, ph + 1 < (int)sched.size() ? stop_free : 0)));
         }
-        launches += tail_T > 0 ? 2 : 1;
         if (profile) LA_CK(cudaEventRecord(ws.ev[2 * ph + 1], s));
     }
     const int fslot = ph & 1;
@@ -804,7 +1144,10 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.wins = (int64_t)c1.wins;
     stats.displaced = (int64_t)c1.displaced;
     stats.launches = launches;
-    stats.refine_launches = (int64_t)sched.size();
+    stats.refine_launches = (int64_t)sched.size() * (1 + pu_rounds);
+    stats.price_updates = (int64_t)c1.pu_updates;
+    stats.price_update_sweeps = (int64_t)c1.pu_iters;
+    stats.price_update_levels = (int64_t)c1.pu_levels;
     stats.max_chain = (int64_t)c1.max_chain;
     stats.full_scans = (int64_t)c1.full_scans;
     stats.list_scans = (int64_t)c1.list_scans;
@@ -972,14 +1315,14 @@ la_status solve_noalloc_locked(const int32_t *cost, int32_t n, cudaStream_t s, i
     for (; ph < (int)sched.size(); ++ph) {
         const int slot = ph & 1;
         k_qmin<<<sg, 256, 0, s>>>(key, n, ctrl, slot);
-        if (wide) k_reset<true><<<sg, 256, 0, s>>>(key, qm, n, qlim, ctrl, slot, ph);
-        else k_reset<false><<<sg, 256, 0, s>>>(key, qm, n, qlim, ctrl, slot, ph);
+        if (wide) k_reset<true><<<sg, 256, 0, s>>>(key, qm, n, qlim, ctrl, slot, ph, 0);
+        else k_reset<false><<<sg, 256, 0, s>>>(key, qm, n, qlim, ctrl, slot, ph, 0);
         if (wide) {
-            if (vec) k_refine<true, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr);
-            else k_refine<true, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr);
+            if (vec) k_refine<true, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr, 0, nullptr, nullptr, 0);
+            else k_refine<true, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr, 0, nullptr, nullptr, 0);
         } else {
-            if (vec) k_refine<false, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr);
-            else k_refine<false, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr);
+            if (vec) k_refine<false, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr, 0, nullptr, nullptr, 0);
+            else k_refine<false, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr, 0, nullptr, nullptr, 0);
         }
     }
     LA_CK(cudaMemsetAsync(cost_out, 0, sizeof(int64_t), s));
