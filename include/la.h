@@ -98,9 +98,9 @@ typedef struct {
        their sweeps cost about what they save). */
     int32_t price_updates;
     /* Intermediate phases (all but the last, eps = 1) stop once this many
-       rows or fewer are free; 0 selects max(1, min(8, n/512)), a negative
-       value runs every phase to a complete assignment (Algorithm 5.2 as
-       written). Only the last phase must end with an eps-optimal flow: the
+       rows or fewer are free; 0 selects min(8, n/512) for n >= 2048 and no
+       cut below, a negative value runs every phase to a complete assignment
+       (Algorithm 5.2 as written). Only the last phase must end with an eps-optimal flow: the
        next phase's initialisation makes any prices eps-optimal, so the
        optimum is unchanged. Large values make the next phase pay for the
        unresolved conflicts (small eps, long price wars); keep it small. */

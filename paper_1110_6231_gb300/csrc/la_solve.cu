@@ -169,9 +169,8 @@ __global__ void k_reset(unsigned long long *__restrict__ key, void *__restrict__
 // value was >= theta then; prices only fall (Lemma 5.2), so its value stays
 // >= theta, up to the uniform per-phase shift R that is tracked in the
 // control block. A later scan of x may therefore gather only the 64 listed
-// prices: when the list's best is <= theta it is the row's best, and
-// min(list second best, theta) is a lower bound of the row's second best
-// (exact when the list's second best is <= theta).
+// prices: when the list's second best is <= theta, its best and second best
+// are those of the whole row, and the bid is the same as a full scan's.
 struct RowLists {
     int *cols;                  // [n][64] column, -1 = empty
     void *costs;                // [n][64] scaled cost, u32 or u64
@@ -314,18 +313,13 @@ __device__ __forceinline__ auto scan_for_bid(const int32_t *__restrict__ C, int 
         unsigned long long th = 0;
         t = list_scan<WIDE>(row, n, prices, lane, L, th);
         if (th != 0) {
-            // The list's best is the row's best when it does not exceed
-            // theta (every other column is >= theta). The second best is
-            // then min(list second, theta) at least, and bidding with that
-            // lower bound still leaves x eps-optimal at w: the price drop is
-            // at least eps and at most the full double push's.
-            if (th == ~0ull) {
-                ok = true;
-            } else if ((unsigned long long)t.b1 + R + 1 <= th) {
-                ok = true;
-                const unsigned long long tf = th - R - 1;     // theta in this phase's frame
-                if ((unsigned long long)t.b2 > tf) t.b2 = (V)tf;
-            }
+            // Exact when the list's second best does not exceed theta: every
+            // other column is >= theta, so the list holds the row's best and
+            // second best. (Bidding with theta as a lower bound of the
+            // second best would also keep x eps-optimal, but as a list runs
+            // out its price drops shrink towards eps, and at eps = 1 two
+            // such rows can trade a column for a very long time.)
+            ok = th == ~0ull || (unsigned long long)t.b2 + R + 1 <= th;
         }
     }
     full = !ok;
@@ -1011,9 +1005,8 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     if (pu_rounds < 0 || !lists) pu_rounds = 0;
     const int pu_T = std::max(16, n / 128);
     // intermediate phases stop at this many free rows (the last phase never does)
-    // (default max(1, min(8, n / 512)); a negative value runs every phase to the end)
-    const int stop_free = (opt && opt->phase_cutoff) ? std::max(0, opt->phase_cutoff)
-                                                      : std::max(1, std::min(8, n / 512));
+    // (off unless asked: see la_options.phase_cutoff)
+    const int stop_free = (opt && opt->phase_cutoff > 0) ? opt->phase_cutoff : 0;
     if (alpha < 2 || eps0 < 0 || block < 32 || block > 256 || block % 32) return LA_ERR_INVALID;
     if (opt && opt->scan_budget < 0) return LA_ERR_INVALID;
 
