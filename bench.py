@@ -366,12 +366,12 @@ def run_gpu(args):
 
     # roofline of the dominant kernel (refine): algorithmic bytes / event time.
     # A full row scan must read the 4n-byte cost row; a candidate-list scan
-    # reads the row's 64 list entries (column + scaled cost).
+    # reads the row's list entries (column + raw cost, 8 bytes each) and
+    # its bound theta.
     scans = sum(s["scans"] for s in stats)
     full = sum(s["full_scans"] for s in stats)
     listed = sum(s["list_scans"] for s in stats)
-    wide0 = stats[0]["wide"] if stats else 0
-    list_bytes = 64 * (4 + (8 if wide0 else 4))
+    list_bytes = stats[0]["list_entries"] * 8 + 8 if stats else 0
     refine_ms = sum(s["refine_ms"] for s in stats)
     refine_launches = sum(s["refine_launches"] for s in stats)
     launches = sum(s["launches"] for s in stats)

@@ -98,12 +98,12 @@ typedef struct {
        their sweeps cost about what they save). */
     int32_t price_updates;
     /* Intermediate phases (all but the last, eps = 1) stop once this many
-       rows or fewer are free; 0 selects min(8, n/512) for n >= 2048 and no
-       cut below, a negative value runs every phase to a complete assignment
-       (Algorithm 5.2 as written). Only the last phase must end with an eps-optimal flow: the
-       next phase's initialisation makes any prices eps-optimal, so the
-       optimum is unchanged. Large values make the next phase pay for the
-       unresolved conflicts (small eps, long price wars); keep it small. */
+       rows or fewer are free; 0 or a negative value runs every phase to a
+       complete assignment (Algorithm 5.2 as written; the default). Only the
+       last phase must end with an eps-optimal flow: the next phase's
+       initialisation makes any prices eps-optimal, so the optimum is
+       unchanged. Large values make the next phase pay for the unresolved
+       conflicts (small eps, long price wars); keep it small. */
     int32_t phase_cutoff;
 } la_options;
 
@@ -127,7 +127,8 @@ typedef struct {
     int32_t vector_loads;    /* 1 if the 128-bit row-load path ran */
     int64_t launches;        /* kernels this call launched */
     int64_t refine_launches; /* of which refine kernels */
-    double refine_ms;        /* summed refine kernel time (profile != 0) */
+    double refine_ms;        /* summed time of each phase's refine, price-update
+                                and tail kernels (profile != 0) */
     int64_t max_chain;       /* most row scans one warp made within a phase
                                 (the length of the longest displacement chain
                                 plus lost bids: the refine's critical path) */
@@ -136,12 +137,16 @@ typedef struct {
                                               (profile != 0) */
     int64_t full_scans;      /* scans that read the whole cost row */
     int64_t list_scans;      /* scans answered exactly by the row's candidate
-                                list (64 columns) without reading the row */
+                                list (128 columns) without reading the row */
     int64_t tail_scans;      /* scans made by the one-CTA tail kernel */
     int32_t tail_phases;     /* phases that handed their last rows to it */
     int64_t price_updates;   /* global price updates applied */
     int64_t price_update_sweeps;  /* relaxation sweeps they took */
     int64_t price_update_levels;  /* sum of their truncation levels */
+    int32_t list_entries;    /* candidate-list entries per row (0: lists off) */
+    double tail_ms;          /* of refine_ms, the time from the end of each
+                                phase's refine kernel to the end of its
+                                one-CTA tail kernel (profile != 0) */
 } la_stats;
 
 /*

@@ -74,6 +74,8 @@ class la_stats(ctypes.Structure):
         ("price_updates", ctypes.c_int64),
         ("price_update_sweeps", ctypes.c_int64),
         ("price_update_levels", ctypes.c_int64),
+        ("list_entries", ctypes.c_int32),
+        ("tail_ms", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:

@@ -188,6 +188,40 @@ __device__ __forceinline__ void lane2_push(Lane2<V> &t, V v, int y) {
     t.b1 = better ? v : t.b1;
 }
 
+// Lane-local K smallest of a stream of (value, column) pairs, kept sorted
+// (b[0] <= b[1] <= ...). Equal values keep the earlier column first, so
+// b[0] / w[0] is the lane's best in the same sense as Lane2. A
+// predicated insertion network: every element costs the same, whatever
+// the data, so the lanes of a warp never diverge.
+template <typename V, int K>
+struct LaneK {
+    V b[K];
+    int w[K];
+};
+
+template <typename V, int K>
+__device__ __forceinline__ void lanek_init(LaneK<V, K> &t) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        t.b[k] = (V)~(V)0;
+        t.w[k] = -1;
+    }
+}
+
+template <typename V, int K>
+__device__ __forceinline__ void lanek_push(LaneK<V, K> &t, V v, int y) {
+    bool lt[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) lt[k] = v < t.b[k];    // strict: keeps the earlier column first
+#pragma unroll
+    for (int k = K - 1; k > 0; --k) {
+        t.b[k] = lt[k - 1] ? t.b[k - 1] : (lt[k] ? v : t.b[k]);
+        t.w[k] = lt[k - 1] ? t.w[k - 1] : (lt[k] ? y : t.w[k]);
+    }
+    t.b[0] = lt[0] ? v : t.b[0];
+    t.w[0] = lt[0] ? y : t.w[0];
+}
+
 // Butterfly merge of the lanes' (b1, w, c1, b2): every lane ends with the
 // row's best value, its column (lowest index among equal minima), that
 // column's scaled cost and the second-best value.

@@ -162,20 +162,44 @@ __global__ void k_reset(unsigned long long *__restrict__ key, void *__restrict__
 }
 
 // Candidate lists (exact lazy scans). A full scan leaves, for row x, the
-// lane-local best and second-best columns of each of the 32 lanes (64
-// entries: column and scaled cost c~ - (n+1) min C) and the bound
-//   theta = min over lanes of the lane's second-best value.
-// Every column outside the list was beaten twice within its lane, so its
-// value was >= theta then; prices only fall (Lemma 5.2), so its value stays
-// >= theta, up to the uniform per-phase shift R that is tracked in the
-// control block. A later scan of x may therefore gather only the 64 listed
+// kListK lane-local best columns of each of the 32 lanes (kListLen entries:
+// column and raw cost C[x][y]) and the bound
+//   theta = min over lanes of the lane's kListK-th best value.
+// Every column outside the list was beaten kListK times within its lane, so
+// its value was >= theta then; prices only fall (Lemma 5.2), so its value
+// stays >= theta, up to the uniform per-phase shift R that is tracked in the
+// control block. A later scan of x may therefore gather only the listed
 // prices: when the list's second best is <= theta, its best and second best
 // are those of the whole row, and the bid is the same as a full scan's.
+// A longer list raises theta (the kListK-th order statistic of each lane
+// instead of the second), so it stays exact through more price changes.
+constexpr int kListK = 4;                 // entries per lane (int4 groups of columns and of costs)
+constexpr int kListLen = 32 * kListK;     // entries per row
+static_assert(kListK % 4 == 0, "a lane's list entries are loaded and stored as int4 groups");
+
 struct RowLists {
-    int *cols;                  // [n][64] column, -1 = empty
-    void *costs;                // [n][64] scaled cost, u32 or u64
+    int *cols;                  // [n][32][kListK] column, -1 = empty
+    int *costs;                 // [n][32][kListK] raw cost C[x][y]
     unsigned long long *theta;  // [n]: 0 = no list, ~0 = unbounded, else theta + R + 1
 };
+
+// One lane's list entries of row x (two 128-bit loads at L2).
+struct LaneList {
+    int y[kListK];
+    int c[kListK];
+};
+__device__ __forceinline__ LaneList load_lane_list(const RowLists &L, int row, int lane) {
+    const size_t base = (size_t)row * kListLen + kListK * lane;
+    LaneList e;
+#pragma unroll
+    for (int g = 0; g < kListK / 4; ++g) {
+        const int4 yy = __ldcg(reinterpret_cast<const int4 *>(L.cols + base) + g);
+        const int4 cc = __ldcg(reinterpret_cast<const int4 *>(L.costs + base) + g);
+        e.y[4 * g] = yy.x; e.y[4 * g + 1] = yy.y; e.y[4 * g + 2] = yy.z; e.y[4 * g + 3] = yy.w;
+        e.c[4 * g] = cc.x; e.c[4 * g + 1] = cc.y; e.c[4 * g + 2] = cc.z; e.c[4 * g + 3] = cc.w;
+    }
+    return e;
+}
 
 template <bool WIDE>
 __device__ __forceinline__ auto load_q(const void *qmv, int y) {
@@ -220,8 +244,8 @@ __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int 
                                           uint32_t np1, const P &prices, int lane,
                                           const RowLists &L, unsigned long long R) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
-    Lane2<V> t;
-    lane2_init(t);
+    LaneK<V, kListK> t;
+    lanek_init(t);
     int cnt;
     if (VEC) {
         const int4 *r4 = reinterpret_cast<const int4 *>(crow);
@@ -233,68 +257,75 @@ __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int 
             const int y = j << 2;
             V qa, qb, qc, qd;
             prices.q4(y, qa, qb, qc, qd);
-            lane2_push<V>(t, (V)(uint32_t)(c.x - cmin) * np1 + qa, y);
-            lane2_push<V>(t, (V)(uint32_t)(c.y - cmin) * np1 + qb, y + 1);
-            lane2_push<V>(t, (V)(uint32_t)(c.z - cmin) * np1 + qc, y + 2);
-            lane2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + qd, y + 3);
+            lanek_push<V, kListK>(t, (V)(uint32_t)(c.x - cmin) * np1 + qa, y);
+            lanek_push<V, kListK>(t, (V)(uint32_t)(c.y - cmin) * np1 + qb, y + 1);
+            lanek_push<V, kListK>(t, (V)(uint32_t)(c.z - cmin) * np1 + qc, y + 2);
+            lanek_push<V, kListK>(t, (V)(uint32_t)(c.w - cmin) * np1 + qd, y + 3);
         }
     } else {
         cnt = lane < n ? ((n - lane + 31) >> 5) : 0;
         for (int y = lane; y < n; y += 32) {
             const int c = ld_row1(crow + y);
-            lane2_push<V>(t, (V)(uint32_t)(c - cmin) * np1 + prices.q(y), y);
+            lanek_push<V, kListK>(t, (V)(uint32_t)(c - cmin) * np1 + prices.q(y), y);
         }
     }
-    // scaled costs of the lane's two columns (the row was just read: L2 hits)
-    const V c1 = t.w1 >= 0 ? (V)(uint32_t)(ld_row1(crow + t.w1) - cmin) * np1 : (V)0;
-    const V c2 = t.w2 >= 0 ? (V)(uint32_t)(ld_row1(crow + t.w2) - cmin) * np1 : (V)0;
+    // raw costs of the lane's listed columns (the row was just read: L2 hits)
+    int craw[kListK];
+#pragma unroll
+    for (int k = 0; k < kListK; ++k)
+        craw[k] = (t.w[k] >= 0 && (k == 0 || L.cols)) ? ld_row1(crow + t.w[k]) : 0;
+    const V c1 = t.w[0] >= 0 ? (V)(uint32_t)(craw[0] - cmin) * np1 : (V)0;
     if (L.cols) {
-        const size_t base = (size_t)row * 64 + 2 * lane;
-        *reinterpret_cast<int2 *>(L.cols + base) = make_int2(t.w1, t.w2);
-        V *cc = static_cast<V *>(L.costs) + base;
-        cc[0] = c1;
-        cc[1] = c2;
-        const V th = warp_min<V>(cnt > 2 ? t.b2 : (V)~(V)0);
+        const size_t base = (size_t)row * kListLen + kListK * lane;
+#pragma unroll
+        for (int g = 0; g < kListK / 4; ++g) {
+            reinterpret_cast<int4 *>(L.cols + base)[g] =
+                make_int4(t.w[4 * g], t.w[4 * g + 1], t.w[4 * g + 2], t.w[4 * g + 3]);
+            reinterpret_cast<int4 *>(L.costs + base)[g] =
+                make_int4(craw[4 * g], craw[4 * g + 1], craw[4 * g + 2], craw[4 * g + 3]);
+        }
+        const V th = warp_min<V>(cnt > kListK ? t.b[kListK - 1] : (V)~(V)0);
         if (lane == 0)
             L.theta[row] = th == (V)~(V)0 ? ~0ull : (unsigned long long)th + R + 1;
         __threadfence();   // the list is complete before this row can change hands
     }
-    ScanResult<V> r{t.b1, t.b2, c1, t.w1 < 0 ? INT_MAX : t.w1};
+    ScanResult<V> r{t.b[0], t.b[1], c1, t.w[0] < 0 ? INT_MAX : t.w[0]};
     warp_merge(r);
     return r;
 }
 
-// Short scan of row x over its candidate list (two entries per lane). The
-// list entries and the row's bound theta are loaded in the same round trip;
-// the prices are gathered only when a list exists (theta != 0).
+// Short scan of row x over its candidate list (kListK entries per lane).
+// The list entries and the row's bound theta are loaded in the same round
+// trip; the prices are gathered only when a list exists (theta != 0).
 template <bool WIDE, class P>
-__device__ __forceinline__ auto list_scan(int row, int n, const P &prices, int lane, const RowLists &L,
-                                          unsigned long long &theta) {
+__device__ __forceinline__ auto list_scan(int row, int n, int cmin, uint32_t np1, const P &prices, int lane,
+                                          const RowLists &L, unsigned long long &theta) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
-    const size_t base = (size_t)row * 64 + 2 * lane;
     theta = __ldcg(L.theta + row);
-    const int2 yy = __ldcg(reinterpret_cast<const int2 *>(L.cols + base));
-    V c0, c1;
-    if (WIDE) {
-        const ulonglong2 cc = __ldcg(reinterpret_cast<const ulonglong2 *>(static_cast<const V *>(L.costs) + base));
-        c0 = cc.x;
-        c1 = cc.y;
-    } else {
-        const uint2 cc = __ldcg(reinterpret_cast<const uint2 *>(static_cast<const V *>(L.costs) + base));
-        c0 = cc.x;
-        c1 = cc.y;
-    }
+    const LaneList e = load_lane_list(L, row, lane);
     const V inf = (V)~(V)0;
     ScanResult<V> r{inf, inf, 0, INT_MAX};
     if (theta == 0) return r;            // no list for this row yet (uniform across the warp)
-    const bool ok0 = yy.x >= 0 && yy.x < n, ok1 = yy.y >= 0 && yy.y < n;
-    const V v0 = ok0 ? c0 + prices.q(yy.x) : inf;
-    const V v1 = ok1 ? c1 + prices.q(yy.y) : inf;
-    const bool first = (v0 < v1) || (v0 == v1 && (unsigned)yy.x < (unsigned)yy.y);
-    r.b1 = first ? v0 : v1;
-    r.b2 = first ? v1 : v0;
-    r.c1 = first ? c0 : c1;
-    r.w = first ? (ok0 ? yy.x : INT_MAX) : (ok1 ? yy.y : INT_MAX);
+    V v[kListK], cs[kListK];
+#pragma unroll
+    for (int k = 0; k < kListK; ++k) {
+        const bool ok = e.y[k] >= 0 && e.y[k] < n;
+        cs[k] = (V)(uint32_t)(e.c[k] - cmin) * np1;
+        const V q = prices.q(ok ? e.y[k] : 0);
+        v[k] = ok ? cs[k] + q : inf;
+    }
+#pragma unroll
+    for (int k = 0; k < kListK; ++k) {
+        const bool ok = v[k] != inf;
+        // lowest value, then lowest column; the second best is the minimum
+        // over the other entries
+        const bool better = ok && (v[k] < r.b1 || (v[k] == r.b1 && (unsigned)e.y[k] < (unsigned)r.w));
+        const V hi = better ? r.b1 : v[k];
+        r.b2 = hi < r.b2 ? hi : r.b2;
+        r.c1 = better ? cs[k] : r.c1;
+        r.w = better ? e.y[k] : r.w;
+        r.b1 = better ? v[k] : r.b1;
+    }
     warp_merge(r);
     return r;
 }
@@ -311,7 +342,7 @@ __device__ __forceinline__ auto scan_for_bid(const int32_t *__restrict__ C, int 
     bool ok = false;
     if (L.cols) {
         unsigned long long th = 0;
-        t = list_scan<WIDE>(row, n, prices, lane, L, th);
+        t = list_scan<WIDE>(row, n, cmin, np1, prices, lane, L, th);
         if (th != 0) {
             // Exact when the list's second best does not exceed theta: every
             // other column is >= theta, so the list holds the row's best and
@@ -567,7 +598,7 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
 // price p(x) = eps - v(x, M(x)) of a matched row x (v = c~ - p), the arc
 // x -> y (y != M(x)) has length floor((v(x,y) - v(x,M(x)) + eps) / eps) and
 // the matched arc M(x) -> x has length 0, so the label of a matched column
-// is that of its row. Only the 64 arcs of x's candidate list are relaxed;
+// is that of its row. Only the kListLen arcs of x's candidate list are relaxed;
 // every other column has v >= theta (see RowLists), so the row's label is
 // also capped at floor((theta - v(x,M(x)) + eps) / eps), which keeps the
 // required inequality label(x) <= label(y) + length(x,y) on those arcs
@@ -621,7 +652,6 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
      Ctrl *__restrict__ ctrl, RowLists L, const int *__restrict__ tail_rows, int *__restrict__ qlist0,
      int *__restrict__ qlist1, unsigned *__restrict__ lab, unsigned long long *__restrict__ vref,
      unsigned *__restrict__ cap, int *__restrict__ rowcol, int max_sweeps) {
-    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
     __shared__ int s_ok;
     if (*reinterpret_cast<volatile int *>(&ctrl->handoff) != 2) return;
     if (threadIdx.x == 0) s_ok = 1;
@@ -659,12 +689,12 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
             vr = (unsigned long long)(uint32_t)(ld_row1(C + (size_t)x * n + w) - cmin) * np1 + key_q(__ldcg(key + w));
         } else if (th != 0) {
             // free row: min over the list and theta is <= min_y v(x,y)
-            const size_t base = (size_t)x * 64 + 2 * lane;
-            const int2 yy = __ldcg(reinterpret_cast<const int2 *>(L.cols + base));
-            const V *cc = static_cast<const V *>(L.costs) + base;
+            const LaneList e = load_lane_list(L, x, lane);
             unsigned long long m = ~0ull;
-            if (yy.x >= 0 && yy.x < n) m = min(m, (unsigned long long)__ldcg(cc) + key_q(__ldcg(key + yy.x)));
-            if (yy.y >= 0 && yy.y < n) m = min(m, (unsigned long long)__ldcg(cc + 1) + key_q(__ldcg(key + yy.y)));
+#pragma unroll
+            for (int k = 0; k < kListK; ++k)
+                if (e.y[k] >= 0 && e.y[k] < n)
+                    m = min(m, (unsigned long long)(uint32_t)(e.c[k] - cmin) * np1 + key_q(__ldcg(key + e.y[k])));
             for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
             vr = th == ~0ull ? m : min(m, th - R - 1);
         }
@@ -700,16 +730,13 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
             const unsigned long long th = L.cols ? __ldcg(L.theta + x) : 0ull;
             if (th == 0) continue;
             const unsigned long long vr = vref[x];
-            const size_t base = (size_t)x * 64 + 2 * lane;
-            const int2 yy = __ldcg(reinterpret_cast<const int2 *>(L.cols + base));
-            const V *cc = static_cast<const V *>(L.costs) + base;
+            const LaneList e = load_lane_list(L, x, lane);
             unsigned long long best = cap[x];
-            const int ys[2] = {yy.x, yy.y};
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int y = ys[e];
+            for (int k = 0; k < kListK; ++k) {
+                const int y = e.y[k];
                 if (y < 0 || y >= n || y == w) continue;
-                const unsigned long long vy = (unsigned long long)__ldcg(cc + e) + key_q(__ldcg(key + y));
+                const unsigned long long vy = (unsigned long long)(uint32_t)(e.c[k] - cmin) * np1 + key_q(__ldcg(key + y));
                 const unsigned long long len = vy + eps >= vr ? (vy + eps - vr) / eps : 0;
                 best = min(best, (unsigned long long)__ldcg(lab + y) + len);
             }
@@ -736,14 +763,12 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
         unsigned long long best = cap[x];
         if (th != 0) {
             const unsigned long long vr = vref[x];
-            const size_t base = (size_t)x * 64 + 2 * lane;
-            const int2 yy = __ldcg(reinterpret_cast<const int2 *>(L.cols + base));
-            const V *cc = static_cast<const V *>(L.costs) + base;
-            const int ys[2] = {yy.x, yy.y};
-            for (int e = 0; e < 2; ++e) {
-                const int y = ys[e];
+            const LaneList e = load_lane_list(L, x, lane);
+#pragma unroll
+            for (int k = 0; k < kListK; ++k) {
+                const int y = e.y[k];
                 if (y < 0 || y >= n) continue;
-                const unsigned long long vy = (unsigned long long)__ldcg(cc + e) + key_q(__ldcg(key + y));
+                const unsigned long long vy = (unsigned long long)(uint32_t)(e.c[k] - cmin) * np1 + key_q(__ldcg(key + y));
                 const unsigned long long len = vy >= vr ? (vy - vr) / eps : 0;
                 best = min(best, (unsigned long long)__ldcg(lab + y) + len);
             }
@@ -825,7 +850,7 @@ struct Workspace {
     unsigned long long *key = nullptr;
     void *qm = nullptr;
     int *lcols = nullptr;                 // candidate lists
-    unsigned long long *lcosts = nullptr;
+    int *lcosts = nullptr;
     unsigned long long *ltheta = nullptr;
     int *tail_rows = nullptr;             // rows handed to the tail kernel / price update
     int *qlist[2] = {nullptr, nullptr};   // row queues after a price update
@@ -838,7 +863,7 @@ struct Workspace {
     Ctrl *h_ctrl = nullptr;
     int num_sms = 0;
     bool events = false;
-    cudaEvent_t ev[2 * kMaxPhases];
+    cudaEvent_t ev[3 * kMaxPhases];   // per phase: refine start, tail start, end
 };
 
 std::mutex g_mu;
@@ -903,8 +928,8 @@ la_status ensure_ws(Workspace &ws, int64_t n) {
         const int64_t cap = std::max<int64_t>(n, 1024);
         if (cudaMalloc(&ws.key, sizeof(unsigned long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
         if (cudaMalloc(&ws.qm, sizeof(unsigned long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
-        if (cudaMalloc(&ws.lcols, sizeof(int) * 64 * cap) != cudaSuccess) return LA_ERR_NOMEM;
-        if (cudaMalloc(&ws.lcosts, sizeof(unsigned long long) * 64 * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.lcols, sizeof(int) * kListLen * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&ws.lcosts, sizeof(int) * kListLen * cap) != cudaSuccess) return LA_ERR_NOMEM;
         if (cudaMalloc(&ws.ltheta, sizeof(unsigned long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
         if (cudaMalloc(&ws.tail_rows, sizeof(int) * cap) != cudaSuccess) return LA_ERR_NOMEM;
         if (cudaMalloc(&ws.qlist[0], sizeof(int) * cap) != cudaSuccess) return LA_ERR_NOMEM;
@@ -952,7 +977,7 @@ template <bool WIDE, bool VEC>
 cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C, int n, int cmin, uint32_t np1,
                           unsigned long long eps, unsigned long long qlim, Workspace &ws,
                           unsigned long long budget, const RowLists &L, int tail_T, int pu_T, int pu_rounds,
-                          int64_t &launches, int stop_free) {
+                          int64_t &launches, int stop_free, cudaEvent_t ev_tail) {
     for (int r = 0; r <= pu_rounds; ++r) {
         if (r > 0) {
             cudaError_t e = launch_pu<WIDE>(s, C, n, cmin, np1, eps, qlim, ws, L);
@@ -964,6 +989,10 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
                                                    tail_T, ws.tail_rows, r < pu_rounds ? pu_T : 0,
                                                    ws.qlist[0], ws.qlist[1], stop_free);
         ++launches;
+    }
+    if (ev_tail) {
+        cudaError_t e = cudaEventRecord(ev_tail, s);
+        if (e != cudaSuccess) return e;
     }
     if (tail_T > 0) {
         ++launches;
@@ -1108,15 +1137,17 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         if (wide) k_reset<true><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds);
         else k_reset<false><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds);
         launches += 2;
-        if (profile) LA_CK(cudaEventRecord(ws.ev[2 * ph], s));
+        if (profile) LA_CK(cudaEventRecord(ws.ev[3 * ph], s));
+        const int sf = ph + 1 < (int)sched.size() ? stop_free : 0;
+        cudaEvent_t evt = profile ? ws.ev[3 * ph + 1] : nullptr;
         if (wide) {
-            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, ph + 1 < (int)sched.size() ? stop_free : 0)));
-            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, ph + 1 < (int)sched.size() ? stop_free : 0)));
+            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt)));
+            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt)));
         } else {
-            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, ph + 1 < (int)sched.size() ? stop_free : 0)));
-            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, ph + 1 < (int)sched.size() ? stop_free : 0)));
+            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt)));
+            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt)));
         }
-        if (profile) LA_CK(cudaEventRecord(ws.ev[2 * ph + 1], s));
+        if (profile) LA_CK(cudaEventRecord(ws.ev[3 * ph + 2], s));
     }
     const int fslot = ph & 1;
     if (prices_out) {
@@ -1150,15 +1181,19 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         const unsigned long long end = (k + 1 < ph) ? c1.phase_start_scans[k + 1] : c1.scans;
         stats.phase_scans[k] = (int64_t)(end - c1.phase_start_scans[k]);
     }
+    stats.list_entries = lists ? kListLen : 0;
     if (profile) {
-        double ms = 0;
+        double ms = 0, tail_ms = 0;
         for (int k = 0; k < ph; ++k) {
-            float t = 0;
-            LA_CK(cudaEventElapsedTime(&t, ws.ev[2 * k], ws.ev[2 * k + 1]));
+            float t = 0, tt = 0;
+            LA_CK(cudaEventElapsedTime(&t, ws.ev[3 * k], ws.ev[3 * k + 2]));
+            LA_CK(cudaEventElapsedTime(&tt, ws.ev[3 * k + 1], ws.ev[3 * k + 2]));
             ms += t;
+            tail_ms += tt;
             if (k < LA_STATS_PHASES) stats.phase_ms[k] = t;
         }
         stats.refine_ms = ms;
+        stats.tail_ms = tail_ms;
     }
     if (st) *st = stats;
     return (la_status)c1.status;
