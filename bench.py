@@ -244,7 +244,7 @@ def bench_batched(args, la, synth, dev, stream):
             "scans": stats["scans"], "cost_bytes": int(flat.size) * 4,
             "per_instance_la_solve_per_s": per, "per_instance_sample": len(idx),
             "speedup_vs_per_instance": (args.batch / best) / per, "generate_s": gen_s,
-            "autotuned": {"block_threads": table["block_threads"], "max_n": table["max_n"],
+            "autotuned": {"block_threads": table["block_threads"], "slots": table["slots"], "max_n": table["max_n"],
                           "alpha_by_log2n": table["alpha"], "tune_s": t_tune}}
 
 

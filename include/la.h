@@ -200,8 +200,8 @@ int32_t la_version(void);
 #define LA_BATCH_MAX_N 8192   /* largest instance of a batched solve */
 
 typedef struct {
-    /* Threads per CTA: 32 x the warps that bid concurrently on one instance
-       (64, 128, 256 or 512; 0 selects 128). */
+    /* Threads per CTA (64, 128, 256, 512 or 1024; 0 selects 512): the warps
+       that share the CTA's resident instances (see slots). */
     int32_t block_threads;
     /* Largest n the launch must hold in shared memory (0 = LA_BATCH_MAX_N);
        smaller values let more CTAs share an SM. Instances with n > max_n
@@ -220,6 +220,10 @@ typedef struct {
        packed like match_out (paper sign, units of (n_i+1) C, up to a
        constant per instance). */
     int64_t *prices_out;
+    /* Instances resident per CTA (1..8, 0 selects 4; fewer when their keys,
+       8 max_n bytes each, would exceed 192 KB of shared memory). The CTA's
+       warps take free rows from any resident instance. */
+    int32_t slots;
 } la_batch_options;
 
 typedef struct {
@@ -235,6 +239,7 @@ typedef struct {
     int32_t block_threads;
     int32_t graph;          /* 1 if the launch was a CUDA graph replay */
     double device_ms;       /* launch time (profile != 0) */
+    int32_t slots;          /* instances resident per CTA */
 } la_batch_stats;
 
 la_status la_solve_batched(const int32_t *cost, const int64_t *offsets, const int32_t *ns,

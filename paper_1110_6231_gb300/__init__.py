@@ -107,6 +107,7 @@ class la_batch_options(ctypes.Structure):
         ("no_graph", ctypes.c_int32),
         ("profile", ctypes.c_int32),
         ("prices_out", ctypes.c_void_p),
+        ("slots", ctypes.c_int32),
     ]
 
 
@@ -124,6 +125,7 @@ class la_batch_stats(ctypes.Structure):
         ("block_threads", ctypes.c_int32),
         ("graph", ctypes.c_int32),
         ("device_ms", ctypes.c_double),
+        ("slots", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -356,7 +358,8 @@ class BatchSolution:
 
 
 def batch_options(block_threads: int = 0, max_n: int = 0, alpha=None, budget_factor: int = 0,
-                  no_graph: bool = False, profile: bool = False, prices_out=None) -> la_batch_options:
+                  no_graph: bool = False, profile: bool = False, prices_out=None,
+                  slots: int = 0) -> la_batch_options:
     """Build la_batch_options; ``alpha`` is an int or a per-bucket list
     (bucket k holds 2^k <= n < 2^(k+1))."""
     o = la_batch_options()
@@ -370,6 +373,7 @@ def batch_options(block_threads: int = 0, max_n: int = 0, alpha=None, budget_fac
     o.no_graph = int(bool(no_graph))
     o.profile = int(bool(profile))
     o.prices_out = _ptr(prices_out)
+    o.slots = slots
     return o
 
 

@@ -33,6 +33,8 @@ using namespace la;
 namespace {
 
 constexpr int kPrepThreads = 1024;
+constexpr int kDefaultSlots = 4;                 // instances resident per CTA
+constexpr size_t kSlotSmemBudget = 192 * 1024;   // shared memory for their column keys
 constexpr int kMaxDevices = 64;
 
 struct BatchCtrl {
@@ -130,149 +132,140 @@ k_batch_prep(const int *__restrict__ ns, int B, int max_n, long long *__restrict
     }
 }
 
-// One refine phase of one instance by one warp (all warps of the CTA run it
-// concurrently on the shared keys).
-template <bool WIDE>
-__device__ __forceinline__ void warp_refine(const int32_t *__restrict__ Ci, int n, int cmin, uint32_t np1,
-                                            unsigned long long eps, unsigned long long qlim,
-                                            unsigned long long *skey, int *s_next_row,
-                                            unsigned long long *s_scans, int *s_status,
-                                            unsigned long long budget, bool vec, int lane,
-                                            unsigned long long &wins, unsigned long long &displaced) {
-    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
-    const volatile unsigned long long *vkey = skey;
-    int row = -1;
-    for (;;) {
-        if (row < 0) {
-            int r = 0;
-            if (lane == 0) r = atomicAdd(s_next_row, 1);
-            row = __shfl_sync(0xffffffffu, r, 0);
-            if (row >= n) break;
-        }
-        unsigned long long s = 0;
-        int st = 0;
-        if (lane == 0) {
-            s = atomicAdd(s_scans, 1ull);
-            st = *reinterpret_cast<volatile int *>(s_status);
-        }
-        s = __shfl_sync(0xffffffffu, s, 0);
-        st = __shfl_sync(0xffffffffu, st, 0);
-        if (st != 0) break;
-        if (s >= budget) {
-            if (lane == 0) atomicCAS(s_status, 0, (int)LA_ERR_ITER_LIMIT);
-            break;
-        }
-        const int32_t *crow = Ci + (size_t)row * n;
-        Lane2<V> t;
-        lane2_init(t);
-        if (vec) {
-            const int4 *r4 = reinterpret_cast<const int4 *>(crow);
-            const int nv = n >> 2;
-#pragma unroll 2
-            for (int j = lane; j < nv; j += 32) {
-                const int4 c = ld_row4(r4 + j);
-                const int y = j << 2;
-                lane2_push<V>(t, (V)(uint32_t)(c.x - cmin) * np1 + (V)key_q(vkey[y]), y);
-                lane2_push<V>(t, (V)(uint32_t)(c.y - cmin) * np1 + (V)key_q(vkey[y + 1]), y + 1);
-                lane2_push<V>(t, (V)(uint32_t)(c.z - cmin) * np1 + (V)key_q(vkey[y + 2]), y + 2);
-                lane2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + (V)key_q(vkey[y + 3]), y + 3);
-            }
-        } else {
-#pragma unroll 4
-            for (int y = lane; y < n; y += 32) {
-                const int c = ld_row1(crow + y);
-                lane2_push<V>(t, (V)(uint32_t)(c - cmin) * np1 + (V)key_q(vkey[y]), y);
-            }
-        }
-        const V c1 = t.w1 >= 0 ? (V)(uint32_t)(ld_row1(crow + t.w1) - cmin) * np1 : (V)0;
-        ScanResult<V> r{t.b1, t.b2, c1, t.w1 < 0 ? INT_MAX : t.w1};
-        warp_merge(r);
-        const unsigned long long nq = (unsigned long long)(r.b1 - r.c1) + (r.b2 - r.b1) + eps;
-        if (r.w >= n || nq > qlim) {
-            if (lane == 0) atomicCAS(s_status, 0, (int)(r.w >= n ? LA_ERR_INTERNAL : LA_ERR_OVERFLOW));
-            break;
-        }
-        const unsigned long long nk = pack_key(nq, (uint32_t)row);
-        unsigned long long old = 0;
-        if (lane == 0) old = atomicMin(skey + r.w, nk);
-        old = __shfl_sync(0xffffffffu, old, 0);
-        if (old > nk) {
-            ++wins;
-            const uint32_t m = key_mate(old);
-            if (m != kNone) {
-                ++displaced;
-                row = (int)m;
+// Per-instance min and max cost (a bandwidth-bound pass over the whole
+// batch before the solve): block b reduces instances b, b + gridDim.x, ...
+__global__ void __launch_bounds__(256)
+k_batch_minmax(const int32_t *__restrict__ C, const long long *__restrict__ offsets,
+               const int *__restrict__ ns, int B, int max_n, int2 *__restrict__ cminmax) {
+    __shared__ int s_lo[8], s_hi[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = blockIdx.x; i < B; i += gridDim.x) {
+        const int n = ns[i];
+        int lo = INT_MAX, hi = INT_MIN;
+        if (n > 0 && n <= max_n) {
+            const int32_t *Ci = C + offsets[i];
+            const long long tot = (long long)n * n;
+            if ((reinterpret_cast<uintptr_t>(Ci) & 15) == 0) {
+                const int4 *C4 = reinterpret_cast<const int4 *>(Ci);
+                const long long nv = tot >> 2;
+                for (long long e = tid; e < nv; e += 256) {
+                    const int4 c = ld_row4(C4 + e);
+                    lo = min(lo, min(min(c.x, c.y), min(c.z, c.w)));
+                    hi = max(hi, max(max(c.x, c.y), max(c.z, c.w)));
+                }
+                for (long long e = (nv << 2) + tid; e < tot; e += 256) {
+                    const int c = ld_row1(Ci + e);
+                    lo = min(lo, c);
+                    hi = max(hi, c);
+                }
             } else {
-                row = -1;
+                for (long long e = tid; e < tot; e += 256) {
+                    const int c = ld_row1(Ci + e);
+                    lo = min(lo, c);
+                    hi = max(hi, c);
+                }
             }
         }
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if (lane == 0) {
+            s_lo[warp] = lo;
+            s_hi[warp] = hi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < 8; ++w) {
+                lo = min(lo, s_lo[w]);
+                hi = max(hi, s_hi[w]);
+            }
+            cminmax[i] = make_int2(lo, hi);
+        }
+        __syncthreads();
     }
 }
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-k_batch_solve(const int32_t *__restrict__ C, const long long *__restrict__ offsets,
-              const int *__restrict__ ns, const int *__restrict__ order,
-              const long long *__restrict__ moff, int B, int max_n, BatchParams P,
-              int32_t *__restrict__ match_out, long long *__restrict__ cost_out,
-              int *__restrict__ inst_status, BatchCtrl *ctrl, long long *__restrict__ prices_out) {
-    extern __shared__ unsigned long long skey[];
-    __shared__ int s_k, s_next_row, s_cmin, s_cmax, s_status;
-    __shared__ unsigned long long s_qmin, s_scans, s_cost;
-    const int tid = threadIdx.x, lane = tid & 31;
-    unsigned long long wins = 0, displaced = 0, phases_run = 0;
+// One instance resident in a CTA. Rows are claimed with one atomicAdd on
+// `claim` = (n << 32) | next row: a claim is valid exactly when the returned
+// index is below the returned n, so no claim can land between two phases or
+// two instances (the slot is republished by one atomicExch after its fields
+// are written).
+struct Slot {
+    unsigned long long claim;
+    unsigned long long eps, qlim, budget, scans;
+    long long off;       // element offset of the instance's matrix
+    long long moff;      // offset of its rows in match_out / prices_out
+    int inst;            // instance index, -1 = empty
+    int n, cmin, phase, nph, alpha, wide, vec;
+    int unmatched;       // rows not yet matched (or given up) in this phase
+    int status;
+};
+constexpr int kMaxSlots = 8;
+
+struct BatchArgs {
+    const int32_t *C;
+    const long long *offsets;
+    const int *ns;
+    const int *order;
+    const long long *moff;
+    const int2 *cminmax;
+    int B, max_n;
+    BatchParams P;
+    int32_t *match_out;
+    long long *cost_out;
+    int *inst_status;
+    BatchCtrl *ctrl;
+    long long *prices_out;
+};
+
+__device__ __forceinline__ void finish_trivial(const BatchArgs &a, int i, int st, long long cost, int ctrl_failed) {
+    if (a.cost_out) a.cost_out[i] = cost;
+    if (a.inst_status) a.inst_status[i] = st;
+    if (st && ctrl_failed) {
+        atomicAdd(&a.ctrl->failed, 1);
+        atomicCAS(&a.ctrl->status, 0, st);
+    }
+}
+
+// Loads the next instance of the work queue (largest first) into a slot
+// (one warp). Instances that need no refine (n = 0 or 1, an invalid n, a
+// cost range beyond the exact price field) are finished on the spot. The
+// slot is left empty once the queue is drained.
+__device__ void load_next(const BatchArgs &a, Slot &sl, unsigned long long *keys, int lane) {
+    volatile Slot &v = sl;
     for (;;) {
-        if (tid == 0) s_k = atomicAdd(&ctrl->next, 1);
-        __syncthreads();
-        const int k = s_k;
-        if (k >= B) break;
-        const int i = order[k];
-        const int n = ns[i];
-        if (tid == 0) {
-            s_cmin = INT_MAX;
-            s_cmax = INT_MIN;
-            s_status = 0;
-            s_scans = 0;
-            s_cost = 0;
-        }
-        __syncthreads();
-        if (n < 0 || n > max_n || n == 0) {
-            if (tid == 0) {
-                const int st = n == 0 ? 0 : (int)LA_ERR_INVALID;
-                if (cost_out) cost_out[i] = 0;
-                if (inst_status) inst_status[i] = st;
-                if (st) {
-                    atomicAdd(&ctrl->failed, 1);
-                    atomicCAS(&ctrl->status, 0, st);
-                }
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&a.ctrl->next, 1);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= a.B) {
+            if (lane == 0) {
+                v.inst = -1;
+                v.claim = 0ull;
             }
-            __syncthreads();
+            __syncwarp();
+            return;
+        }
+        const int i = a.order[k];
+        const int n = a.ns[i];
+        if (n < 0 || n > a.max_n || n == 0) {
+            if (lane == 0) finish_trivial(a, i, n == 0 ? 0 : (int)LA_ERR_INVALID, 0, 1);
             continue;
         }
-        const int32_t *Ci = C + offsets[i];
-        int32_t *Mi = match_out ? match_out + moff[i] : nullptr;
-        // min and max cost of the instance
-        {
-            int lo = INT_MAX, hi = INT_MIN;
-            const long long tot = (long long)n * n;
-            for (long long e = tid; e < tot; e += BLOCK) {
-                const int c = ld_row1(Ci + e);
-                lo = min(lo, c);
-                hi = max(hi, c);
-            }
-            lo = __reduce_min_sync(0xffffffffu, lo);
-            hi = __reduce_max_sync(0xffffffffu, hi);
-            if (lane == 0) {
-                atomicMin(&s_cmin, lo);
-                atomicMax(&s_cmax, hi);
-            }
-        }
-        for (int y = tid; y < n; y += BLOCK) skey[y] = ~0ull;   // q = 0, no mate
-        __syncthreads();
-        const int cmin = s_cmin;
+        const int2 mm = a.cminmax[i];
         const unsigned long long np1 = (unsigned long long)n + 1;
-        const unsigned long long Ct = np1 * (unsigned long long)((long long)s_cmax - (long long)cmin);
-        const int alpha = max(2, P.alpha[log2_bucket(n)]);
+        const unsigned long long Ct = np1 * (unsigned long long)((long long)mm.y - (long long)mm.x);
+        if (Ct >= (1ull << 40)) {
+            if (lane == 0) finish_trivial(a, i, (int)LA_ERR_OVERFLOW, 0, 1);
+            continue;
+        }
+        if (n == 1) {
+            if (lane == 0) {
+                if (a.match_out) a.match_out[a.moff[i]] = 0;
+                if (a.prices_out) a.prices_out[a.moff[i]] = 0;
+                finish_trivial(a, i, 0, (long long)a.C[a.offsets[i]], 0);
+            }
+            continue;
+        }
+        const int alpha = max(2, a.P.alpha[log2_bucket(n)]);
         int nph = 0;
         {
             unsigned long long e = Ct;
@@ -283,86 +276,272 @@ k_batch_solve(const int32_t *__restrict__ C, const long long *__restrict__ offse
         }
         const unsigned long long eps1 = max(1ull, Ct / (unsigned long long)alpha);
         const bool wide = 4 * Ct + 2 * eps1 + 16 >= (1ull << 32);
-        const unsigned long long qlim = wide ? (kQMax - 1) : ((1ull << 32) - 2 - Ct);
-        const bool vec = ((offsets[i] & 3) == 0) && (n % 4 == 0) &&
-                         ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
-        const unsigned long long budget = (unsigned long long)P.budget_factor * n * nph + 65536;
-        if (Ct >= (1ull << 40)) {
-            if (tid == 0) s_status = LA_ERR_OVERFLOW;
-        } else if (n == 1) {
-            if (tid == 0) {
-                if (Mi) Mi[0] = 0;
-                s_cost = (unsigned long long)(long long)Ci[0];
-            }
-        } else {
-            unsigned long long eps = Ct;
-            for (int ph = 0; ph < nph; ++ph) {
-                eps = max(1ull, eps / (unsigned long long)alpha);
-                // refine initialisation: shift prices so that min q = 0,
-                // clear every mate, reset the row queue
-                if (tid == 0) s_qmin = ~0ull;
-                __syncthreads();
-                unsigned long long m = ~0ull;
-                for (int y = tid; y < n; y += BLOCK) m = min(m, key_q(skey[y]));
-                for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
-                if (lane == 0) atomicMin(&s_qmin, m);
-                __syncthreads();
-                const unsigned long long qmin = s_qmin;
-                for (int y = tid; y < n; y += BLOCK) skey[y] = pack_key(key_q(skey[y]) - qmin, kNone);
-                if (tid == 0) s_next_row = 0;
-                __syncthreads();
-                if (wide)
-                    warp_refine<true>(Ci, n, cmin, (uint32_t)np1, eps, qlim, skey, &s_next_row, &s_scans,
-                                      &s_status, budget, vec, lane, wins, displaced);
-                else
-                    warp_refine<false>(Ci, n, cmin, (uint32_t)np1, eps, qlim, skey, &s_next_row, &s_scans,
-                                       &s_status, budget, vec, lane, wins, displaced);
-                __syncthreads();
-                ++phases_run;
-                if (s_status) break;
-            }
-            if (!s_status) {
-                long long sum = 0;
-                for (int y = tid; y < n; y += BLOCK) {
-                    const uint32_t mm = key_mate(skey[y]);
-                    if (mm >= (uint32_t)n) {
-                        atomicCAS(&s_status, 0, (int)LA_ERR_INTERNAL);
-                        continue;
-                    }
-                    if (Mi) Mi[mm] = y;
-                    if (prices_out) prices_out[moff[i] + y] = -(long long)key_q(skey[y]);
-                    sum += Ci[(size_t)mm * n + y];
+        for (int y = lane; y < n; y += 32) keys[y] = ~0ull;   // q = 0, no mate
+        if (lane == 0) {
+            v.inst = i;
+            v.n = n;
+            v.cmin = mm.x;
+            v.off = a.offsets[i];
+            v.moff = a.moff[i];
+            v.alpha = alpha;
+            v.nph = nph;
+            v.phase = 0;
+            v.eps = eps1;
+            v.wide = wide;
+            v.qlim = wide ? (kQMax - 1) : ((1ull << 32) - 2 - Ct);
+            v.vec = ((a.offsets[i] & 3) == 0) && (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15) == 0);
+            v.budget = (unsigned long long)a.P.budget_factor * n * nph + 65536;
+            v.scans = 0;
+            v.status = 0;
+            v.unmatched = n;
+        }
+        __syncwarp();
+        __threadfence_block();
+        if (lane == 0) atomicExch(&sl.claim, (unsigned long long)n << 32);
+        __syncwarp();
+        return;
+    }
+}
+
+// The displacement chain of one claimed row (one warp): scan, double push
+// (one shared-memory atomicMin on the column key), continue with the row it
+// displaced, until a bid lands on a column nobody held. Returns true when
+// that made the slot's last row matched: the phase is over and the caller
+// runs the next one.
+template <bool WIDE>
+__device__ bool run_chain(Slot &sl, unsigned long long *keys, const int32_t *__restrict__ Ci, int row, int n,
+                          int cmin, unsigned long long eps, unsigned long long qlim, unsigned long long budget,
+                          bool vec, int lane, unsigned long long &wins, unsigned long long &displaced) {
+    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    const volatile unsigned long long *vkey = keys;
+    const uint32_t np1 = (uint32_t)n + 1;
+    for (;;) {
+        unsigned long long s = 0;
+        int st = 0;
+        if (lane == 0) {
+            s = atomicAdd(&sl.scans, 1ull);
+            st = *reinterpret_cast<volatile int *>(&sl.status);
+        }
+        s = __shfl_sync(0xffffffffu, s, 0);
+        st = __shfl_sync(0xffffffffu, st, 0);
+        bool give_up = st != 0 || s >= budget;
+        if (give_up && st == 0 && lane == 0) atomicCAS(&sl.status, 0, (int)LA_ERR_ITER_LIMIT);
+        ScanResult<V> r{0, 0, 0, 0};
+        if (!give_up) {
+            const int32_t *crow = Ci + (size_t)row * n;
+            prefetch_row_l2(crow, n, lane);
+            Lane2<V> t;
+            lane2_init(t);
+            if (vec) {
+                const int4 *r4 = reinterpret_cast<const int4 *>(crow);
+                const int nv = n >> 2;
+#pragma unroll 2
+                for (int j = lane; j < nv; j += 32) {
+                    const int4 c = ld_row4(r4 + j);
+                    const int y = j << 2;
+                    lane2_push<V>(t, (V)(uint32_t)(c.x - cmin) * np1 + (V)key_q(vkey[y]), y);
+                    lane2_push<V>(t, (V)(uint32_t)(c.y - cmin) * np1 + (V)key_q(vkey[y + 1]), y + 1);
+                    lane2_push<V>(t, (V)(uint32_t)(c.z - cmin) * np1 + (V)key_q(vkey[y + 2]), y + 2);
+                    lane2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + (V)key_q(vkey[y + 3]), y + 3);
                 }
-                for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-                if (lane == 0 && sum) atomicAdd(&s_cost, (unsigned long long)sum);
+            } else {
+#pragma unroll 4
+                for (int y = lane; y < n; y += 32) {
+                    const int c = ld_row1(crow + y);
+                    lane2_push<V>(t, (V)(uint32_t)(c - cmin) * np1 + (V)key_q(vkey[y]), y);
+                }
+            }
+            const V c1 = t.w1 >= 0 ? (V)(uint32_t)(ld_row1(crow + t.w1) - cmin) * np1 : (V)0;
+            r = ScanResult<V>{t.b1, t.b2, c1, t.w1 < 0 ? INT_MAX : t.w1};
+            warp_merge(r);
+        }
+        const unsigned long long nq = give_up ? 0ull : (unsigned long long)(r.b1 - r.c1) + (r.b2 - r.b1) + eps;
+        if (!give_up && (r.w >= n || nq > qlim)) {
+            if (lane == 0) atomicCAS(&sl.status, 0, (int)(r.w >= n ? LA_ERR_INTERNAL : LA_ERR_OVERFLOW));
+            give_up = true;
+        }
+        if (give_up) {
+            // The instance has failed: its rows are given up one by one, so
+            // the phase still ends (and the slot is released) once every row
+            // is matched or given up.
+            int left = 1;
+            if (lane == 0) left = atomicSub(&sl.unmatched, 1) - 1;
+            left = __shfl_sync(0xffffffffu, left, 0);
+            return left == 0;
+        }
+        const unsigned long long nk = pack_key(nq, (uint32_t)row);
+        unsigned long long old = 0;
+        int left = 1;
+        if (lane == 0) {
+            old = atomicMin(keys + r.w, nk);
+            if (old > nk && key_mate(old) == kNone) {
+                __threadfence_block();   // the commit is visible before the count can reach 0
+                left = atomicSub(&sl.unmatched, 1) - 1;
             }
         }
-        __syncthreads();
-        if (tid == 0) {
-            const int st = s_status;
-            if (cost_out) cost_out[i] = (long long)s_cost;
-            if (inst_status) inst_status[i] = st;
-            atomicAdd(&ctrl->scans, s_scans);
-            atomicAdd(&ctrl->scan_bytes, s_scans * 4ull * (unsigned long long)n);
-            if (st) {
-                atomicAdd(&ctrl->failed, 1);
-                atomicCAS(&ctrl->status, 0, st);
-            }
+        old = __shfl_sync(0xffffffffu, old, 0);
+        left = __shfl_sync(0xffffffffu, left, 0);
+        if (old > nk) {
+            ++wins;
+            const uint32_t m = key_mate(old);
+            if (m == kNone) return left == 0;
+            ++displaced;
+            row = (int)m;
         }
-        __syncthreads();
+        // else: a lower price got there first; rescan this row
+    }
+}
+
+// After a slot's last row was matched (one warp; no other warp can touch the
+// slot: none of its rows is free and every claim fails): the next phase's
+// refine initialisation (Algorithm 5.2: keep prices shifted so that min q =
+// 0, clear every mate, all rows free), or, after the eps = 1 phase, the
+// instance's outputs and the next instance.
+__device__ void end_phase(const BatchArgs &a, Slot &sl, unsigned long long *keys, int lane,
+                          unsigned long long &phases_run) {
+    volatile Slot &v = sl;
+    __threadfence_block();
+    ++phases_run;
+    const int n = v.n;
+    const int st = v.status;
+    if (st == 0 && v.phase + 1 < v.nph) {
+        unsigned long long m = ~0ull;
+        for (int y = lane; y < n; y += 32) m = min(m, key_q(keys[y]));
+        m = warp_min(m);
+        for (int y = lane; y < n; y += 32) keys[y] = pack_key(key_q(keys[y]) - m, kNone);
+        if (lane == 0) {
+            v.eps = max(1ull, v.eps / (unsigned long long)v.alpha);
+            v.phase = v.phase + 1;
+            v.unmatched = n;
+        }
+        __syncwarp();
+        __threadfence_block();
+        if (lane == 0) atomicExch(&sl.claim, (unsigned long long)n << 32);
+        __syncwarp();
+        return;
+    }
+    const int i = v.inst;
+    const int32_t *Ci = a.C + v.off;
+    const long long mo = v.moff;
+    int fst = st;
+    long long sum = 0;
+    if (fst == 0) {
+        bool bad = false;
+        for (int y = lane; y < n; y += 32) {
+            const uint32_t mm = key_mate(keys[y]);
+            if (mm >= (uint32_t)n) {
+                bad = true;
+                continue;
+            }
+            if (a.match_out) a.match_out[mo + mm] = y;
+            if (a.prices_out) a.prices_out[mo + y] = -(long long)key_q(keys[y]);
+            sum += Ci[(size_t)mm * n + y];
+        }
+        if (__any_sync(0xffffffffu, bad)) fst = LA_ERR_INTERNAL;
+        for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     }
     if (lane == 0) {
-        atomicAdd(&ctrl->wins, wins);
-        atomicAdd(&ctrl->displaced, displaced);
+        const unsigned long long sc = v.scans;
+        if (a.cost_out) a.cost_out[i] = fst == 0 ? sum : 0;
+        if (a.inst_status) a.inst_status[i] = fst;
+        atomicAdd(&a.ctrl->scans, sc);
+        atomicAdd(&a.ctrl->scan_bytes, sc * 4ull * (unsigned long long)n);
+        if (fst) {
+            atomicAdd(&a.ctrl->failed, 1);
+            atomicCAS(&a.ctrl->status, 0, fst);
+        }
     }
-    if (tid == 0) atomicAdd(&ctrl->phases, phases_run);
+    __syncwarp();
+    load_next(a, sl, keys, lane);
+}
+
+// The batched solve: a persistent grid; each CTA keeps up to S instances
+// resident in shared memory (one slot each: column keys and state), and
+// every warp takes free rows from any slot. A phase of an instance ends when
+// its last row is matched, with no CTA barrier, so warps never wait for
+// another instance's displacement chains.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_batch_solve(BatchArgs a, int S) {
+    extern __shared__ unsigned long long skey[];
+    __shared__ Slot s_slot[kMaxSlots];
+    constexpr int kWarps = BLOCK / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long wins = 0, displaced = 0, phases_run = 0;
+    for (int s = warp; s < S; s += kWarps) load_next(a, s_slot[s], skey + (size_t)s * a.max_n, lane);
+    __syncthreads();
+    int s0 = warp % S;
+    unsigned long long t_idle = 0, p_idle = 0;
+    for (;;) {
+        int row = -1, sl = -1;
+        bool live = false;
+        unsigned long long progress = 0;
+        if (lane == 0) {
+            for (int k = 0; k < S; ++k) {
+                const int s = s0 + k < S ? s0 + k : s0 + k - S;
+                volatile Slot &t = s_slot[s];
+                if (t.inst < 0) continue;
+                live = true;
+                progress += t.scans + (unsigned long long)t.inst;
+                const unsigned long long w = t.claim;
+                if ((uint32_t)w >= (uint32_t)(w >> 32)) continue;
+                const unsigned long long old = atomicAdd(&s_slot[s].claim, 1ull);
+                if ((uint32_t)old < (uint32_t)(old >> 32)) {
+                    row = (int)(uint32_t)old;
+                    sl = s;
+                    break;
+                }
+            }
+        }
+        row = __shfl_sync(0xffffffffu, row, 0);
+        sl = __shfl_sync(0xffffffffu, sl, 0);
+        live = __shfl_sync(0xffffffffu, (int)live, 0) != 0;
+        if (row < 0) {
+            if (!live) break;
+            // Nothing to claim: the other warps are running this CTA's
+            // chains. A CTA that makes no progress at all for 10 s has
+            // broken its own bookkeeping: stop with an error, never spin.
+            int stop = 0;
+            if (lane == 0) {
+                const unsigned long long now = global_timer_ns();
+                if (t_idle == 0 || progress != p_idle) {
+                    t_idle = now;
+                    p_idle = progress;
+                } else if (now - t_idle > 10000000000ull) {
+                    atomicCAS(&a.ctrl->status, 0, (int)LA_ERR_INTERNAL);
+                    stop = 1;
+                }
+                __nanosleep(256);
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) break;
+            continue;
+        }
+        t_idle = 0;
+        __threadfence_block();
+        Slot &t = s_slot[sl];
+        volatile Slot &v = t;
+        unsigned long long *keys = skey + (size_t)sl * a.max_n;
+        const int n = v.n;
+        const bool done = v.wide
+            ? run_chain<true>(t, keys, a.C + v.off, row, n, v.cmin, v.eps, v.qlim, v.budget, v.vec != 0, lane,
+                              wins, displaced)
+            : run_chain<false>(t, keys, a.C + v.off, row, n, v.cmin, v.eps, v.qlim, v.budget, v.vec != 0, lane,
+                               wins, displaced);
+        if (done) end_phase(a, t, keys, lane, phases_run);
+        s0 = sl;
+    }
+    if (lane == 0) {
+        atomicAdd(&a.ctrl->wins, wins);
+        atomicAdd(&a.ctrl->displaced, displaced);
+        atomicAdd(&a.ctrl->phases, phases_run);
+    }
 }
 
 // ---------------------------------------------------------------- host side
 
 struct GraphKey {
     const void *cost, *offsets, *ns, *match, *costout, *status, *prices;
-    int B, block, max_n;
+    int B, block, max_n, slots;
     cudaStream_t stream;
     BatchParams P;
     bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
@@ -375,6 +554,7 @@ struct BatchWorkspace {
     int *order = nullptr;
     int *hist = nullptr;
     int *status = nullptr;
+    int2 *cminmax = nullptr;
     BatchCtrl *ctrl = nullptr;
     BatchCtrl *h_ctrl = nullptr;
     int num_sms = 0;
@@ -407,6 +587,8 @@ la_status ensure_bws(BatchWorkspace &w, int64_t B, int max_n) {
         cudaFree(w.order);
         cudaFree(w.hist);
         cudaFree(w.status);
+        cudaFree(w.cminmax);
+        w.cminmax = nullptr;
         w.moff = nullptr;
         w.order = nullptr;
         w.hist = nullptr;
@@ -416,6 +598,7 @@ la_status ensure_bws(BatchWorkspace &w, int64_t B, int max_n) {
         if (cudaMalloc(&w.moff, sizeof(long long) * cap) != cudaSuccess) return LA_ERR_NOMEM;
         if (cudaMalloc(&w.order, sizeof(int) * cap) != cudaSuccess) return LA_ERR_NOMEM;
         if (cudaMalloc(&w.status, sizeof(int) * cap) != cudaSuccess) return LA_ERR_NOMEM;
+        if (cudaMalloc(&w.cminmax, sizeof(int2) * cap) != cudaSuccess) return LA_ERR_NOMEM;
         if (cudaMalloc(&w.hist, sizeof(int) * (mcap + 2)) != cudaSuccess) return LA_ERR_NOMEM;
         w.capB = cap;
         w.max_n_cap = mcap;
@@ -424,45 +607,39 @@ la_status ensure_bws(BatchWorkspace &w, int64_t B, int max_n) {
 }
 
 template <int BLOCK>
-cudaError_t launch_solve(cudaStream_t s, int grid, size_t smem, const int32_t *cost, const int64_t *offsets,
-                         const int32_t *ns, const BatchWorkspace &w, int B, int max_n, const BatchParams &P,
-                         int32_t *match_out, int64_t *cost_out, int *status, int64_t *prices) {
-    k_batch_solve<BLOCK><<<grid, BLOCK, smem, s>>>(cost, reinterpret_cast<const long long *>(offsets), ns,
-                                                   w.order, w.moff, B, max_n, P, match_out,
-                                                   reinterpret_cast<long long *>(cost_out), status, w.ctrl,
-                                                   reinterpret_cast<long long *>(prices));
-    return cudaGetLastError();
-}
-
-template <int BLOCK>
 int solve_grid(int num_sms, size_t smem) {
-    static int occ[2] = {0, 0};
-    static size_t occ_smem[2] = {0, 0};
-    const int slot = 0;
-    if (!occ[slot] || occ_smem[slot] != smem) {
+    static int occ = 0;
+    static size_t occ_smem = 0;
+    if (!occ || occ_smem != smem) {
         int o = 0;
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k_batch_solve<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch_solve<BLOCK>, BLOCK, smem);
-        occ[slot] = std::max(1, o);
-        occ_smem[slot] = smem;
+        occ = std::max(1, o);
+        occ_smem = smem;
     }
-    return num_sms * occ[slot];
+    return num_sms * occ;
 }
 
-cudaError_t enqueue(cudaStream_t s, int block, int grid, size_t smem, const int32_t *cost,
-                    const int64_t *offsets, const int32_t *ns, BatchWorkspace &w, int B, int max_n,
-                    const BatchParams &P, int32_t *match_out, int64_t *cost_out, int *status, int64_t *prices) {
-    cudaError_t e = cudaMemsetAsync(w.ctrl, 0, sizeof(BatchCtrl), s);
+cudaError_t enqueue(cudaStream_t s, int block, int grid, size_t smem, int slots, const BatchArgs &args,
+                    int *hist, int num_sms) {
+    cudaError_t e = cudaMemsetAsync(args.ctrl, 0, sizeof(BatchCtrl), s);
     if (e != cudaSuccess) return e;
-    k_batch_prep<<<1, kPrepThreads, 0, s>>>(ns, B, max_n, w.moff, w.order, w.hist, w.ctrl);
+    k_batch_prep<<<1, kPrepThreads, 0, s>>>(args.ns, args.B, args.max_n, const_cast<long long *>(args.moff),
+                                            const_cast<int *>(args.order), hist, args.ctrl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int mm_grid = std::max(1, std::min(args.B, 8 * num_sms));
+    k_batch_minmax<<<mm_grid, 256, 0, s>>>(args.C, args.offsets, args.ns, args.B, args.max_n,
+                                           const_cast<int2 *>(args.cminmax));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     switch (block) {
-    case 64: return launch_solve<64>(s, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status, prices);
-    case 128: return launch_solve<128>(s, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status, prices);
-    case 256: return launch_solve<256>(s, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status, prices);
-    default: return launch_solve<512>(s, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status, prices);
+    case 64: k_batch_solve<64><<<grid, 64, smem, s>>>(args, slots); break;
+    case 128: k_batch_solve<128><<<grid, 128, smem, s>>>(args, slots); break;
+    case 256: k_batch_solve<256><<<grid, 256, smem, s>>>(args, slots); break;
+    case 512: k_batch_solve<512><<<grid, 512, smem, s>>>(args, slots); break;
+    default: k_batch_solve<1024><<<grid, 1024, smem, s>>>(args, slots); break;
     }
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -475,11 +652,11 @@ cudaError_t enqueue(cudaStream_t s, int block, int grid, size_t smem, const int3
 static la_status batched_locked(const int32_t *cost, const int64_t *offsets, const int32_t *ns, int32_t B,
                                 const la_batch_options *opt, cudaStream_t s, int32_t *match_out,
                                 int64_t *cost_out, int32_t *status_out, la_batch_stats *st) {
-    const int block = (opt && opt->block_threads) ? opt->block_threads : 128;
+    const int block = (opt && opt->block_threads) ? opt->block_threads : 512;
     const int max_n = (opt && opt->max_n) ? opt->max_n : LA_BATCH_MAX_N;
     const bool graph = !(opt && opt->no_graph);
     int64_t *prices = opt ? opt->prices_out : nullptr;
-    if (block != 64 && block != 128 && block != 256 && block != 512) return LA_ERR_INVALID;
+    if (block != 64 && block != 128 && block != 256 && block != 512 && block != 1024) return LA_ERR_INVALID;
     if (max_n < 1 || max_n > LA_BATCH_MAX_N) return LA_ERR_INVALID;
     BatchParams P;
     for (int k = 0; k < LA_ALPHA_BUCKETS; ++k) {
@@ -497,15 +674,35 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
     BatchWorkspace &w = g_bws[dev];
     if (la_status e = ensure_bws(w, B, max_n)) return e;
     int *status = status_out ? status_out : w.status;
-    const size_t smem = sizeof(unsigned long long) * (size_t)max_n;
+    // instances resident per CTA, bounded by the shared memory their keys take
+    int slots = (opt && opt->slots > 0) ? opt->slots : kDefaultSlots;
+    slots = std::min(slots, kMaxSlots);
+    slots = std::max(1, std::min(slots, (int)(kSlotSmemBudget / (sizeof(unsigned long long) * (size_t)max_n))));
+    const size_t smem = sizeof(unsigned long long) * (size_t)max_n * slots;
     int grid = 0;
     switch (block) {
     case 64: grid = solve_grid<64>(w.num_sms, smem); break;
     case 128: grid = solve_grid<128>(w.num_sms, smem); break;
     case 256: grid = solve_grid<256>(w.num_sms, smem); break;
-    default: grid = solve_grid<512>(w.num_sms, smem); break;
+    case 512: grid = solve_grid<512>(w.num_sms, smem); break;
+    default: grid = solve_grid<1024>(w.num_sms, smem); break;
     }
-    grid = std::max(1, std::min(grid, (int)B));
+    grid = std::max(1, std::min(grid, (int)((B + slots - 1) / slots)));
+    BatchArgs args;
+    args.C = cost;
+    args.offsets = reinterpret_cast<const long long *>(offsets);
+    args.ns = ns;
+    args.order = w.order;
+    args.moff = w.moff;
+    args.cminmax = w.cminmax;
+    args.B = B;
+    args.max_n = max_n;
+    args.P = P;
+    args.match_out = match_out;
+    args.cost_out = reinterpret_cast<long long *>(cost_out);
+    args.inst_status = status;
+    args.ctrl = w.ctrl;
+    args.prices_out = reinterpret_cast<long long *>(prices);
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool profile = opt && opt->profile;
@@ -528,6 +725,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
         key.B = B;
         key.block = block;
         key.max_n = max_n;
+        key.slots = slots;
         key.stream = s;
         key.P = P;
         if (!(w.have_key && w.key == key && w.exec)) {
@@ -537,8 +735,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
             cudaGraph_t g = nullptr;
             cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (ce == cudaSuccess) {
-                const cudaError_t le = enqueue(cs, block, grid, smem, cost, offsets, ns, w, B, max_n, P,
-                                               match_out, cost_out, status, prices);
+                const cudaError_t le = enqueue(cs, block, grid, smem, slots, args, w.hist, w.num_sms);
                 ce = cudaStreamEndCapture(cs, &g);
                 if (le != cudaSuccess) ce = le;
             }
@@ -555,8 +752,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
         LA_BCK(cudaGraphLaunch(w.exec, s));
         launched_graph = true;
     } else {
-        LA_BCK(enqueue(s, block, grid, smem, cost, offsets, ns, w, B, max_n, P, match_out, cost_out, status,
-                       prices));
+        LA_BCK(enqueue(s, block, grid, smem, slots, args, w.hist, w.num_sms));
     }
     if (profile) LA_BCK(cudaEventRecord(e1, s));
     LA_BCK(cudaMemcpyAsync(w.h_ctrl, w.ctrl, sizeof(BatchCtrl), cudaMemcpyDeviceToHost, s));
@@ -573,6 +769,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
         st->max_n = c.max_n;
         st->grid = grid;
         st->block_threads = block;
+        st->slots = slots;
         st->graph = launched_graph;
         if (profile) {
             float ms = 0;

@@ -73,6 +73,13 @@ struct Ctrl {
     int pu_abort;                    // sweeps did not settle: no update
 };
 
+// Global nanosecond timer (bounds every wait in the kernels).
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // --- loads ---------------------------------------------------------------
 
 // Cost rows are read once per scan and never written: non-coherent path,
@@ -88,6 +95,14 @@ __device__ __forceinline__ int ld_row1(const int *p) {
     int r;
     asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(r) : "l"(p));
     return r;
+}
+
+// Asks L2 for every 128-byte line of an n-int row (one line per 32 ints,
+// spread over the warp's lanes), so that the scan's own dependent loads
+// wait on L2 rather than on HBM. A hint: nothing is read into registers.
+__device__ __forceinline__ void prefetch_row_l2(const int32_t *crow, int n, int lane) {
+    for (int b = lane * 32; b < n; b += 32 * 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(crow + b));
+    if (lane == 0 && n > 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(crow + n - 1));
 }
 
 // Prices are written by other SMs during the scan. Reading them at L2

@@ -610,12 +610,6 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
 constexpr unsigned kLabelInf = 0x7fffffffu;
 constexpr unsigned kMaxPuLevel = 2048;
 
-__device__ __forceinline__ unsigned long long global_timer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // Barrier of a co-resident grid. A wait longer than 2 s sets
 // LA_ERR_INTERNAL and returns false instead of spinning on.
 __device__ bool pu_grid_sync(Ctrl *ctrl, int *s_ok) {
@@ -629,10 +623,10 @@ __device__ bool pu_grid_sync(Ctrl *ctrl, int *s_ok) {
             __threadfence();
             atomicAdd(&ctrl->pu_bar[1], 1u);
         } else {
-            const unsigned long long t0 = global_timer();
+            const unsigned long long t0 = global_timer_ns();
             while (*gen == g) {
                 __nanosleep(64);
-                if (global_timer() - t0 > 2000000000ull) {
+                if (global_timer_ns() - t0 > 2000000000ull) {
                     atomicCAS(&ctrl->status, 0, (int)LA_ERR_INTERNAL);
                     *s_ok = 0;
                     break;

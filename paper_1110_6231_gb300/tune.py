@@ -5,8 +5,9 @@ It picks, by measurement on the caller's own batch (or a sample of it):
 * alpha per size bucket (bucket k holds 2^k <= n < 2^(k+1)). alpha is the
   divisor of eps between refine phases (Algorithm 5.0; the paper uses 10):
   a larger alpha means fewer phases with more bidding each.
-* the CTA size, i.e. how many warps bid concurrently on one instance (rows
-  in flight per CTA).
+* the CTA shape: its size (warps that bid concurrently) and how many
+  instances it keeps resident (slots); its warps take free rows from any
+  resident instance.
 * the shared-memory key capacity ``max_n`` (the largest n in the batch), which
   sets how many CTAs fit on an SM.
 
@@ -22,7 +23,7 @@ import json
 import paper_1110_6231_gb300 as la
 
 DEFAULT_ALPHAS = (4, 6, 8, 10, 16)
-DEFAULT_BLOCKS = (64, 128, 256)
+DEFAULT_SHAPES = ((256, 2), (512, 2), (512, 4), (1024, 8))   # (threads per CTA, resident instances)
 
 
 def _bucket(n: int) -> int:
@@ -45,14 +46,14 @@ def _time(costs, offsets, ns, opt, reps):
     return best
 
 
-def autotune_batched(costs, offsets, ns, *, alphas=DEFAULT_ALPHAS, blocks=DEFAULT_BLOCKS,
+def autotune_batched(costs, offsets, ns, *, alphas=DEFAULT_ALPHAS, shapes=DEFAULT_SHAPES,
                      per_bucket: int = 0, reps: int = 2, seed: int = 0) -> dict:
     """Tune on CUDA tensors (int32 costs, int64 offsets, int32 ns).
 
     Each bucket's alpha is timed on that bucket's instances (all of them, or
     a sample of ``per_bucket`` when it is > 0): a bucket's sub-batch must be
     large enough to fill the GPU for its timing to reflect throughput. The
-    CTA size is then timed on the union of the samples with the tuned alphas.
+    CTA shape is then timed on the union of the samples with the tuned alphas.
     """
     import numpy as np
     import torch
@@ -76,7 +77,7 @@ def autotune_batched(costs, offsets, ns, *, alphas=DEFAULT_ALPHAS, blocks=DEFAUL
         sub_ns = torch.from_numpy(ns_h[idx]).to(costs.device)
         res = {}
         for a in alphas:
-            opt = la.batch_options(block_threads=128 if b >= 7 else 64, max_n=max_n, alpha=int(a), no_graph=True,
+            opt = la.batch_options(block_threads=512, slots=4, max_n=max_n, alpha=int(a), no_graph=True,
                                    profile=True)
             res[int(a)] = _time(costs, sub_off, sub_ns, opt, reps)
         alpha_tab[b] = min(res, key=res.get)
@@ -84,19 +85,19 @@ def autotune_batched(costs, offsets, ns, *, alphas=DEFAULT_ALPHAS, blocks=DEFAUL
     idx = np.array(sorted(sample_all))
     sub_off = torch.from_numpy(off_h[idx]).to(costs.device)
     sub_ns = torch.from_numpy(ns_h[idx]).to(costs.device)
-    for blk in blocks:
-        opt = la.batch_options(block_threads=int(blk), max_n=max_n, alpha=alpha_tab, no_graph=True,
-                               profile=True)
-        timings["block"][int(blk)] = _time(costs, sub_off, sub_ns, opt, reps)
-    block = min(timings["block"], key=timings["block"].get)
-    return {"block_threads": int(block), "max_n": max_n, "alpha": [int(a) for a in alpha_tab],
+    for blk, slots in shapes:
+        opt = la.batch_options(block_threads=int(blk), slots=int(slots), max_n=max_n, alpha=alpha_tab,
+                               no_graph=True, profile=True)
+        timings["block"][(int(blk), int(slots))] = _time(costs, sub_off, sub_ns, opt, reps)
+    block, slots = min(timings["block"], key=timings["block"].get)
+    return {"block_threads": int(block), "slots": int(slots), "max_n": max_n, "alpha": [int(a) for a in alpha_tab],
             "timings_ms": {"alpha": {str(k): v for k, v in timings["alpha"].items()},
-                           "block": {str(k): v for k, v in timings["block"].items()}}}
+                           "shape": {f"{b}x{s}": v for (b, s), v in timings["block"].items()}}}
 
 
 def options_from_table(table: dict, **extra) -> "la.la_batch_options":
-    return la.batch_options(block_threads=table["block_threads"], max_n=table["max_n"],
-                            alpha=table["alpha"], **extra)
+    return la.batch_options(block_threads=table["block_threads"], slots=table.get("slots", 0),
+                            max_n=table["max_n"], alpha=table["alpha"], **extra)
 
 
 def save_table(path: str, table: dict) -> None:

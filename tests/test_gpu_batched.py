@@ -70,16 +70,29 @@ def test_mixed_small_batch(la):
     verify(flat, off, ns, sol)
 
 
-@pytest.mark.parametrize("block", [64, 128, 256, 512])
-def test_block_sizes_and_no_graph(la, block):
+@pytest.mark.parametrize("block,slots", [(64, 1), (128, 2), (256, 4), (512, 8), (1024, 3), (512, 0)])
+def test_cta_shapes_and_no_graph(la, block, slots):
+    """Every CTA shape (threads x resident instances, more slots than warps
+    included) gives the oracle's costs, launched directly or from a graph."""
     flat, off, ns = synth.batch(40, 7, lo=16, hi=400)
     expected = [oracle.cost_scaling(flat[off[i]:off[i] + int(ns[i]) ** 2].reshape(int(ns[i]), int(ns[i])))[0]
                 for i in range(len(ns))]
     for no_graph in (False, True):
-        sol = run(la, flat, off, ns, block_threads=block, no_graph=no_graph, max_n=512)
+        sol = run(la, flat, off, ns, block_threads=block, slots=slots, no_graph=no_graph, max_n=512)
         assert sol.stats["rc"] == 0
         assert sol.stats["graph"] == (0 if no_graph else 1)
+        assert sol.stats["slots"] == (slots or 4)
         verify(flat, off, ns, sol, expected)
+
+
+def test_slots_bounded_by_shared_memory(la):
+    """Eight slots of max_n = 8192 keys would need 512 KB: the launch keeps
+    as many as fit in 192 KB (three) and still solves a large instance."""
+    inst = [synth.uniform_costs(n, 0, 1000, n) for n in (2000, 700, 5)]
+    flat, off, ns = pack(inst)
+    sol = run(la, flat, off, ns, slots=8, max_n=8192)
+    assert sol.stats["rc"] == 0 and sol.stats["slots"] == 3
+    verify(flat, off, ns, sol)
 
 
 def test_batch_workload_sample_and_graph_replay(la):
