@@ -16,6 +16,9 @@ builds it with gcc on first use and marshals numpy arrays. Functions:
   push/relabel taken as the Goldberg-Kennedy double push, on costs scaled by
   n + 1.
 * ``check_matching``, ``check_duals``, ``check_eps_cs`` -- certificates.
+* ``sparse_brute_force``, ``sparse_ssp`` and ``sparse_check_*`` -- the same
+  problem on a sparse bipartite graph given by its arcs in CSR form
+  (``row_ptr, cols, costs``); ``INFEASIBLE`` when it has no perfect matching.
 """
 
 from __future__ import annotations
@@ -33,7 +36,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-OK, INVALID, INVARIANT, OVERFLOW, NOMEM = 0, 1, 2, 3, 4
+OK, INVALID, INVARIANT, OVERFLOW, NOMEM, INFEASIBLE = 0, 1, 2, 3, 4, 5
 
 
 class OracleError(RuntimeError):
@@ -64,8 +67,15 @@ def _load():
             lib.or_check_matching.argtypes = [P, i32, P, i64]
             lib.or_check_duals.argtypes = [P, i32, P, P, P]
             lib.or_check_eps_cs.argtypes = [P, i32, P, P, i64]
+            lib.or_sparse_brute_force.argtypes = [i32, P, P, P, P, P]
+            lib.or_sparse_ssp.argtypes = [i32, P, P, P, P, P, P, P]
+            lib.or_sparse_check_matching.argtypes = [i32, P, P, P, P, i64]
+            lib.or_sparse_check_duals.argtypes = [i32, P, P, P, P, P, P]
+            lib.or_sparse_check_eps_cs.argtypes = [i32, P, P, P, P, P, i64]
             for f in (lib.or_brute_force, lib.or_hungarian, lib.or_cost_scaling,
-                      lib.or_check_matching, lib.or_check_duals, lib.or_check_eps_cs):
+                      lib.or_check_matching, lib.or_check_duals, lib.or_check_eps_cs,
+                      lib.or_sparse_brute_force, lib.or_sparse_ssp, lib.or_sparse_check_matching,
+                      lib.or_sparse_check_duals, lib.or_sparse_check_eps_cs):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -164,3 +174,70 @@ def eps_schedule(Ct: int, alpha: int = 10, eps0: int = 0, final_eps: int = 1):
         out.append(eps)
         if eps <= final_eps:
             return out
+
+
+# ---------------------------------------------------------------- sparse graphs
+
+class Infeasible(OracleError):
+    """The graph has no perfect matching."""
+
+
+def _csr(row_ptr, cols, costs):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    costs = np.ascontiguousarray(costs, dtype=np.int32)
+    if row_ptr.ndim != 1 or row_ptr.size < 1 or cols.shape != costs.shape:
+        raise ValueError("bad CSR arrays")
+    return row_ptr.size - 1, row_ptr, cols, costs
+
+
+def sparse_brute_force(row_ptr, cols, costs):
+    """Min over permutations made of arcs (n <= 10). Returns ``(cost, match)``;
+    raises ``Infeasible`` when there is none."""
+    n, rp, cc, cs = _csr(row_ptr, cols, costs)
+    match = np.zeros(max(n, 1), dtype=np.int32)
+    cost = np.zeros(1, dtype=np.int64)
+    rc = _load().or_sparse_brute_force(n, _ptr(rp), _ptr(cc), _ptr(cs), _ptr(match), _ptr(cost))
+    if rc == INFEASIBLE:
+        raise Infeasible("no perfect matching")
+    if rc:
+        raise OracleError(f"or_sparse_brute_force returned {rc}")
+    return int(cost[0]), match[:n]
+
+
+def sparse_ssp(row_ptr, cols, costs):
+    """Successive shortest paths with integer duals. Returns
+    ``(cost, match, u, v)``; raises ``Infeasible`` when the graph has no
+    perfect matching."""
+    n, rp, cc, cs = _csr(row_ptr, cols, costs)
+    match = np.zeros(max(n, 1), dtype=np.int32)
+    cost = np.zeros(1, dtype=np.int64)
+    u = np.zeros(max(n, 1), dtype=np.int64)
+    v = np.zeros(max(n, 1), dtype=np.int64)
+    rc = _load().or_sparse_ssp(n, _ptr(rp), _ptr(cc), _ptr(cs), _ptr(match), _ptr(cost), _ptr(u), _ptr(v))
+    if rc == INFEASIBLE:
+        raise Infeasible("no perfect matching")
+    if rc:
+        raise OracleError(f"or_sparse_ssp returned {rc}")
+    return int(cost[0]), match[:n], u[:n], v[:n]
+
+
+def sparse_check_matching(row_ptr, cols, costs, match, claimed_cost) -> int:
+    n, rp, cc, cs = _csr(row_ptr, cols, costs)
+    m = np.ascontiguousarray(match, dtype=np.int32)
+    return _load().or_sparse_check_matching(n, _ptr(rp), _ptr(cc), _ptr(cs), _ptr(m), int(claimed_cost))
+
+
+def sparse_check_duals(row_ptr, cols, costs, match, u, v) -> int:
+    n, rp, cc, cs = _csr(row_ptr, cols, costs)
+    m = np.ascontiguousarray(match, dtype=np.int32)
+    u = np.ascontiguousarray(u, dtype=np.int64)
+    v = np.ascontiguousarray(v, dtype=np.int64)
+    return _load().or_sparse_check_duals(n, _ptr(rp), _ptr(cc), _ptr(cs), _ptr(m), _ptr(u), _ptr(v))
+
+
+def sparse_check_eps_cs(row_ptr, cols, costs, match, prices, eps: int = 1) -> int:
+    n, rp, cc, cs = _csr(row_ptr, cols, costs)
+    m = np.ascontiguousarray(match, dtype=np.int32)
+    p = np.ascontiguousarray(prices, dtype=np.int64)
+    return _load().or_sparse_check_eps_cs(n, _ptr(rp), _ptr(cc), _ptr(cs), _ptr(m), _ptr(p), int(eps))

@@ -26,7 +26,9 @@
  *                     of Algorithm 5.2 (unmatch all, p(x) implicit), and the
  *                     push/relabel step of Algorithm 5.4 taken as the
  *                     Goldberg-Kennedy double push (the paper's reference [9]).
- * and certificate checkers for any claimed matching.
+ * and certificate checkers for any claimed matching. The same problem on
+ * sparse bipartite graphs (arcs in CSR form) has its own brute force,
+ * successive-shortest-path solver and checkers (or_sparse_*, below).
  *
  * All arithmetic is exact int64.
  */
@@ -334,6 +336,215 @@ int or_check_eps_cs(const int32_t *C, int32_t n, const int32_t *match,
         }
         const int64_t mine = np1 * (int64_t)row[match[x]] - p[match[x]];
         if (mine > mn + eps) return 15;
+    }
+    return OR_OK;
+}
+
+/* ================================================================== */
+/* Sparse bipartite graphs.                                            */
+/*                                                                     */
+/* The paper's implementation takes arbitrary bipartite graphs (Sect.  */
+/* 1 and Sect. 6), not only complete ones. A graph on rows 0..n-1 and  */
+/* columns 0..n-1 is given by its arcs in CSR form: row x's arcs are   */
+/* k = row_ptr[x] .. row_ptr[x+1]-1, to column cols[k] at cost         */
+/* costs[k]. A row may list the same column twice (parallel arcs: the  */
+/* cheaper one is the one a matching would use). The problem: a        */
+/* perfect matching that uses arcs only and minimises its total cost,  */
+/* or OR_INFEASIBLE when the graph has no perfect matching.            */
+/* ================================================================== */
+#define OR_INFEASIBLE 5
+
+static int sp_valid(int32_t n, const int32_t *row_ptr, const int32_t *cols)
+{
+    if (n < 0 || (n > 0 && (!row_ptr || row_ptr[0] != 0))) return 0;
+    for (int32_t x = 0; x < n; ++x) {
+        if (row_ptr[x + 1] < row_ptr[x]) return 0;
+        for (int32_t k = row_ptr[x]; k < row_ptr[x + 1]; ++k)
+            if (cols[k] < 0 || cols[k] >= n) return 0;
+    }
+    return 1;
+}
+
+/* Cheapest arc x -> y, or OR_INF when there is none. */
+static int64_t sp_arc(const int32_t *row_ptr, const int32_t *cols, const int32_t *costs,
+                      int32_t x, int32_t y)
+{
+    int64_t best = OR_INF;
+    for (int32_t k = row_ptr[x]; k < row_ptr[x + 1]; ++k)
+        if (cols[k] == y && costs[k] < best) best = costs[k];
+    return best;
+}
+
+/* Brute force: every permutation of the columns, kept only if each of its
+ * pairs is an arc (n <= 10). */
+int or_sparse_brute_force(int32_t n, const int32_t *row_ptr, const int32_t *cols,
+                          const int32_t *costs, int32_t *match, int64_t *cost)
+{
+    if (n < 0 || n > 10 || !cost || (n > 0 && !match) || !sp_valid(n, row_ptr, cols)) return OR_INVALID;
+    if (n == 0) { *cost = 0; return OR_OK; }
+    int32_t perm[10], cnt[10];
+    int64_t w[10][10];
+    for (int x = 0; x < n; ++x)
+        for (int y = 0; y < n; ++y) w[x][y] = sp_arc(row_ptr, cols, costs, x, y);
+    for (int i = 0; i < n; ++i) { perm[i] = i; cnt[i] = 0; }
+    int64_t best = OR_INF;
+    for (;;) {
+        int64_t s = 0;
+        for (int x = 0; x < n && s < OR_INF; ++x) s = w[x][perm[x]] >= OR_INF ? OR_INF : s + w[x][perm[x]];
+        if (s < best) { best = s; for (int x = 0; x < n; ++x) match[x] = perm[x]; }
+        int i = 1;                      /* next permutation (Heap's algorithm) */
+        while (i < n && cnt[i] >= i) { cnt[i] = 0; ++i; }
+        if (i >= n) break;
+        int j = (i % 2 == 0) ? 0 : cnt[i];
+        int32_t t = perm[j]; perm[j] = perm[i]; perm[i] = t;
+        cnt[i]++;
+    }
+    if (best >= OR_INF) return OR_INFEASIBLE;
+    *cost = best;
+    return OR_OK;
+}
+
+/* Successive shortest augmenting paths on the arcs (the sparse form of
+ * or_hungarian; not from the paper, an independent ground truth). Rows
+ * enter one at a time; a Dijkstra search over columns with reduced costs
+ * c(x,y) - u(x) - v(y) >= 0 on arcs finds the cheapest alternating path
+ * from the entering row to a free column; the duals move by the search
+ * distances and the path is flipped. If no free column can be reached the
+ * graph has no perfect matching (the search has found a set of rows whose
+ * arcs reach fewer columns: Hall's condition fails). Integer duals u, v
+ * (optional) certify the result: u(x) + v(y) <= c(x,y) on every arc, with
+ * equality on the matching. */
+int or_sparse_ssp(int32_t n, const int32_t *row_ptr, const int32_t *cols, const int32_t *costs,
+                  int32_t *match, int64_t *cost, int64_t *u_out, int64_t *v_out)
+{
+    if (!cost || (n > 0 && !match) || !sp_valid(n, row_ptr, cols)) return OR_INVALID;
+    if (n == 0) { *cost = 0; return OR_OK; }
+    int64_t *u = calloc((size_t)n, sizeof(int64_t));
+    int64_t *v = calloc((size_t)n, sizeof(int64_t));
+    int64_t *dist = malloc(sizeof(int64_t) * n);
+    int32_t *owner = malloc(sizeof(int32_t) * n);   /* row matched to column y */
+    int32_t *from = malloc(sizeof(int32_t) * n);    /* column before y on the path, -1 = root row */
+    char *done = malloc((size_t)n);
+    if (!u || !v || !dist || !owner || !from || !done) {
+        free(u); free(v); free(dist); free(owner); free(from); free(done);
+        return OR_NOMEM;
+    }
+    for (int32_t y = 0; y < n; ++y) owner[y] = -1;
+    int rc = OR_OK;
+    for (int32_t r = 0; r < n && rc == OR_OK; ++r) {
+        for (int32_t y = 0; y < n; ++y) { dist[y] = OR_INF; done[y] = 0; from[y] = -1; }
+        /* the entering row's arcs; u(r) = 0 before the search */
+        u[r] = 0;
+        for (int32_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+            const int64_t red = (int64_t)costs[k] - u[r] - v[cols[k]];
+            if (red < dist[cols[k]]) { dist[cols[k]] = red; from[cols[k]] = -1; }
+        }
+        int32_t yfree = -1;
+        int64_t dfree = 0;
+        for (;;) {
+            int32_t y = -1;
+            int64_t dmin = OR_INF;
+            for (int32_t j = 0; j < n; ++j)
+                if (!done[j] && dist[j] < dmin) { dmin = dist[j]; y = j; }
+            if (y < 0) { rc = OR_INFEASIBLE; break; }
+            done[y] = 1;
+            if (owner[y] < 0) { yfree = y; dfree = dmin; break; }
+            const int32_t x = owner[y];          /* continue through y's row */
+            for (int32_t k = row_ptr[x]; k < row_ptr[x + 1]; ++k) {
+                const int32_t j = cols[k];
+                if (done[j]) continue;
+                const int64_t red = dmin + (int64_t)costs[k] - u[x] - v[j];
+                if (red < dist[j]) { dist[j] = red; from[j] = y; }
+            }
+        }
+        if (rc != OR_OK) break;
+        /* dual update: settled columns move by (dfree - dist), their rows too */
+        u[r] += dfree;
+        for (int32_t j = 0; j < n; ++j) {
+            if (!done[j] || j == yfree) continue;
+            const int64_t d = dfree - dist[j];
+            v[j] -= d;
+            u[owner[j]] += d;
+        }
+        /* flip the path: yfree <- ... <- root row r */
+        int32_t y = yfree;
+        while (from[y] >= 0) {
+            const int32_t yp = from[y];
+            owner[y] = owner[yp];
+            y = yp;
+        }
+        owner[y] = r;
+    }
+    if (rc == OR_OK) {
+        int64_t total = 0;
+        for (int32_t y = 0; y < n; ++y) {
+            match[owner[y]] = y;
+            total += sp_arc(row_ptr, cols, costs, owner[y], y);
+        }
+        *cost = total;
+        if (u_out) memcpy(u_out, u, sizeof(int64_t) * n);
+        if (v_out) memcpy(v_out, v, sizeof(int64_t) * n);
+    }
+    free(u); free(v); free(dist); free(owner); free(from); free(done);
+    return rc;
+}
+
+/* match is a permutation made of arcs and its cost (cheapest parallel arc)
+ * equals claimed. */
+int or_sparse_check_matching(int32_t n, const int32_t *row_ptr, const int32_t *cols,
+                             const int32_t *costs, const int32_t *match, int64_t claimed)
+{
+    if (!sp_valid(n, row_ptr, cols)) return OR_INVALID;
+    char *seen = calloc((size_t)(n > 0 ? n : 1), 1);
+    if (!seen) return OR_NOMEM;
+    int64_t total = 0;
+    int rc = OR_OK;
+    for (int32_t x = 0; x < n && rc == OR_OK; ++x) {
+        const int32_t y = match[x];
+        if (y < 0 || y >= n || seen[y]) { rc = 11; break; }
+        seen[y] = 1;
+        const int64_t c = sp_arc(row_ptr, cols, costs, x, y);
+        if (c >= OR_INF) { rc = 12; break; }
+        total += c;
+    }
+    free(seen);
+    if (rc == OR_OK && total != claimed) rc = 13;
+    return rc;
+}
+
+/* LP duality certificate on the arcs: u(x) + v(y) <= c(x,y) on every arc,
+ * equality on the matching; then sum u + sum v = cost(match) is optimal. */
+int or_sparse_check_duals(int32_t n, const int32_t *row_ptr, const int32_t *cols,
+                          const int32_t *costs, const int32_t *match,
+                          const int64_t *u, const int64_t *v)
+{
+    if (!sp_valid(n, row_ptr, cols)) return OR_INVALID;
+    for (int32_t x = 0; x < n; ++x)
+        for (int32_t k = row_ptr[x]; k < row_ptr[x + 1]; ++k)
+            if (u[x] + v[cols[k]] > (int64_t)costs[k]) return 14;
+    for (int32_t x = 0; x < n; ++x)
+        if (u[x] + v[match[x]] != sp_arc(row_ptr, cols, costs, x, match[x])) return 16;
+    return OR_OK;
+}
+
+/* eps-complementary slackness of every row on costs scaled by n + 1, over
+ * its arcs: (n+1) c(x,M(x)) - p(M(x)) <= min over arcs (n+1) c(x,y) - p(y)
+ * + eps. At eps = 1 it proves the matching optimal (Sect. 5.1, Lemma 5.6:
+ * summed over the rows, (n+1) cost <= (n+1) OPT + n). */
+int or_sparse_check_eps_cs(int32_t n, const int32_t *row_ptr, const int32_t *cols,
+                           const int32_t *costs, const int32_t *match, const int64_t *p, int64_t eps)
+{
+    if (!sp_valid(n, row_ptr, cols)) return OR_INVALID;
+    const int64_t np1 = (int64_t)n + 1;
+    for (int32_t x = 0; x < n; ++x) {
+        int64_t mn = OR_INF;
+        for (int32_t k = row_ptr[x]; k < row_ptr[x + 1]; ++k) {
+            const int64_t cp = np1 * (int64_t)costs[k] - p[cols[k]];
+            if (cp < mn) mn = cp;
+        }
+        const int64_t c = sp_arc(row_ptr, cols, costs, x, match[x]);
+        if (c >= OR_INF) return 12;
+        if (np1 * c - p[match[x]] > mn + eps) return 15;
     }
     return OR_OK;
 }

@@ -23,6 +23,11 @@ motivating application, optical flow by assignment (Sect. 1):
   ``round_half_even(scale * |a_i - b_j|^2)``.
 * ``batch``           -- many independent instances of uneven size,
   ``n = floor(exp(U(ln lo, ln hi)))``, half uniform and half geometric.
+* ``sparse_uniform``, ``sparse_geometric`` -- sparse bipartite graphs (the
+  paper's implementation takes arbitrary bipartite graphs, Sect. 1 and
+  Sect. 6) in CSR form ``(row_ptr, cols, costs)``, each with a planted
+  perfect matching: random arcs with uniform costs, and the optical-flow
+  points linked to the targets in their 3 x 3 grid neighbourhood.
 """
 
 from __future__ import annotations
@@ -41,7 +46,11 @@ __all__ = [
     "batch_sizes",
     "batch",
     "instance",
+    "sparse_uniform",
+    "sparse_geometric",
+    "sparse_instance",
     "WORKLOADS",
+    "SPARSE_WORKLOADS",
 ]
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -54,6 +63,8 @@ _TAG_POINTS = 2
 _TAG_PERM = 3
 _TAG_JITTER = 4
 _TAG_SIZES = 5
+_TAG_ARCS = 6
+_TAG_ARC_COSTS = 7
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -253,3 +264,94 @@ def instance(name: str, seed: int, n: int | None = None) -> np.ndarray:
     if w["kind"] == "uniform":
         return uniform_costs(nn, w["lo"], w["hi"], seed)
     return geometric_costs(nn, seed)
+
+
+# ---------------------------------------------------------------- sparse graphs
+
+def _csr_from_pairs(n: int, rows: np.ndarray, cols: np.ndarray):
+    """Sorted, duplicate-free arcs (row-major order) and their row offsets."""
+    key = np.unique(rows.astype(np.int64) * n + cols.astype(np.int64))
+    r = (key // n).astype(np.int64)
+    c = (key % n).astype(np.int32)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, r + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    if row_ptr[-1] >= (1 << 31):
+        raise ValueError("too many arcs for int32 offsets")
+    return row_ptr.astype(np.int32), c, r
+
+
+def sparse_uniform(n: int, degree: int, seed: int, lo: int = 0, hi: int = 10_000):
+    """Row x has arcs to ``degree`` uniform random columns and to its planted
+    partner ``pi(x)`` (duplicates merged), costs uniform on ``[lo, hi]``.
+    Returns ``(row_ptr, cols, costs)`` (int32)."""
+    if n < 0 or degree < 0:
+        raise ValueError("n and degree must be >= 0")
+    pi = _permutation(n, seed)
+    rnd = uniform_ints(seed, _TAG_ARCS, n * degree, 0, max(n - 1, 0)) if n else np.zeros(0, np.int64)
+    rows = np.concatenate([np.arange(n, dtype=np.int64), np.repeat(np.arange(n, dtype=np.int64), degree)])
+    cols = np.concatenate([pi, rnd.astype(np.int64)])
+    row_ptr, c, _ = _csr_from_pairs(n, rows, cols)
+    costs = uniform_ints(seed, _TAG_ARC_COSTS, c.size, lo, hi).astype(np.int32)
+    return row_ptr, c, costs
+
+
+def sparse_geometric(n: int, seed: int, sigma: float = 0.01, scale: float = 1.0e3):
+    """Optical-flow-like sparse graph: the points of ``geometric_points`` on
+    a G x G grid (G = floor(sqrt(n / 4)), about four targets per cell); row
+    i has arcs to every target b_j in the 3 x 3 cells around a_i, and to its
+    true partner (the j with pi(j) = i), at cost
+    ``rint(scale * (G |a_i - b_j|)^2)`` (distances in units of a cell).
+    Returns ``(row_ptr, cols, costs)`` (int32)."""
+    if n < 0:
+        raise ValueError("n must be >= 0")
+    a, pi, b = geometric_points(n, seed, sigma)
+    G = max(1, math.isqrt(n // 4))
+
+    def cell(p):
+        q = np.floor(np.clip(p, 0.0, 1.0) * G).astype(np.int64)
+        return np.minimum(q, G - 1)
+
+    bcx, bcy = cell(b[:, 0]), cell(b[:, 1])
+    bcell = bcy * G + bcx
+    order = np.argsort(bcell, kind="stable")
+    counts = np.bincount(bcell, minlength=G * G)
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    acx, acy = cell(a[:, 0]), cell(a[:, 1])
+    rows_l, cols_l = [], []
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            nx, ny = acx + dx, acy + dy
+            ok = (nx >= 0) & (nx < G) & (ny >= 0) & (ny < G)
+            rr = np.nonzero(ok)[0]
+            cc = (ny[rr] * G + nx[rr])
+            k = counts[cc]
+            rep = np.repeat(rr, k)
+            first = np.repeat(starts[cc], k)
+            within = np.arange(rep.size) - np.repeat(np.cumsum(k) - k, k)
+            rows_l.append(rep)
+            cols_l.append(order[first + within])
+    inv = np.empty(n, dtype=np.int64)
+    inv[pi] = np.arange(n, dtype=np.int64)
+    rows_l.append(np.arange(n, dtype=np.int64))
+    cols_l.append(inv)
+    row_ptr, c, r = _csr_from_pairs(n, np.concatenate(rows_l), np.concatenate(cols_l))
+    dx = (a[r, 0] - b[c, 0]) * G
+    dy = (a[r, 1] - b[c, 1]) * G
+    costs = np.rint((dx * dx + dy * dy) * scale).astype(np.int32)
+    return row_ptr, c, costs
+
+
+# Named sparse workloads (n, kind, degree).
+SPARSE_WORKLOADS = {
+    "sparse-uniform-n65536-d32": dict(kind="uniform", n=65536, degree=32),
+    "sparse-geometric-n65536": dict(kind="geometric", n=65536),
+}
+
+
+def sparse_instance(name: str, seed: int, n: int | None = None):
+    w = SPARSE_WORKLOADS[name]
+    n = w["n"] if n is None else n
+    if w["kind"] == "uniform":
+        return sparse_uniform(n, w["degree"], seed)
+    return sparse_geometric(n, seed)

@@ -69,6 +69,62 @@ def run_all_pins(orc):
             assert st["phases"] == len(orc.eps_schedule(Ct))
 
 
+def _sparse_fixture(path):
+    lines = [l for l in open(path) if l.strip() and not l.startswith("#")]
+    c = lines[0].split()[1]
+    cost = None if c == "infeasible" else int(c)
+    n = int(lines[2].split()[1])
+    arcs = sorted((tuple(int(t) for t in l.split()) for l in lines[4:]), key=lambda a: a[0])
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    for r, _, _ in arcs:
+        row_ptr[r + 1] += 1
+    return (np.cumsum(row_ptr).astype(np.int32), np.array([a[1] for a in arcs], dtype=np.int32),
+            np.array([a[2] for a in arcs], dtype=np.int32)), cost
+
+
+def run_sparse_pins(orc):
+    from paper_1110_6231_gb300 import synth
+    for path in sorted(glob.glob(os.path.join(HERE, "golden", "sparse", "*.txt"))):
+        (rp, cols, costs), cost = _sparse_fixture(path)
+        for solve in (orc.sparse_brute_force, orc.sparse_ssp):
+            try:
+                got = solve(rp, cols, costs)[0]
+            except orc.Infeasible:
+                got = None
+            assert got == cost, path
+    rng = np.random.default_rng(6)
+    for t in range(150):
+        n = int(rng.integers(1, 7))
+        arcs = [(x, y, int(rng.integers(-20, 20))) for x in range(n) for y in range(n) if rng.random() < 0.6]
+        if t % 2 and arcs:   # parallel arcs: a matching uses the cheaper one
+            arcs += [(a[0], a[1], int(rng.integers(-20, 20))) for a in arcs[: max(1, len(arcs) // 3)]]
+        arcs.sort(key=lambda a: a[0])
+        w = {}
+        for r, c, x in arcs:
+            w[(r, c)] = min(x, w.get((r, c), x))
+        feas = [sum(w[(x, p[x])] for x in range(n)) for p in itertools.permutations(range(n))
+                if all((x, p[x]) in w for x in range(n))]
+        ref = min(feas) if feas else None
+        row_ptr = np.zeros(n + 1, dtype=np.int32)
+        for r, _, _ in arcs:
+            row_ptr[r + 1] += 1
+        rp = np.cumsum(row_ptr).astype(np.int32)
+        cols = np.array([a[1] for a in arcs], dtype=np.int32)
+        costs = np.array([a[2] for a in arcs], dtype=np.int32)
+        for solve in (orc.sparse_brute_force, orc.sparse_ssp):
+            try:
+                got = solve(rp, cols, costs)
+            except orc.Infeasible:
+                got = None
+            assert (got and got[0]) == ref if ref is not None else got is None
+            if got is not None and solve is orc.sparse_ssp:
+                assert orc.sparse_check_duals(rp, cols, costs, got[1], got[2], got[3]) == 0
+    rp, cols, costs = synth.sparse_uniform(150, 5, 2)
+    c, m, u, v = orc.sparse_ssp(rp, cols, costs)
+    assert orc.sparse_check_duals(rp, cols, costs, m, u, v) == 0
+    assert int(u.sum() + v.sum()) == c
+
+
 def main(argv):
     import oracle as orc
     if len(argv) > 1:
@@ -78,6 +134,7 @@ def main(argv):
         orc._LIB = os.path.join(tmp, "liboracle.so")
     try:
         run_all_pins(orc)
+        run_sparse_pins(orc)
     except AssertionError:
         return 1
     return 0

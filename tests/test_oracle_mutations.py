@@ -37,6 +37,14 @@ MUTANTS = [
     ("hungarian-transposed", "const int32_t *row = C + (int64_t)i * n;\n            int64_t delta",
      "const int32_t *row = C + (int64_t)i;\n            int64_t delta"),
     ("brute-force-skips-perms", "while (i < n) {", "while (i < n - 1) {"),
+    ("sparse-ssp-dual-sign", "const int64_t red = dmin + (int64_t)costs[k] - u[x] - v[j];",
+     "const int64_t red = dmin + (int64_t)costs[k] - u[x] + v[j];"),
+    ("sparse-ssp-no-row-dual", "            u[owner[j]] += d;\n", ""),
+    ("sparse-ssp-root-dual-kept", "        u[r] += dfree;\n", ""),
+    ("sparse-parallel-arc-max", "if (cols[k] == y && costs[k] < best) best = costs[k];",
+     "if (cols[k] == y && (best == OR_INF || costs[k] > best)) best = costs[k];"),
+    ("sparse-brute-force-ignores-arcs", "s = w[x][perm[x]] >= OR_INF ? OR_INF : s + w[x][perm[x]];",
+     "s = w[x][perm[x]] >= OR_INF ? s : s + w[x][perm[x]];"),
 ]
 
 
