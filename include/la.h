@@ -51,8 +51,10 @@ typedef enum {
                                refine finished (see la_options.scan_budget) */
     LA_ERR_NOMEM = 5,       /* device workspace allocation failed */
     LA_ERR_INTERNAL = 6,    /* a device-side consistency check failed */
-    LA_ERR_TOO_LARGE = 7    /* n exceeds a fixed scratch size
+    LA_ERR_TOO_LARGE = 7,   /* n exceeds a fixed scratch size
                                (la_solve_noalloc: LA_NOALLOC_MAX_N) */
+    LA_ERR_INFEASIBLE = 8   /* la_solve_sparse: the graph has no perfect
+                               matching */
 } la_status;
 
 /* Largest n accepted by the solver (the mate field of a column key is 20
@@ -332,6 +334,42 @@ la_status la_predict_prices_ex(const int32_t *cost, int32_t n, const void *weigh
  * predicted prices and eps0. Same results as la_solve. */
 la_status la_solve_warm(const int32_t *cost, int32_t n, const void *weights, void *stream,
                         int32_t *match_out, int64_t *cost_out, la_stats *stats_out);
+
+/*
+ * la_solve_sparse -- exact minimum-cost perfect matching of a sparse
+ * bipartite graph. The paper's implementation takes arbitrary bipartite
+ * graphs (Sect. 1 and Sect. 6), and Sect. 5 reduces the assignment problem
+ * to a min-cost flow on the graph's arcs (u(x,y) = 1, c(x,y) = w(x,y)); the
+ * method is the same cost scaling as la_solve (Algorithm 5.0's eps loop on
+ * costs scaled by n + 1, Algorithm 5.2's initialisation, Algorithm 5.4's
+ * push/relabel as a double push), each free row scanning only its own arcs.
+ *   row_ptr   device const int32[n+1]: row x's arcs are k = row_ptr[x] ..
+ *             row_ptr[x+1] - 1; row_ptr[0] = 0, row_ptr[n] = nnz,
+ *             non-decreasing.
+ *   cols      device const int32[nnz]: column of arc k, 0 <= cols[k] < n.
+ *             Order within a row is free; a row may list a column twice
+ *             (the cheaper arc is the one a matching uses).
+ *   costs     device const int32[nnz]: cost of arc k.
+ *   n, nnz    0 <= n <= LA_MAX_N, 0 <= nnz < 2^31.
+ *   match_out device int32[n] or NULL: match_out[x] = column of x's arc in
+ *             the matching.
+ *   cost_out  device int64[1]: the optimal total cost.
+ * Returns LA_OK; LA_ERR_INVALID for malformed CSR arrays (checked on the
+ * device before any solving); LA_ERR_INFEASIBLE when no perfect matching
+ * exists (a row or column without arcs, or a price drop in a first refine
+ * phase on zero costs beyond what a feasible graph allows: 4n + 4, against
+ * the bound (2n - 1) eps of cost scaling); else as la_solve. Blocks until
+ * the result is in place. Uses the same la_options / la_stats as
+ * la_solve_ex: alpha, eps0, prices_out, scan_budget (0 = 256 n (phases + 1)
+ * + 2^22) and profile are honoured; init_prices must be NULL. phase_scans[0]
+ * counts the feasibility phase.
+ */
+la_status la_solve_sparse(const int32_t *row_ptr, const int32_t *cols, const int32_t *costs,
+                          int32_t n, int32_t nnz, void *stream, int32_t *match_out,
+                          int64_t *cost_out);
+la_status la_solve_sparse_ex(const int32_t *row_ptr, const int32_t *cols, const int32_t *costs,
+                             int32_t n, int32_t nnz, const la_options *opt, void *stream,
+                             int32_t *match_out, int64_t *cost_out, la_stats *stats_out);
 
 /*
  * la_solve_noalloc -- la_solve for callers that must not allocate memory.

@@ -29,6 +29,7 @@ LA_ERR_ITER_LIMIT = 4
 LA_ERR_NOMEM = 5
 LA_ERR_INTERNAL = 6
 LA_ERR_TOO_LARGE = 7
+LA_ERR_INFEASIBLE = 8
 LA_MAX_N = (1 << 20) - 1
 LA_NOALLOC_MAX_N = 16384
 LA_FLAG_NO_CANDIDATE_LISTS = 1
@@ -156,6 +157,8 @@ def lib() -> ctypes.CDLL:
             L.la_solve.argtypes = [P, i32, P, P, P]
             L.la_solve_ex.argtypes = [P, i32, P, P, P, P, P]
             L.la_solve_noalloc.argtypes = [P, i32, P, P, P]
+            L.la_solve_sparse.argtypes = [P, P, P, i32, i32, P, P, P]
+            L.la_solve_sparse_ex.argtypes = [P, P, P, i32, i32, P, P, P, P, P]
             L.la_solve_batched.argtypes = [P, P, P, i32, P, P, P]
             L.la_solve_batched_ex.argtypes = [P, P, P, i32, P, P, P, P, P, P]
             L.la_predictor_param_count.argtypes = []
@@ -178,7 +181,7 @@ def lib() -> ctypes.CDLL:
             L.la_version.argtypes = []
             L.la_version.restype = i32
             for f in (L.la_solve, L.la_solve_ex, L.la_solve_noalloc, L.la_release_workspace,
-                      L.la_solve_batched, L.la_solve_batched_ex):
+                      L.la_solve_batched, L.la_solve_batched_ex, L.la_solve_sparse, L.la_solve_sparse_ex):
                 f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -218,6 +221,18 @@ def la_solve_noalloc(cost, n, stream, match_out, cost_out) -> int:
     """la_solve without any allocation: scratch is a fixed device array of the
     library (n <= LA_NOALLOC_MAX_N), for callers that cannot allocate."""
     return lib().la_solve_noalloc(_ptr(cost), int(n), _stream(stream), _ptr(match_out), _ptr(cost_out))
+
+
+def la_solve_sparse(row_ptr, cols, costs, n, nnz, stream, match_out, cost_out) -> int:
+    return lib().la_solve_sparse(_ptr(row_ptr), _ptr(cols), _ptr(costs), int(n), int(nnz), _stream(stream),
+                                 _ptr(match_out), _ptr(cost_out))
+
+
+def la_solve_sparse_ex(row_ptr, cols, costs, n, nnz, opt, stream, match_out, cost_out, stats_out) -> int:
+    return lib().la_solve_sparse_ex(_ptr(row_ptr), _ptr(cols), _ptr(costs), int(n), int(nnz),
+                                    None if opt is None else ctypes.byref(opt), _stream(stream),
+                                    _ptr(match_out), _ptr(cost_out),
+                                    None if stats_out is None else ctypes.byref(stats_out))
 
 
 def la_solve_batched(cost, offsets, ns, B, stream, match_out, cost_out) -> int:
@@ -347,6 +362,41 @@ def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bo
         raise LaError(rc, "la_solve_ex")
     return Solution(cost=int(cost.item()) if rc == LA_OK else None, match=match,
                     stats=dict(st.as_dict(), status=rc), prices=prices)
+
+
+def solve_sparse(row_ptr, cols, costs, *, alpha: int = 0, eps0: int = 0, want_prices: bool = False,
+                 scan_budget: int = 0, profile: bool = False, stream=None, check: bool = True) -> Solution:
+    """Exact minimum-cost perfect matching of a sparse bipartite graph given
+    by int32 CUDA tensors in CSR form (``row_ptr`` of length n + 1, ``cols``
+    and ``costs`` of length nnz). Raises ``LaError`` on a non-OK status when
+    ``check`` (``LA_ERR_INFEASIBLE`` when there is no perfect matching)."""
+    import torch
+    for t in (row_ptr, cols, costs):
+        if t.dtype != torch.int32 or not t.is_cuda or t.dim() != 1:
+            raise ValueError("row_ptr, cols and costs must be 1-D int32 CUDA tensors")
+    if cols.numel() != costs.numel():
+        raise ValueError("cols and costs must have the same length")
+    row_ptr, cols, costs = row_ptr.contiguous(), cols.contiguous(), costs.contiguous()
+    n = row_ptr.numel() - 1
+    if n < 0:
+        raise ValueError("row_ptr must have n + 1 entries")
+    dev = row_ptr.device
+    match = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    cost = torch.empty(1, dtype=torch.int64, device=dev)
+    prices = torch.empty(max(n, 1), dtype=torch.int64, device=dev) if want_prices else None
+    opt = la_options()
+    opt.alpha = alpha
+    opt.eps0 = eps0
+    opt.prices_out = _ptr(prices)
+    opt.scan_budget = scan_budget
+    opt.profile = int(bool(profile))
+    st = la_stats()
+    with torch.cuda.device(dev):
+        rc = la_solve_sparse_ex(row_ptr, cols, costs, n, cols.numel(), opt, stream, match, cost, st)
+    if rc != LA_OK and check:
+        raise LaError(rc, "la_solve_sparse_ex")
+    return Solution(cost=int(cost.item()) if rc == LA_OK else None, match=match[:n],
+                    stats=dict(st.as_dict(), status=rc), prices=None if prices is None else prices[:n])
 
 
 @dataclass

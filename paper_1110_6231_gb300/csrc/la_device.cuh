@@ -71,6 +71,7 @@ struct Ctrl {
     int pu_changed[3];               // a label fell in this sweep (triple buffered)
     unsigned pu_last;                // largest label of a free row
     int pu_abort;                    // sweeps did not settle: no update
+    int colseen_missing;             // sparse graphs: columns without an arc
 };
 
 // Global nanosecond timer (bounds every wait in the kernels).

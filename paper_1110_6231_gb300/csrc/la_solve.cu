@@ -1216,6 +1216,7 @@ const char *la_status_string(la_status s) {
     case LA_ERR_NOMEM: return "LA_ERR_NOMEM: device workspace allocation failed";
     case LA_ERR_INTERNAL: return "LA_ERR_INTERNAL: device consistency check failed";
     case LA_ERR_TOO_LARGE: return "LA_ERR_TOO_LARGE: n exceeds the fixed scratch size";
+    case LA_ERR_INFEASIBLE: return "LA_ERR_INFEASIBLE: the graph has no perfect matching";
     }
     return "unknown la_status";
 }

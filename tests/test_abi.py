@@ -48,7 +48,7 @@ def test_library_exports_every_declared_symbol(libla):
 def test_status_strings_without_gpu(libla):
     libla.la_status_string.restype = ctypes.c_char_p
     libla.la_status_string.argtypes = [ctypes.c_int]
-    for s in range(8):
+    for s in range(9):
         assert libla.la_status_string(s).startswith(b"LA_")
     assert libla.la_version() >= 100
 
