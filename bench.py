@@ -8,8 +8,9 @@ One step = one complete solve of one instance already resident in HBM
 matrix in L2.
 
 Prints ONE JSON line. ``value`` is solves/s over all ranks; ``roofline`` is
-the refine kernel's algorithmic arc-scan bandwidth (4 n bytes per row scan,
-counted on the device) over its CUDA-event time; ``e2e`` repeats the solve
+the dominant refine-phase kernel's algorithmic arc-scan bandwidth (4 n bytes
+per full row scan, the list bytes per candidate-list scan, counted on the
+device) over its CUDA-event time (``roofline_by_kernel`` has both kernels); ``e2e`` repeats the solve
 through the public Python API from pinned host memory with the host<->device
 copies inside the timed region; ``cpu_baseline`` times the oracle's
 sequential cost scaling on the host. ``--impl reference`` times that oracle
@@ -85,17 +86,17 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per refine launch from the committed ncu summary, if it was
-    taken on the kernel source that is built now."""
-    path = os.path.join(ROOT, "profiles", "refine_traffic.json")
+def recorded_traffic(workload, kernel):
+    """DRAM bytes (read + write) per launch of ``kernel`` from the committed
+    ncu summary, if it was taken on the kernel source that is built now."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         rec = json.load(open(path))
     except Exception:
         return None
     if rec.get("kernel_hash") != kernel_hash() or rec.get("workload") != workload:
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec.get("dram_bytes_per_launch", {}).get(kernel)
 
 
 class Clocks:
@@ -217,7 +218,10 @@ def bench_batched(args, la, synth, dev, stream):
     dc, do, dn = (torch.from_numpy(a).to(dev) for a in (flat, off, ns))
     from paper_1110_6231_gb300 import tune
     t_tune = time.perf_counter()
-    table = tune.autotune_batched(dc, do, dn, reps=1)   # CTA size and alpha per size bucket
+    if args.no_tune:   # library defaults (for profiling runs: no tuning launches first)
+        table = {"block_threads": 0, "slots": 0, "max_n": int(ns.max()), "alpha": [0] * 16}
+    else:
+        table = tune.autotune_batched(dc, do, dn, reps=1)   # CTA shape and alpha per size bucket
     t_tune = time.perf_counter() - t_tune
     opt = tune.options_from_table(table, profile=True)
     la.solve_batched(dc, do, dn, options=opt)           # capture the graph
@@ -285,6 +289,30 @@ def bench_warm(args, la, synth, dev):
         out[f"n{n}"] = {"instances": cnt, "cold_ms": 1e3 * tc / cnt, "warm_ms": 1e3 * tw / cnt,
                         "speedup": tc / tw, "cold_scans": sc / cnt, "warm_scans": sw / cnt,
                         "identical_cost": True, "warm_includes": "features + set encoder + solve"}
+    return out
+
+
+def bench_sparse(la, synth, dev, reps=2):
+    """The sparse-graph solver on the two n = 65536 workloads (planted perfect
+    matching; uniform arcs of degree 32, and the geometric neighbourhood
+    graph): best of ``reps`` solves, exact cost certified in the tests."""
+    import torch
+    out = {}
+    for name in sorted(synth.SPARSE_WORKLOADS):
+        rp, cols, costs = synth.sparse_instance(name, 0)
+        t = [torch.from_numpy(a).to(dev) for a in (rp, cols, costs)]
+        la.solve_sparse(*t)
+        best, st = None, None
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            sol = la.solve_sparse(*t, profile=True)
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t0
+            if best is None or dt < best:
+                best, st = dt, sol.stats
+        out[name] = {"ms": 1e3 * best, "arcs": int(cols.size), "scans": st["scans"], "phases": st["phases"],
+                     "max_chain": st["max_chain"], "solves_per_s": 1.0 / best}
     return out
 
 
@@ -364,21 +392,35 @@ def run_gpu(args):
     elapsed = max_over_ranks(max(wall, dev_ms / 1e3), dev)
     value = replica_throughput(args.steps, world, elapsed)
 
-    # roofline of the dominant kernel (refine): algorithmic bytes / event time.
-    # A full row scan must read the 4n-byte cost row; a candidate-list scan
-    # reads the row's list entries (column + raw cost, 8 bytes each) and
-    # its bound theta.
+    # Roofline of each refine-phase kernel from algorithmic bytes over its
+    # CUDA-event time (events on the solve's stream around the refine kernel
+    # and around the one-CTA tail kernel of every phase). A full row scan
+    # must read the 4n-byte cost row; a candidate-list scan reads the row's
+    # list entries (column + raw cost, 8 bytes each) and its bound theta.
     scans = sum(s["scans"] for s in stats)
     full = sum(s["full_scans"] for s in stats)
     listed = sum(s["list_scans"] for s in stats)
+    tail_scans = sum(s["tail_scans"] for s in stats)
+    tail_full = sum(s["tail_full_scans"] for s in stats)
     list_bytes = stats[0]["list_entries"] * 8 + 8 if stats else 0
-    refine_ms = sum(s["refine_ms"] for s in stats)
-    refine_launches = sum(s["refine_launches"] for s in stats)
+    phase_ms = sum(s["refine_ms"] for s in stats)
+    tail_ms = sum(s["tail_ms"] for s in stats)
+    phases_run = sum(s["phases"] for s in stats)
     launches = sum(s["launches"] for s in stats)
-    alg_bytes = 4.0 * n * full + list_bytes * listed
-    achieved = alg_bytes / (refine_ms * 1e-3) / 1e9
     peak, peak_src = peaks()
-    traffic = recorded_traffic(WORKLOAD)
+    per_kernel = {}
+    for kname, kfull, klist, kms in (
+            ("k_refine", full - tail_full, listed - (tail_scans - tail_full), phase_ms - tail_ms),
+            ("k_tail", tail_full, tail_scans - tail_full, tail_ms)):
+        kbytes = 4.0 * n * kfull + list_bytes * klist
+        ach = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else 0.0
+        per_kernel[kname] = {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": peak,
+                             "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak,
+                             "traffic": recorded_traffic(WORKLOAD, kname),
+                             "algorithmic_bytes_per_launch": kbytes / max(1, phases_run),
+                             "avg_launch_ms": kms / max(1, phases_run),
+                             "share_of_refine_time": kms / phase_ms if phase_ms > 0 else None}
+    dominant = max(per_kernel, key=lambda k: per_kernel[k]["avg_launch_ms"])
 
     # end to end through the public API: pinned host input, copies timed
     pinned = [torch.from_numpy(h).pin_memory() for h in host[:3]]
@@ -399,10 +441,15 @@ def run_gpu(args):
     e2e_t = max_over_ranks(time.perf_counter() - t0, dev)
 
     extra = {}
-    if not args.no_extra:
+    wanted = set() if args.no_extra else set(args.extras.split(","))
+    if "batched" in wanted:
         extra["batched"] = bench_batched(args, la, synth, dev, stream)
+    if "warm" in wanted:
         extra["warm_start"] = bench_warm(args, la, synth, dev)
+    if "geometric" in wanted:
         extra["geometric_n8192"] = bench_single(la, synth, dev, "geometric-n8192", reps=2)
+    if "sparse" in wanted:
+        extra["sparse"] = bench_sparse(la, synth, dev)
 
     line = None
     if rank == 0:
@@ -420,11 +467,8 @@ def run_gpu(args):
                        "alpha": 10, "start_prices": "zero (cold)",
                        "l2": f"{ROTATE} rotating instances ({ROTATE * 4 * n * n >> 20} MiB) > 129 MB L2",
                        "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "hbm", "kernel": "k_refine", "achieved": achieved, "peak": peak,
-                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic,
-                         "algorithmic_bytes_per_launch": alg_bytes / max(1, refine_launches),
-                         "avg_launch_ms": refine_ms / max(1, refine_launches)},
+            "roofline": per_kernel[dominant],
+            "roofline_by_kernel": per_kernel,
             "arc_scans_per_solve": scans / max(1, len(stats)),
             "full_row_scans_per_solve": full / max(1, len(stats)),
             "list_scans_per_solve": listed / max(1, len(stats)),
@@ -453,8 +497,11 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the batched / warm-start / n=8192 lines")
+    ap.add_argument("--no-extra", action="store_true", help="skip every extra line")
+    ap.add_argument("--extras", default="batched,warm,geometric,sparse",
+                    help="comma-separated extra lines: batched, warm, geometric, sparse")
     ap.add_argument("--batch", type=int, default=10_000)
+    ap.add_argument("--no-tune", action="store_true", help="batched line with the library defaults, no autotuner")
     ap.add_argument("--warm-n1024", type=int, default=100)
     ap.add_argument("--warm-n8192", type=int, default=2)
     args = ap.parse_args()

@@ -149,6 +149,7 @@ typedef struct {
     double tail_ms;          /* of refine_ms, the time from the end of each
                                 phase's refine kernel to the end of its
                                 one-CTA tail kernel (profile != 0) */
+    int64_t tail_full_scans; /* of tail_scans, those that read the whole row */
 } la_stats;
 
 /*

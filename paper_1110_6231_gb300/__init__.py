@@ -77,6 +77,7 @@ class la_stats(ctypes.Structure):
         ("price_update_levels", ctypes.c_int64),
         ("list_entries", ctypes.c_int32),
         ("tail_ms", ctypes.c_double),
+        ("tail_full_scans", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

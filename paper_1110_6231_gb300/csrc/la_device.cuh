@@ -72,6 +72,7 @@ struct Ctrl {
     unsigned pu_last;                // largest label of a free row
     int pu_abort;                    // sweeps did not settle: no update
     int colseen_missing;             // sparse graphs: columns without an arc
+    unsigned long long tail_full;    // full row scans made by the tail kernel
 };
 
 // Global nanosecond timer (bounds every wait in the kernels).

@@ -575,6 +575,7 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
     if (lane == 0 && total) {
         atomicAdd(&ctrl->scans, (unsigned long long)pending);
         atomicAdd(&ctrl->tail_scans, total);
+        atomicAdd(&ctrl->tail_full, full);
         atomicAdd(&ctrl->wins, wins);
         atomicAdd(&ctrl->displaced, displaced);
         atomicAdd(&ctrl->full_scans, full);
@@ -1170,6 +1171,7 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.full_scans = (int64_t)c1.full_scans;
     stats.list_scans = (int64_t)c1.list_scans;
     stats.tail_scans = (int64_t)c1.tail_scans;
+    stats.tail_full_scans = (int64_t)c1.tail_full;
     stats.tail_phases = c1.tail_phases;
     for (int k = 0; k < ph && k < LA_STATS_PHASES; ++k) {
         const unsigned long long end = (k + 1 < ph) ? c1.phase_start_scans[k + 1] : c1.scans;
