@@ -92,7 +92,10 @@ typedef struct {
     int32_t flags;
     /* When a phase is down to this many free rows, the refine hands them to
        a one-CTA kernel that finishes the phase with the column keys in
-       shared memory (n <= 16384). 0 selects 32; negative disables it. */
+       shared memory (n <= 16384). 0 selects 32; negative disables it. If the
+       candidate lists stop answering there (more than a quarter of its scans,
+       after 64, read whole rows), the rows go back to a refine launch over
+       the whole grid. */
     int32_t tail_threshold;
     /* Global price updates (Sect. 5.2, Algorithm 5.3) per phase, each run
        when the phase is down to max(16, n/128) free rows after a stretch of
@@ -150,6 +153,8 @@ typedef struct {
                                 phase's refine kernel to the end of its
                                 one-CTA tail kernel (profile != 0) */
     int64_t tail_full_scans; /* of tail_scans, those that read the whole row */
+    int32_t tail_giveups;    /* phases whose tail kernel handed its rows back to
+                                the grid (its lists stopped answering) */
 } la_stats;
 
 /*

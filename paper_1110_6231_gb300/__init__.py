@@ -78,6 +78,7 @@ class la_stats(ctypes.Structure):
         ("list_entries", ctypes.c_int32),
         ("tail_ms", ctypes.c_double),
         ("tail_full_scans", ctypes.c_int64),
+        ("tail_giveups", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

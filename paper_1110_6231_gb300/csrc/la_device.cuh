@@ -73,6 +73,7 @@ struct Ctrl {
     int pu_abort;                    // sweeps did not settle: no update
     int colseen_missing;             // sparse graphs: columns without an arc
     unsigned long long tail_full;    // full row scans made by the tail kernel
+    int tail_giveups;                // phases whose tail kernel gave its rows back
 };
 
 // Global nanosecond timer (bounds every wait in the kernels).

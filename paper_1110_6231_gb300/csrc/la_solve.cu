@@ -48,6 +48,7 @@ constexpr unsigned long long kRangeLimit = 1ull << 40;  // C~ limit (LA_ERR_OVER
 constexpr int kTailMaxN = 16384;      // shared-memory keys of the tail kernel (128 KB)
 constexpr int kTailThreads = 1024;
 constexpr int kDefaultTailRows = 32;
+constexpr unsigned kTailGiveUpFull = 64;   // full scans before the tail kernel may give its rows back
 constexpr int kDefaultPuRounds = 0;   // global price updates per phase (off unless asked)
 
 // ---------------------------------------------------------------- kernels
@@ -295,17 +296,25 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
 // and its commit (the same packed atomicMin) stay on the SM. The rows handed
 // over, and any still in the queue, are finished by the CTA's 32 warps, then
 // the keys go back to global memory.
+//
+// One SM is the right place for chains of list scans, not for full scans:
+// when the lists stop answering (more than a quarter of the tail's scans,
+// after kTailGiveUpFull of them, read whole rows), the CTA stops, and every
+// row still free goes back to the row queue for a refine launch over the
+// whole grid that follows the tail kernel in every phase.
 template <bool WIDE, bool VEC>
 __global__ void __launch_bounds__(1024)
 k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
-       unsigned long long qlim, unsigned long long *__restrict__ key, Ctrl *__restrict__ ctrl,
-       unsigned long long budget, RowLists L, const int *__restrict__ tail_rows,
-       const int *__restrict__ qlist0, const int *__restrict__ qlist1) {
+       unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
+       Ctrl *__restrict__ ctrl, unsigned long long budget, RowLists L, const int *__restrict__ tail_rows,
+       int *__restrict__ qlist0, int *__restrict__ qlist1) {
     extern __shared__ unsigned long long skey[];
-    __shared__ int s_next, s_tc, s_q0, s_count;
+    __shared__ int s_next, s_tc, s_q0, s_count, s_back, s_stop;
+    __shared__ unsigned s_full, s_hits;
     if (*reinterpret_cast<volatile int *>(&ctrl->handoff) != 1) return;
-    const int qmode = ctrl->qmode, qlen = ctrl->qlen;
-    const int *qlist = ctrl->qsel ? qlist1 : qlist0;
+    const int qmode = ctrl->qmode, qlen = ctrl->qlen, qsel = ctrl->qsel;
+    const int *qlist = qsel ? qlist1 : qlist0;
+    int *qback = qsel ? qlist0 : qlist1;       // rows handed back to the grid
     constexpr unsigned kFlush = 8;
     const int tid = threadIdx.x, lane = tid & 31;
     for (int y = tid; y < n; y += blockDim.x) skey[y] = __ldcg(key + y);
@@ -315,10 +324,15 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
         s_tc = ctrl->tail_count;
         s_q0 = min(ctrl->next_row, qend);
         s_count = s_tc + (qend - s_q0);
+        s_back = 0;
+        s_stop = 0;
+        s_full = 0;
+        s_hits = 0;
     }
     __syncthreads();
     const unsigned long long R = ctrl->rebase_total;
     const SharedKeyPrices<WIDE> prices{skey};
+    volatile int *stop = &s_stop;
     int row = -1;
     unsigned long long wins = 0, displaced = 0, total = 0, full = 0, hits = 0;
     unsigned pending = 0;
@@ -330,6 +344,10 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
             if (k >= s_count) break;
             if (k < s_tc) row = __ldcg(tail_rows + k);
             else row = qmode ? __ldcg(qlist + s_q0 + (k - s_tc)) : s_q0 + (k - s_tc);
+        }
+        if (*stop) {   // the lists no longer answer: this free row goes back to the grid
+            if (lane == 0) qback[atomicAdd(&s_back, 1)] = row;
+            break;
         }
         if (pending == kFlush) {
             unsigned long long s = 0;
@@ -353,6 +371,11 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
         const auto t = scan_for_bid<WIDE, VEC>(C, row, n, cmin, np1, prices, lane, L, R, was_full);
         if (was_full) ++full;
         else ++hits;
+        if (lane == 0) {
+            const unsigned f = was_full ? atomicAdd(&s_full, 1u) + 1 : s_full;
+            const unsigned h = was_full ? s_hits : atomicAdd(&s_hits, 1u) + 1;
+            if (f >= kTailGiveUpFull && 4 * f > f + h) *stop = 1;
+        }
         __syncwarp();
         const unsigned long long nq = (unsigned long long)(t.b1 - t.c1) + (t.b2 - t.b1) + eps;
         if (t.w >= n || nq > qlim) {
@@ -375,7 +398,18 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
         }
     }
     __syncthreads();
-    for (int y = tid; y < n; y += blockDim.x) key[y] = skey[y];
+    if (*stop) {   // rows never claimed go back too
+        for (int k = min(s_next, s_count) + tid; k < s_count; k += blockDim.x) {
+            const int r = k < s_tc ? __ldcg(tail_rows + k) : (qmode ? __ldcg(qlist + s_q0 + (k - s_tc)) : s_q0 + (k - s_tc));
+            qback[atomicAdd(&s_back, 1)] = r;
+        }
+    }
+    for (int y = tid; y < n; y += blockDim.x) {
+        const unsigned long long k = skey[y];
+        key[y] = k;
+        if (WIDE) static_cast<unsigned long long *>(qmv)[y] = key_q(k);
+        else static_cast<uint32_t *>(qmv)[y] = (uint32_t)key_q(k);
+    }
     if (lane == 0 && total) {
         atomicAdd(&ctrl->scans, (unsigned long long)pending);
         atomicAdd(&ctrl->tail_scans, total);
@@ -385,9 +419,16 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
         atomicAdd(&ctrl->full_scans, full);
         atomicAdd(&ctrl->list_scans, hits);
     }
+    __syncthreads();
     if (tid == 0) {
+        // the queue the follow-up refine launch reads: the rows given back, or none
+        ctrl->qsel = *stop ? qsel ^ 1 : qsel;
+        ctrl->qmode = 1;
+        ctrl->qlen = *stop ? s_back : 0;
+        ctrl->next_row = 0;
         ctrl->handoff = 0;
         ctrl->tail_phases += 1;
+        ctrl->tail_giveups += *stop ? 1 : 0;
     }
 }
 
@@ -662,7 +703,7 @@ struct Workspace {
     Ctrl *h_ctrl = nullptr;
     int num_sms = 0;
     bool events = false;
-    cudaEvent_t ev[3 * kMaxPhases];   // per phase: refine start, tail start, end
+    cudaEvent_t ev[4 * kMaxPhases];   // per phase: refine start, tail start, tail end, end
 };
 
 std::mutex g_mu;
@@ -776,7 +817,7 @@ template <bool WIDE, bool VEC>
 cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C, int n, int cmin, uint32_t np1,
                           unsigned long long eps, unsigned long long qlim, Workspace &ws,
                           unsigned long long budget, const RowLists &L, int tail_T, int pu_T, int pu_rounds,
-                          int64_t &launches, int stop_free, cudaEvent_t ev_tail) {
+                          int64_t &launches, int stop_free, cudaEvent_t ev_tail, cudaEvent_t ev_fin) {
     for (int r = 0; r <= pu_rounds; ++r) {
         if (r > 0) {
             cudaError_t e = launch_pu<WIDE>(s, C, n, cmin, np1, eps, qlim, ws, L);
@@ -801,8 +842,19 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
             cudaFuncSetAttribute(k_tail<WIDE, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             smem_set = smem;
         }
-        k_tail<WIDE, VEC><<<1, kTailThreads, smem, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.ctrl, budget, L,
-                                                         ws.tail_rows, ws.qlist[0], ws.qlist[1]);
+        k_tail<WIDE, VEC><<<1, kTailThreads, smem, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget,
+                                                         L, ws.tail_rows, ws.qlist[0], ws.qlist[1]);
+        if (ev_fin) {
+            cudaError_t e = cudaEventRecord(ev_fin, s);
+            if (e != cudaSuccess) return e;
+        }
+        // rows the tail kernel gave back, if any (an empty queue otherwise)
+        k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L,
+                                                   0, ws.tail_rows, 0, ws.qlist[0], ws.qlist[1], stop_free);
+        ++launches;
+    } else if (ev_fin) {
+        cudaError_t e = cudaEventRecord(ev_fin, s);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -936,17 +988,18 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         if (wide) k_reset<true><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds);
         else k_reset<false><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds);
         launches += 2;
-        if (profile) LA_CK(cudaEventRecord(ws.ev[3 * ph], s));
+        if (profile) LA_CK(cudaEventRecord(ws.ev[4 * ph], s));
         const int sf = ph + 1 < (int)sched.size() ? stop_free : 0;
-        cudaEvent_t evt = profile ? ws.ev[3 * ph + 1] : nullptr;
+        cudaEvent_t evt = profile ? ws.ev[4 * ph + 1] : nullptr;
+        cudaEvent_t evf = profile ? ws.ev[4 * ph + 2] : nullptr;
         if (wide) {
-            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt)));
-            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt)));
+            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt, evf)));
+            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt, evf)));
         } else {
-            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt)));
-            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt)));
+            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt, evf)));
+            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt, evf)));
         }
-        if (profile) LA_CK(cudaEventRecord(ws.ev[3 * ph + 2], s));
+        if (profile) LA_CK(cudaEventRecord(ws.ev[4 * ph + 3], s));
     }
     const int fslot = ph & 1;
     if (prices_out) {
@@ -967,7 +1020,7 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.wins = (int64_t)c1.wins;
     stats.displaced = (int64_t)c1.displaced;
     stats.launches = launches;
-    stats.refine_launches = (int64_t)sched.size() * (1 + pu_rounds);
+    stats.refine_launches = (int64_t)sched.size() * (1 + pu_rounds + (tail_T > 0 ? 1 : 0));
     stats.price_updates = (int64_t)c1.pu_updates;
     stats.price_update_sweeps = (int64_t)c1.pu_iters;
     stats.price_update_levels = (int64_t)c1.pu_levels;
@@ -976,6 +1029,7 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.list_scans = (int64_t)c1.list_scans;
     stats.tail_scans = (int64_t)c1.tail_scans;
     stats.tail_full_scans = (int64_t)c1.tail_full;
+    stats.tail_giveups = c1.tail_giveups;
     stats.tail_phases = c1.tail_phases;
     for (int k = 0; k < ph && k < LA_STATS_PHASES; ++k) {
         const unsigned long long end = (k + 1 < ph) ? c1.phase_start_scans[k + 1] : c1.scans;
@@ -986,8 +1040,8 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         double ms = 0, tail_ms = 0;
         for (int k = 0; k < ph; ++k) {
             float t = 0, tt = 0;
-            LA_CK(cudaEventElapsedTime(&t, ws.ev[3 * k], ws.ev[3 * k + 2]));
-            LA_CK(cudaEventElapsedTime(&tt, ws.ev[3 * k + 1], ws.ev[3 * k + 2]));
+            LA_CK(cudaEventElapsedTime(&t, ws.ev[4 * k], ws.ev[4 * k + 3]));
+            LA_CK(cudaEventElapsedTime(&tt, ws.ev[4 * k + 1], ws.ev[4 * k + 2]));
             ms += t;
             tail_ms += tt;
             if (k < LA_STATS_PHASES) stats.phase_ms[k] = t;

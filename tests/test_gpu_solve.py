@@ -210,7 +210,10 @@ def test_profile_counts(la):
     C = synth.uniform_costs(1024, 0, 1000, 1)
     st = check(la, C, profile=True)
     assert st["phases"] == 6
-    assert st["refine_launches"] == st["phases"]               # no price-update rounds by default
+    # per phase: the refine grid and, after the one-CTA tail kernel, a refine
+    # launch for any rows the tail gives back (no price-update rounds by default)
+    assert st["refine_launches"] == 2 * st["phases"]
+    assert 0 <= st["tail_giveups"] <= st["tail_phases"] <= st["phases"]
     assert st["refine_ms"] > 0
     assert st["scans"] >= 1024 * 6
     assert st["wins"] == st["displaced"] + 1024 * 6     # every phase fills all n columns
