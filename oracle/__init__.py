@@ -19,6 +19,9 @@ builds it with gcc on first use and marshals numpy arrays. Functions:
 * ``sparse_brute_force``, ``sparse_ssp`` and ``sparse_check_*`` -- the same
   problem on a sparse bipartite graph given by its arcs in CSR form
   (``row_ptr, cols, costs``); ``INFEASIBLE`` when it has no perfect matching.
+* ``min_cut_brute``, ``maxflow_dinic``, ``cut_capacity`` -- maximum s-t flow
+  (the paper's Sect. 4 problem) on a directed graph given by its arcs, and
+  ``grid_arcs`` for the 4-connected grid graphs with terminal arcs.
 """
 
 from __future__ import annotations
@@ -72,10 +75,14 @@ def _load():
             lib.or_sparse_check_matching.argtypes = [i32, P, P, P, P, i64]
             lib.or_sparse_check_duals.argtypes = [i32, P, P, P, P, P, P]
             lib.or_sparse_check_eps_cs.argtypes = [i32, P, P, P, P, P, i64]
+            lib.or_min_cut_brute.argtypes = [i32, i32, P, P, P, i32, i32, P, P]
+            lib.or_maxflow_dinic.argtypes = [i32, i32, P, P, P, i32, i32, P, P]
+            lib.or_cut_capacity.argtypes = [i32, i32, P, P, P, i32, i32, P, P]
             for f in (lib.or_brute_force, lib.or_hungarian, lib.or_cost_scaling,
                       lib.or_check_matching, lib.or_check_duals, lib.or_check_eps_cs,
                       lib.or_sparse_brute_force, lib.or_sparse_ssp, lib.or_sparse_check_matching,
-                      lib.or_sparse_check_duals, lib.or_sparse_check_eps_cs):
+                      lib.or_sparse_check_duals, lib.or_sparse_check_eps_cs,
+                      lib.or_min_cut_brute, lib.or_maxflow_dinic, lib.or_cut_capacity):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -241,3 +248,75 @@ def sparse_check_eps_cs(row_ptr, cols, costs, match, prices, eps: int = 1) -> in
     m = np.ascontiguousarray(match, dtype=np.int32)
     p = np.ascontiguousarray(prices, dtype=np.int64)
     return _load().or_sparse_check_eps_cs(n, _ptr(rp), _ptr(cc), _ptr(cs), _ptr(m), _ptr(p), int(eps))
+
+
+# ---------------------------------------------------------------- maximum flow
+
+def _arcs(tail, head, cap):
+    tail = np.ascontiguousarray(tail, dtype=np.int32)
+    head = np.ascontiguousarray(head, dtype=np.int32)
+    cap = np.ascontiguousarray(cap, dtype=np.int64)
+    if not (tail.shape == head.shape == cap.shape) or tail.ndim != 1:
+        raise ValueError("tail, head and cap must be 1-D arrays of one length")
+    return tail, head, cap
+
+
+def min_cut_brute(nn, tail, head, cap, s, t):
+    """Minimum s-t cut by enumeration (nn <= 20). Returns ``(value, side)``."""
+    tail, head, cap = _arcs(tail, head, cap)
+    value = np.zeros(1, dtype=np.int64)
+    side = np.zeros(nn, dtype=np.uint8)
+    rc = _load().or_min_cut_brute(int(nn), tail.size, _ptr(tail), _ptr(head), _ptr(cap), int(s), int(t),
+                                  _ptr(value), _ptr(side))
+    if rc:
+        raise OracleError(f"or_min_cut_brute returned {rc}")
+    return int(value[0]), side
+
+
+def maxflow_dinic(nn, tail, head, cap, s, t):
+    """Maximum flow value and the source side of a minimum cut (Dinic)."""
+    tail, head, cap = _arcs(tail, head, cap)
+    value = np.zeros(1, dtype=np.int64)
+    side = np.zeros(nn, dtype=np.uint8)
+    rc = _load().or_maxflow_dinic(int(nn), tail.size, _ptr(tail), _ptr(head), _ptr(cap), int(s), int(t),
+                                  _ptr(value), _ptr(side))
+    if rc:
+        raise OracleError(f"or_maxflow_dinic returned {rc}")
+    return int(value[0]), side
+
+
+def cut_capacity(nn, tail, head, cap, s, t, side) -> int:
+    tail, head, cap = _arcs(tail, head, cap)
+    side = np.ascontiguousarray(side, dtype=np.uint8)
+    value = np.zeros(1, dtype=np.int64)
+    rc = _load().or_cut_capacity(int(nn), tail.size, _ptr(tail), _ptr(head), _ptr(cap), int(s), int(t),
+                                 _ptr(side), _ptr(value))
+    if rc:
+        raise OracleError(f"or_cut_capacity returned {rc}")
+    return int(value[0])
+
+
+def grid_arcs(cap, src, snk):
+    """Arcs of a 4-connected H x W grid graph with terminals: node i*W + j is
+    pixel (i, j), s = H*W, t = H*W + 1. ``cap[d][i][j]`` is the capacity of
+    the arc from (i, j) to its neighbour in direction d (0: (i, j+1),
+    1: (i, j-1), 2: (i+1, j), 3: (i-1, j)); ``src`` / ``snk`` the capacities
+    s -> (i, j) and (i, j) -> t. Returns ``(nn, tail, head, cap, s, t)``."""
+    cap = np.asarray(cap, dtype=np.int64)
+    src = np.asarray(src, dtype=np.int64)
+    snk = np.asarray(snk, dtype=np.int64)
+    _, H, W = cap.shape
+    N = H * W
+    ii, jj = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    u = (ii * W + jj).ravel()
+    tails, heads, caps = [], [], []
+    for d, (di, dj) in enumerate(((0, 1), (0, -1), (1, 0), (-1, 0))):
+        ni, nj = (ii + di).ravel(), (jj + dj).ravel()
+        ok = (ni >= 0) & (ni < H) & (nj >= 0) & (nj < W)
+        tails.append(u[ok])
+        heads.append((ni * W + nj)[ok])
+        caps.append(cap[d].ravel()[ok])
+    tails += [np.full(N, N), u]
+    heads += [u, np.full(N, N + 1)]
+    caps += [src.ravel(), snk.ravel()]
+    return N + 2, np.concatenate(tails), np.concatenate(heads), np.concatenate(caps), N, N + 1

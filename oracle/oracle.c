@@ -548,3 +548,162 @@ int or_sparse_check_eps_cs(int32_t n, const int32_t *row_ptr, const int32_t *col
     }
     return OR_OK;
 }
+
+/* ================================================================== */
+/* Maximum s-t flow (Sect. 4, the paper's first problem).              */
+/*                                                                     */
+/* A directed graph on nodes 0..nn-1 given by its arcs (tail, head,    */
+/* capacity >= 0); parallel and opposite arcs allowed. The maximum     */
+/* flow value from s to t, and a minimum cut: the nodes still reachable */
+/* from s in the final residual graph (by the max-flow min-cut theorem  */
+/* the arcs leaving that set carry exactly the flow value).            */
+/* ================================================================== */
+
+/* Brute force over every s-t cut (nn <= 20): the minimum cut capacity,
+ * which equals the maximum flow value. side_out[v] = 1 on the source side
+ * of one minimum cut. */
+int or_min_cut_brute(int32_t nn, int32_t na, const int32_t *tail, const int32_t *head,
+                     const int64_t *cap, int32_t s, int32_t t, int64_t *value, uint8_t *side_out)
+{
+    if (nn < 2 || nn > 20 || s < 0 || t < 0 || s >= nn || t >= nn || s == t || !value) return OR_INVALID;
+    for (int32_t a = 0; a < na; ++a)
+        if (tail[a] < 0 || tail[a] >= nn || head[a] < 0 || head[a] >= nn || cap[a] < 0) return OR_INVALID;
+    int64_t best = -1;
+    uint32_t best_mask = 0;
+    for (uint32_t mask = 0; mask < (1u << nn); ++mask) {
+        if (!(mask >> s & 1u) || (mask >> t & 1u)) continue;      /* s inside, t outside */
+        int64_t c = 0;
+        for (int32_t a = 0; a < na; ++a)
+            if ((mask >> tail[a] & 1u) && !(mask >> head[a] & 1u)) c += cap[a];
+        if (best < 0 || c < best) { best = c; best_mask = mask; }
+    }
+    *value = best;
+    if (side_out)
+        for (int32_t v = 0; v < nn; ++v) side_out[v] = (uint8_t)(best_mask >> v & 1u);
+    return OR_OK;
+}
+
+/* Dinic's algorithm (Dinic 1970): BFS levels from s in the residual graph,
+ * then blocking flows along level-increasing arcs (iterative DFS with a
+ * per-node arc pointer), until t is unreachable. Not from the paper: an
+ * independent ground truth for its push-relabel method. */
+int or_maxflow_dinic(int32_t nn, int32_t na, const int32_t *tail, const int32_t *head,
+                     const int64_t *cap, int32_t s, int32_t t, int64_t *value, uint8_t *side_out)
+{
+    if (nn < 2 || s < 0 || t < 0 || s >= nn || t >= nn || s == t || na < 0 || !value) return OR_INVALID;
+    for (int32_t a = 0; a < na; ++a)
+        if (tail[a] < 0 || tail[a] >= nn || head[a] < 0 || head[a] >= nn || cap[a] < 0) return OR_INVALID;
+    /* residual arcs 2a (forward) and 2a+1 (backward), adjacency in CSR */
+    const int64_t m = 2 * (int64_t)na;
+    int64_t *res = malloc(sizeof(int64_t) * (m > 0 ? m : 1));
+    int32_t *to = malloc(sizeof(int32_t) * (m > 0 ? m : 1));
+    int32_t *start = calloc((size_t)nn + 1, sizeof(int32_t));
+    int32_t *order = malloc(sizeof(int32_t) * (m > 0 ? m : 1));
+    int32_t *level = malloc(sizeof(int32_t) * nn);
+    int32_t *queue = malloc(sizeof(int32_t) * nn);
+    int32_t *ptr = malloc(sizeof(int32_t) * nn);
+    int32_t *stack_v = malloc(sizeof(int32_t) * nn);     /* DFS path: nodes */
+    int32_t *stack_a = malloc(sizeof(int32_t) * nn);     /* DFS path: arcs into them */
+    if (!res || !to || !start || !order || !level || !queue || !ptr || !stack_v || !stack_a) {
+        free(res); free(to); free(start); free(order); free(level); free(queue); free(ptr);
+        free(stack_v); free(stack_a);
+        return OR_NOMEM;
+    }
+    for (int32_t a = 0; a < na; ++a) {
+        res[2 * a] = cap[a];  to[2 * a] = head[a];
+        res[2 * a + 1] = 0;   to[2 * a + 1] = tail[a];
+        start[tail[a] + 1]++;
+        start[head[a] + 1]++;
+    }
+    for (int32_t v = 0; v < nn; ++v) start[v + 1] += start[v];
+    {
+        int32_t *fill = malloc(sizeof(int32_t) * nn);
+        if (!fill) { free(res); free(to); free(start); free(order); free(level); free(queue); free(ptr);
+                     free(stack_v); free(stack_a); return OR_NOMEM; }
+        for (int32_t v = 0; v < nn; ++v) fill[v] = start[v];
+        for (int32_t a = 0; a < na; ++a) {
+            order[fill[tail[a]]++] = 2 * a;
+            order[fill[head[a]]++] = 2 * a + 1;
+        }
+        free(fill);
+    }
+    int64_t flow = 0;
+    for (;;) {
+        for (int32_t v = 0; v < nn; ++v) level[v] = -1;
+        int32_t qh = 0, qt = 0;
+        level[s] = 0;
+        queue[qt++] = s;
+        while (qh < qt) {
+            const int32_t v = queue[qh++];
+            for (int32_t k = start[v]; k < start[v + 1]; ++k) {
+                const int32_t e = order[k];
+                if (res[e] > 0 && level[to[e]] < 0) { level[to[e]] = level[v] + 1; queue[qt++] = to[e]; }
+            }
+        }
+        if (level[t] < 0) break;
+        for (int32_t v = 0; v < nn; ++v) ptr[v] = start[v];
+        /* blocking flow: advance / retreat along level-increasing arcs */
+        int32_t depth = 0;
+        stack_v[0] = s;
+        while (depth >= 0) {
+            const int32_t v = stack_v[depth];
+            if (v == t) {
+                int64_t d = INT64_MAX;
+                for (int32_t i = 1; i <= depth; ++i) if (res[stack_a[i]] < d) d = res[stack_a[i]];
+                for (int32_t i = 1; i <= depth; ++i) { res[stack_a[i]] -= d; res[stack_a[i] ^ 1] += d; }
+                flow += d;
+                depth = 0;                 /* restart from s; saturated arcs are skipped below */
+                continue;
+            }
+            int advanced = 0;
+            for (; ptr[v] < start[v + 1]; ++ptr[v]) {
+                const int32_t e = order[ptr[v]];
+                const int32_t w = to[e];
+                if (res[e] > 0 && level[w] == level[v] + 1) {
+                    stack_v[++depth] = w;
+                    stack_a[depth] = e;
+                    advanced = 1;
+                    break;
+                }
+            }
+            if (!advanced) {               /* dead end: v leaves the level graph */
+                level[v] = -1;
+                --depth;
+                if (depth >= 0) ++ptr[stack_v[depth]];
+            }
+        }
+    }
+    *value = flow;
+    if (side_out)                          /* reachable from s in the residual graph */
+        for (int32_t v = 0; v < nn; ++v) side_out[v] = 0;
+    if (side_out) {
+        int32_t qh = 0, qt = 0;
+        side_out[s] = 1;
+        queue[qt++] = s;
+        while (qh < qt) {
+            const int32_t v = queue[qh++];
+            for (int32_t k = start[v]; k < start[v + 1]; ++k) {
+                const int32_t e = order[k];
+                if (res[e] > 0 && !side_out[to[e]]) { side_out[to[e]] = 1; queue[qt++] = to[e]; }
+            }
+        }
+    }
+    free(res); free(to); free(start); free(order); free(level); free(queue); free(ptr);
+    free(stack_v); free(stack_a);
+    return OR_OK;
+}
+
+/* Capacity of the cut whose source side is side[v] = 1 (s inside, t outside). */
+int or_cut_capacity(int32_t nn, int32_t na, const int32_t *tail, const int32_t *head, const int64_t *cap,
+                    int32_t s, int32_t t, const uint8_t *side, int64_t *value)
+{
+    if (nn < 2 || !side || !value || s < 0 || t < 0 || s >= nn || t >= nn) return OR_INVALID;
+    if (!side[s] || side[t]) return 17;
+    int64_t c = 0;
+    for (int32_t a = 0; a < na; ++a) {
+        if (tail[a] < 0 || tail[a] >= nn || head[a] < 0 || head[a] >= nn) return OR_INVALID;
+        if (side[tail[a]] && !side[head[a]]) c += cap[a];
+    }
+    *value = c;
+    return OR_OK;
+}

@@ -28,6 +28,9 @@ motivating application, optical flow by assignment (Sect. 1):
   Sect. 6) in CSR form ``(row_ptr, cols, costs)``, each with a planted
   perfect matching: random arcs with uniform costs, and the optical-flow
   points linked to the targets in their 3 x 3 grid neighbourhood.
+* ``grid_cut`` -- max-flow instances (the paper's Sect. 4 problem) in the form
+  of graph-cut segmentation: a 4-connected H x W grid with source and sink
+  arcs, built from a noisy image of bright disks on a dark background.
 """
 
 from __future__ import annotations
@@ -49,6 +52,9 @@ __all__ = [
     "sparse_uniform",
     "sparse_geometric",
     "sparse_instance",
+    "grid_cut",
+    "GRID_WORKLOADS",
+    "grid_instance",
     "WORKLOADS",
     "SPARSE_WORKLOADS",
 ]
@@ -65,6 +71,8 @@ _TAG_JITTER = 4
 _TAG_SIZES = 5
 _TAG_ARCS = 6
 _TAG_ARC_COSTS = 7
+_TAG_BLOBS = 8
+_TAG_PIXEL_NOISE = 9
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -355,3 +363,63 @@ def sparse_instance(name: str, seed: int, n: int | None = None):
     if w["kind"] == "uniform":
         return sparse_uniform(n, w["degree"], seed)
     return sparse_geometric(n, seed)
+
+
+# ---------------------------------------------------------------- grid max-flow
+
+def grid_cut(H: int, W: int, seed: int, disks: int = 12, sigma_noise: float = 0.12,
+             data_scale: float = 1000.0, smooth: float = 300.0, sigma_edge: float = 0.1):
+    """A graph-cut segmentation instance on an H x W 4-connected grid.
+
+    The image: intensity 0.2, and 0.8 inside ``disks`` disks (centres uniform,
+    radii uniform in [0.03, 0.15] min(H, W)), plus N(0, sigma_noise^2) noise.
+    Data terms: s -> (i, j) costs ``rint(data_scale (I - 0.2)^2)`` (taking the
+    pixel to the background side cuts it) and (i, j) -> t costs
+    ``rint(data_scale (I - 0.8)^2)``. Smoothness: the arc to each neighbour
+    costs ``rint(smooth exp(-(I_u - I_v)^2 / (2 sigma_edge^2)))`` both ways;
+    arcs that would leave the grid are 0.
+
+    Returns ``(cap, src, snk)``: int32 arrays [4][H][W], [H][W], [H][W], with
+    directions 0: (i, j+1), 1: (i, j-1), 2: (i+1, j), 3: (i-1, j).
+    """
+    if H < 1 or W < 1:
+        raise ValueError("H and W must be >= 1")
+    d = uniform_doubles(seed, _TAG_BLOBS, 3 * disks).reshape(disks, 3)
+    side = float(min(H, W))
+    cy, cx = d[:, 0] * H, d[:, 1] * W
+    r = (0.03 + 0.12 * d[:, 2]) * side
+    ii = np.arange(H, dtype=np.float64)[:, None] + 0.5
+    jj = np.arange(W, dtype=np.float64)[None, :] + 0.5
+    inside = np.zeros((H, W), dtype=bool)
+    for k in range(disks):
+        dy = ii - cy[k]
+        dx = jj - cx[k]
+        inside |= dy * dy + dx * dx <= r[k] * r[k]
+    zx, _ = normal_pairs(seed, _TAG_PIXEL_NOISE, H * W)
+    img = np.where(inside, 0.8, 0.2) + sigma_noise * zx.reshape(H, W)
+    src = np.rint(data_scale * (img - 0.2) * (img - 0.2)).astype(np.int32)
+    snk = np.rint(data_scale * (img - 0.8) * (img - 0.8)).astype(np.int32)
+    cap = np.zeros((4, H, W), dtype=np.int32)
+    inv = -1.0 / (2.0 * sigma_edge * sigma_edge)
+    if W > 1:
+        dh = img[:, 1:] - img[:, :-1]
+        w = np.rint(smooth * _exp(dh * dh * inv)).astype(np.int32)
+        cap[0, :, :-1] = w
+        cap[1, :, 1:] = w
+    if H > 1:
+        dv = img[1:, :] - img[:-1, :]
+        w = np.rint(smooth * _exp(dv * dv * inv)).astype(np.int32)
+        cap[2, :-1, :] = w
+        cap[3, 1:, :] = w
+    return cap, src, snk
+
+
+GRID_WORKLOADS = {
+    "gridcut-1024x1024": dict(H=1024, W=1024),
+    "gridcut-256x256": dict(H=256, W=256),
+}
+
+
+def grid_instance(name: str, seed: int):
+    w = GRID_WORKLOADS[name]
+    return grid_cut(w["H"], w["W"], seed)

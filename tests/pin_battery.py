@@ -125,6 +125,43 @@ def run_sparse_pins(orc):
     assert int(u.sum() + v.sum()) == c
 
 
+def run_maxflow_pins(orc):
+    from paper_1110_6231_gb300 import synth
+    for path in sorted(glob.glob(os.path.join(HERE, "golden", "maxflow", "*.txt"))):
+        kv = {}
+        for line in open(path):
+            if line.strip() and not line.startswith("#"):
+                parts = line.split()
+                kv[parts[0]] = parts[1:]
+        H, W = int(kv["H"][0]), int(kv["H"][2])
+        cap = np.array([[int(v) for v in kv[k]] for k in ("right", "left", "down", "up")]).reshape(4, H, W)
+        g = orc.grid_arcs(cap, np.array([int(v) for v in kv["src"]]).reshape(H, W),
+                          np.array([int(v) for v in kv["snk"]]).reshape(H, W))
+        assert orc.maxflow_dinic(*g)[0] == int(kv["flow"][0]), path
+        assert orc.min_cut_brute(*g)[0] == int(kv["flow"][0]), path
+    # unit matching r1-c1, r1-c2, r2-c1 with r1 -> c1 tried first: the second
+    # unit needs the first path rerouted through the backward arc c1 -> r1
+    assert orc.maxflow_dinic(6, [0, 0, 1, 1, 2, 3, 4], [1, 2, 3, 4, 3, 5, 5], [1] * 7, 0, 5)[0] == 2
+    rng = np.random.default_rng(8)
+    for t in range(120):
+        nn = int(rng.integers(2, 9))
+        arcs = [(a, b, int(rng.integers(0, 20))) for a in range(nn) for b in range(nn)
+                if a != b and rng.random() < 0.45]
+        tail = np.array([a[0] for a in arcs], np.int32)
+        head = np.array([a[1] for a in arcs], np.int32)
+        cap = np.array([a[2] for a in arcs], np.int64)
+        ref = orc.min_cut_brute(nn, tail, head, cap, 0, nn - 1)[0]
+        v, side = orc.maxflow_dinic(nn, tail, head, cap, 0, nn - 1)
+        assert v == ref
+        assert orc.cut_capacity(nn, tail, head, cap, 0, nn - 1, side) == v
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import maximum_flow
+    nn, tail, head, cap, s, t = orc.grid_arcs(*synth.grid_cut(20, 17, 4))
+    keep = cap > 0
+    m = csr_matrix((cap[keep].astype(np.int32), (tail[keep], head[keep])), shape=(nn, nn))
+    assert orc.maxflow_dinic(nn, tail, head, cap, s, t)[0] == maximum_flow(m, s, t).flow_value
+
+
 def main(argv):
     import oracle as orc
     if len(argv) > 1:
@@ -135,6 +172,7 @@ def main(argv):
     try:
         run_all_pins(orc)
         run_sparse_pins(orc)
+        run_maxflow_pins(orc)
     except AssertionError:
         return 1
     return 0

@@ -43,6 +43,12 @@ MUTANTS = [
     ("sparse-ssp-root-dual-kept", "        u[r] += dfree;\n", ""),
     ("sparse-parallel-arc-max", "if (cols[k] == y && costs[k] < best) best = costs[k];",
      "if (cols[k] == y && (best == OR_INF || costs[k] > best)) best = costs[k];"),
+    ("dinic-backward-residual-sign", "res[stack_a[i]] -= d; res[stack_a[i] ^ 1] += d;",
+     "res[stack_a[i]] -= d; res[stack_a[i] ^ 1] -= d;"),
+    ("dinic-arcs-undirected", "res[2 * a + 1] = 0;   to[2 * a + 1] = tail[a];",
+     "res[2 * a + 1] = cap[a];   to[2 * a + 1] = tail[a];"),
+    ("min-cut-brute-allows-t-inside", "if (!(mask >> s & 1u) || (mask >> t & 1u)) continue;",
+     "if (!(mask >> s & 1u)) continue;"),
     ("sparse-brute-force-ignores-arcs", "s = w[x][perm[x]] >= OR_INF ? OR_INF : s + w[x][perm[x]];",
      "s = w[x][perm[x]] >= OR_INF ? s : s + w[x][perm[x]];"),
 ]
