@@ -378,6 +378,53 @@ la_status la_solve_sparse_ex(const int32_t *row_ptr, const int32_t *cols, const 
                              int32_t *match_out, int64_t *cost_out, la_stats *stats_out);
 
 /*
+ * la_maxflow_grid -- maximum s-t flow and a minimum cut of a 4-connected
+ * H x W grid graph with terminal arcs (the graph-cut form of the paper's
+ * Sect. 4 problem), by Hong's lock-free push-relabel (Algorithm 4.5) run in
+ * cycles with a global relabel between them (Algorithm 4.8, plus the gap
+ * step of the paper's implementation), all on the device.
+ *   cap      device const int32[4][H][W]: cap[d][i][j] is the capacity of
+ *            the arc from pixel (i, j) to its neighbour in direction d
+ *            (0: (i, j+1), 1: (i, j-1), 2: (i+1, j), 3: (i-1, j)); arcs that
+ *            would leave the grid must be 0.
+ *   src, snk device const int32[H][W]: capacities s -> (i, j), (i, j) -> t.
+ *            Every capacity is in [0, 2^30 - 1].
+ *   flow_out device int64[1]: the maximum flow value.
+ *   cut_out  device uint8[H][W] or NULL: 1 for the pixels on the source side
+ *            of a minimum cut (those that cannot reach t in the final
+ *            residual graph), 0 for the others; the capacity of the arcs
+ *            from the source side to the sink side equals the flow value.
+ * Returns LA_OK; LA_ERR_INVALID for bad sizes or capacities (checked on the
+ * device before any push); LA_ERR_ITER_LIMIT after max_rounds cycles.
+ * Blocks until the result is in place. H * W < 2^30.
+ */
+typedef struct {
+    int32_t cycle;        /* push-relabel passes per launch between two
+                             global relabels (the paper's CYCLE); 0 = adaptive:
+                             32 at first, doubled (up to 4096) after every
+                             round that leaves more than half of the active
+                             nodes active */
+    int32_t max_rounds;   /* cycles before LA_ERR_ITER_LIMIT; 0 = 65536 */
+} la_maxflow_options;
+
+typedef struct {
+    int64_t flow;             /* the maximum flow value */
+    int64_t excess_total;     /* sum of the source arcs' capacities */
+    int64_t rounds;           /* push-relabel launches */
+    int64_t global_relabels;
+    int64_t relabel_sweeps;   /* tiled relaxation passes over the grid they took */
+    int64_t launches;         /* kernels launched */
+} la_maxflow_stats;
+
+la_status la_maxflow_grid(const int32_t *cap, const int32_t *src, const int32_t *snk,
+                          int32_t H, int32_t W, void *stream, int64_t *flow_out,
+                          uint8_t *cut_out);
+la_status la_maxflow_grid_ex(const int32_t *cap, const int32_t *src, const int32_t *snk,
+                             int32_t H, int32_t W, const la_maxflow_options *opt,
+                             void *stream, int64_t *flow_out, uint8_t *cut_out,
+                             la_maxflow_stats *stats_out);
+
+/*
  * la_solve_noalloc -- la_solve for callers that must not allocate memory.
  *
  * The paper has no counterpart: this entry point exists for deployments

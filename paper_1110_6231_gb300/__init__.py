@@ -135,6 +135,24 @@ class la_batch_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class la_maxflow_options(ctypes.Structure):
+    _fields_ = [("cycle", ctypes.c_int32), ("max_rounds", ctypes.c_int32)]
+
+
+class la_maxflow_stats(ctypes.Structure):
+    _fields_ = [
+        ("flow", ctypes.c_int64),
+        ("excess_total", ctypes.c_int64),
+        ("rounds", ctypes.c_int64),
+        ("global_relabels", ctypes.c_int64),
+        ("relabel_sweeps", ctypes.c_int64),
+        ("launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class LaError(RuntimeError):
     def __init__(self, status: int, where: str = ""):
         self.status = int(status)
@@ -161,6 +179,8 @@ def lib() -> ctypes.CDLL:
             L.la_solve_noalloc.argtypes = [P, i32, P, P, P]
             L.la_solve_sparse.argtypes = [P, P, P, i32, i32, P, P, P]
             L.la_solve_sparse_ex.argtypes = [P, P, P, i32, i32, P, P, P, P, P]
+            L.la_maxflow_grid.argtypes = [P, P, P, i32, i32, P, P, P]
+            L.la_maxflow_grid_ex.argtypes = [P, P, P, i32, i32, P, P, P, P, P]
             L.la_solve_batched.argtypes = [P, P, P, i32, P, P, P]
             L.la_solve_batched_ex.argtypes = [P, P, P, i32, P, P, P, P, P, P]
             L.la_predictor_param_count.argtypes = []
@@ -183,7 +203,8 @@ def lib() -> ctypes.CDLL:
             L.la_version.argtypes = []
             L.la_version.restype = i32
             for f in (L.la_solve, L.la_solve_ex, L.la_solve_noalloc, L.la_release_workspace,
-                      L.la_solve_batched, L.la_solve_batched_ex, L.la_solve_sparse, L.la_solve_sparse_ex):
+                      L.la_solve_batched, L.la_solve_batched_ex, L.la_solve_sparse, L.la_solve_sparse_ex,
+                      L.la_maxflow_grid, L.la_maxflow_grid_ex):
                 f.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -234,6 +255,18 @@ def la_solve_sparse_ex(row_ptr, cols, costs, n, nnz, opt, stream, match_out, cos
     return lib().la_solve_sparse_ex(_ptr(row_ptr), _ptr(cols), _ptr(costs), int(n), int(nnz),
                                     None if opt is None else ctypes.byref(opt), _stream(stream),
                                     _ptr(match_out), _ptr(cost_out),
+                                    None if stats_out is None else ctypes.byref(stats_out))
+
+
+def la_maxflow_grid(cap, src, snk, H, W, stream, flow_out, cut_out) -> int:
+    return lib().la_maxflow_grid(_ptr(cap), _ptr(src), _ptr(snk), int(H), int(W), _stream(stream),
+                                 _ptr(flow_out), _ptr(cut_out))
+
+
+def la_maxflow_grid_ex(cap, src, snk, H, W, opt, stream, flow_out, cut_out, stats_out) -> int:
+    return lib().la_maxflow_grid_ex(_ptr(cap), _ptr(src), _ptr(snk), int(H), int(W),
+                                    None if opt is None else ctypes.byref(opt), _stream(stream),
+                                    _ptr(flow_out), _ptr(cut_out),
                                     None if stats_out is None else ctypes.byref(stats_out))
 
 
@@ -399,6 +432,39 @@ def solve_sparse(row_ptr, cols, costs, *, alpha: int = 0, eps0: int = 0, want_pr
         raise LaError(rc, "la_solve_sparse_ex")
     return Solution(cost=int(cost.item()) if rc == LA_OK else None, match=match[:n],
                     stats=dict(st.as_dict(), status=rc), prices=None if prices is None else prices[:n])
+
+
+@dataclass
+class MaxFlow:
+    flow: int          # the maximum flow value
+    cut: object        # torch.uint8 [H, W]: 1 = source side of a minimum cut
+    stats: dict
+
+
+def maxflow_grid(cap, src, snk, *, cycle: int = 0, max_rounds: int = 0, stream=None,
+                 check: bool = True) -> MaxFlow:
+    """Maximum flow and a minimum cut of a 4-connected grid graph given by
+    int32 CUDA tensors ``cap`` [4, H, W], ``src`` and ``snk`` [H, W]."""
+    import torch
+    if cap.dim() != 3 or cap.shape[0] != 4 or tuple(src.shape) != tuple(cap.shape[1:]) \
+            or tuple(snk.shape) != tuple(cap.shape[1:]):
+        raise ValueError("cap must be [4, H, W], src and snk [H, W]")
+    for t in (cap, src, snk):
+        if t.dtype != torch.int32 or not t.is_cuda:
+            raise ValueError("capacities must be int32 CUDA tensors")
+    cap, src, snk = cap.contiguous(), src.contiguous(), snk.contiguous()
+    H, W = int(cap.shape[1]), int(cap.shape[2])
+    flow = torch.empty(1, dtype=torch.int64, device=cap.device)
+    cut = torch.empty((H, W), dtype=torch.uint8, device=cap.device)
+    opt = la_maxflow_options()
+    opt.cycle = cycle
+    opt.max_rounds = max_rounds
+    st = la_maxflow_stats()
+    with torch.cuda.device(cap.device):
+        rc = la_maxflow_grid_ex(cap, src, snk, H, W, opt, stream, flow, cut, st)
+    if rc != LA_OK and check:
+        raise LaError(rc, "la_maxflow_grid_ex")
+    return MaxFlow(flow=int(flow.item()) if rc == LA_OK else None, cut=cut, stats=dict(st.as_dict(), status=rc))
 
 
 @dataclass

@@ -30,7 +30,9 @@ motivating application, optical flow by assignment (Sect. 1):
   points linked to the targets in their 3 x 3 grid neighbourhood.
 * ``grid_cut`` -- max-flow instances (the paper's Sect. 4 problem) in the form
   of graph-cut segmentation: a 4-connected H x W grid with source and sink
-  arcs, built from a noisy image of bright disks on a dark background.
+  arcs, built from a noisy image of bright disks on a dark background;
+  ``grid_crossing`` -- the same grid with source arcs on the left column and
+  sink arcs on the right one, so that every unit of flow crosses the grid.
 """
 
 from __future__ import annotations
@@ -53,6 +55,7 @@ __all__ = [
     "sparse_geometric",
     "sparse_instance",
     "grid_cut",
+    "grid_crossing",
     "GRID_WORKLOADS",
     "grid_instance",
     "WORKLOADS",
@@ -414,12 +417,38 @@ def grid_cut(H: int, W: int, seed: int, disks: int = 12, sigma_noise: float = 0.
     return cap, src, snk
 
 
+_TAG_GRID_CAPS = 10
+
+
+def grid_crossing(H: int, W: int, seed: int, hi: int = 100):
+    """A max-flow instance whose flow must cross the grid: source arcs only
+    into column 0 and sink arcs only out of column W - 1 (capacity 100 hi
+    each), neighbour arcs with independent capacities uniform on [1, hi].
+    Augmenting paths are at least W - 1 arcs long. Returns ``(cap, src, snk)``
+    as ``grid_cut`` does."""
+    if H < 1 or W < 1:
+        raise ValueError("H and W must be >= 1")
+    cap = uniform_ints(seed, _TAG_GRID_CAPS, 4 * H * W, 1, hi).astype(np.int32).reshape(4, H, W)
+    cap[0, :, -1] = 0
+    cap[1, :, 0] = 0
+    cap[2, -1, :] = 0
+    cap[3, 0, :] = 0
+    src = np.zeros((H, W), dtype=np.int32)
+    snk = np.zeros((H, W), dtype=np.int32)
+    src[:, 0] = 100 * hi
+    snk[:, -1] = 100 * hi
+    return cap, src, snk
+
+
 GRID_WORKLOADS = {
-    "gridcut-1024x1024": dict(H=1024, W=1024),
-    "gridcut-256x256": dict(H=256, W=256),
+    "gridcut-1024x1024": dict(kind="cut", H=1024, W=1024),
+    "gridcut-256x256": dict(kind="cut", H=256, W=256),
+    "gridcross-512x512": dict(kind="cross", H=512, W=512),
 }
 
 
 def grid_instance(name: str, seed: int):
     w = GRID_WORKLOADS[name]
+    if w["kind"] == "cross":
+        return grid_crossing(w["H"], w["W"], seed)
     return grid_cut(w["H"], w["W"], seed)

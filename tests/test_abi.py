@@ -57,7 +57,8 @@ def test_struct_layout_matches_header(tmp_path):
     import paper_1110_6231_gb300 as la
     src = tmp_path / "layout.c"
     fields = {name: [f for f, _ in getattr(la, name)._fields_]
-              for name in ("la_options", "la_stats", "la_batch_options", "la_batch_stats")}
+              for name in ("la_options", "la_stats", "la_batch_options", "la_batch_stats",
+                           "la_maxflow_options", "la_maxflow_stats")}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "la.h"', "int main(void){"]
     for st, fs in fields.items():
         lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
