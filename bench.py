@@ -530,7 +530,7 @@ def main():
     ap.add_argument("--batch", type=int, default=10_000)
     ap.add_argument("--no-tune", action="store_true", help="batched line with the library defaults, no autotuner")
     ap.add_argument("--warm-n1024", type=int, default=100)
-    ap.add_argument("--warm-n8192", type=int, default=2)
+    ap.add_argument("--warm-n8192", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

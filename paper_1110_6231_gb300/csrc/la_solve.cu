@@ -309,8 +309,9 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
        Ctrl *__restrict__ ctrl, unsigned long long budget, RowLists L, const int *__restrict__ tail_rows,
        int *__restrict__ qlist0, int *__restrict__ qlist1) {
     extern __shared__ unsigned long long skey[];
-    __shared__ int s_next, s_tc, s_q0, s_count, s_back, s_stop;
+    __shared__ int s_next, s_tc, s_q0, s_count, s_back, s_stop, s_status;
     __shared__ unsigned s_full, s_hits;
+    __shared__ unsigned long long s_scans;
     if (*reinterpret_cast<volatile int *>(&ctrl->handoff) != 1) return;
     const int qmode = ctrl->qmode, qlen = ctrl->qlen, qsel = ctrl->qsel;
     const int *qlist = qsel ? qlist1 : qlist0;
@@ -328,8 +329,14 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
         s_stop = 0;
         s_full = 0;
         s_hits = 0;
+        s_status = 0;
+        s_scans = 0;
+        if (*reinterpret_cast<volatile int *>(&ctrl->status) != 0) s_count = 0;   // the phase has failed
     }
     __syncthreads();
+    // No other kernel runs during this one: the scan budget and the status
+    // are kept in shared memory and published at the end.
+    const unsigned long long scans0 = ctrl->scans;
     const unsigned long long R = ctrl->rebase_total;
     const SharedKeyPrices<WIDE> prices{skey};
     volatile int *stop = &s_stop;
@@ -353,15 +360,15 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
             unsigned long long s = 0;
             int st = 0;
             if (lane == 0) {
-                s = atomicAdd(&ctrl->scans, (unsigned long long)kFlush);
-                st = *reinterpret_cast<volatile int *>(&ctrl->status);
+                s = atomicAdd(&s_scans, (unsigned long long)kFlush);
+                st = *reinterpret_cast<volatile int *>(&s_status);
             }
             s = __shfl_sync(0xffffffffu, s, 0);
             st = __shfl_sync(0xffffffffu, st, 0);
             pending = 0;
             if (st != 0) break;
-            if (s + kFlush > budget) {
-                if (lane == 0) set_status(ctrl, LA_ERR_ITER_LIMIT);
+            if (scans0 + s + kFlush > budget) {
+                if (lane == 0) atomicCAS(&s_status, 0, (int)LA_ERR_ITER_LIMIT);
                 break;
             }
         }
@@ -379,7 +386,7 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
         __syncwarp();
         const unsigned long long nq = (unsigned long long)(t.b1 - t.c1) + (t.b2 - t.b1) + eps;
         if (t.w >= n || nq > qlim) {
-            if (lane == 0) set_status(ctrl, t.w >= n ? LA_ERR_INTERNAL : LA_ERR_OVERFLOW);
+            if (lane == 0) atomicCAS(&s_status, 0, (int)(t.w >= n ? LA_ERR_INTERNAL : LA_ERR_OVERFLOW));
             break;
         }
         const unsigned long long nk = pack_key(nq, (uint32_t)row);
@@ -411,7 +418,7 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
         else static_cast<uint32_t *>(qmv)[y] = (uint32_t)key_q(k);
     }
     if (lane == 0 && total) {
-        atomicAdd(&ctrl->scans, (unsigned long long)pending);
+        atomicAdd(&ctrl->scans, total);
         atomicAdd(&ctrl->tail_scans, total);
         atomicAdd(&ctrl->tail_full, full);
         atomicAdd(&ctrl->wins, wins);
@@ -421,6 +428,7 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
     }
     __syncthreads();
     if (tid == 0) {
+        if (s_status) set_status(ctrl, s_status);
         // the queue the follow-up refine launch reads: the rows given back, or none
         ctrl->qsel = *stop ? qsel ^ 1 : qsel;
         ctrl->qmode = 1;
