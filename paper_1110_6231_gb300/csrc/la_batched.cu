@@ -606,19 +606,15 @@ la_status ensure_bws(BatchWorkspace &w, int64_t B, int max_n) {
     return LA_OK;
 }
 
+// Persistent grid size on the current device (the shared-memory attribute is
+// per device, so it is set on every call; both are host calls, no GPU work).
 template <int BLOCK>
 int solve_grid(int num_sms, size_t smem) {
-    static int occ = 0;
-    static size_t occ_smem = 0;
-    if (!occ || occ_smem != smem) {
-        int o = 0;
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_batch_solve<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch_solve<BLOCK>, BLOCK, smem);
-        occ = std::max(1, o);
-        occ_smem = smem;
-    }
-    return num_sms * occ;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_batch_solve<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch_solve<BLOCK>, BLOCK, smem);
+    return num_sms * std::max(1, o);
 }
 
 cudaError_t enqueue(cudaStream_t s, int block, int grid, size_t smem, int slots, const BatchArgs &args,

@@ -793,16 +793,18 @@ la_status ensure_ws(Workspace &ws, int64_t n) {
 
 template <bool WIDE, bool VEC>
 int refine_grid(int num_sms, int block, int n) {
-    static int occ[5] = {0, 0, 0, 0, 0};   // per block size / 64 (cached)
+    static int occ[kMaxDevices][5];   // per device and block size / 64 (cached; calls are serialised)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
     const int slot = std::min(4, block / 64);
-    if (!occ[slot]) {
+    if (!occ[dev][slot]) {
         int o = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_refine<WIDE, VEC>, block, 0);
-        occ[slot] = std::max(1, o);
+        occ[dev][slot] = std::max(1, o);
     }
     const int warps_per_block = block / 32;
     const int need = (n + warps_per_block - 1) / warps_per_block;
-    return std::max(1, std::min(num_sms * occ[slot], need));
+    return std::max(1, std::min(num_sms * occ[dev][slot], need));
 }
 
 template <bool WIDE>
@@ -844,11 +846,10 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
     }
     if (tail_T > 0) {
         ++launches;
-        static int smem_set = 0;
         const int smem = (int)(sizeof(unsigned long long) * n);
-        if (smem > 48 * 1024 && smem > smem_set) {
-            cudaFuncSetAttribute(k_tail<WIDE, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            smem_set = smem;
+        if (smem > 48 * 1024) {   // a per-device attribute: set on every launch (a host call, no GPU work)
+            cudaError_t e = cudaFuncSetAttribute(k_tail<WIDE, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
         }
         k_tail<WIDE, VEC><<<1, kTailThreads, smem, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget,
                                                          L, ws.tail_rows, ws.qlist[0], ws.qlist[1]);
