@@ -217,7 +217,8 @@ typedef struct {
     int32_t max_n;
     /* alpha for each size bucket (0 = 10). */
     int32_t alpha[LA_ALPHA_BUCKETS];
-    /* Row scans per row and phase before LA_ERR_ITER_LIMIT (0 = 256). */
+    /* Row scans per row and phase before LA_ERR_ITER_LIMIT (0 = 256): an
+       instance may make budget_factor * n_i * phases + 4096 row scans. */
     int32_t budget_factor;
     /* Nonzero: launch directly instead of capturing and replaying a CUDA
        graph (a graph is captured once per distinct argument set). */

@@ -290,7 +290,7 @@ __device__ void load_next(const BatchArgs &a, Slot &sl, unsigned long long *keys
             v.wide = wide;
             v.qlim = wide ? (kQMax - 1) : ((1ull << 32) - 2 - Ct);
             v.vec = ((a.offsets[i] & 3) == 0) && (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15) == 0);
-            v.budget = (unsigned long long)a.P.budget_factor * n * nph + 65536;
+            v.budget = (unsigned long long)a.P.budget_factor * n * nph + 4096;
             v.scans = 0;
             v.status = 0;
             v.unmatched = n;

@@ -122,55 +122,8 @@ __device__ __forceinline__ ulonglong2 ld_q2(const unsigned long long *p) {
 // --- best / second best ---------------------------------------------------
 
 template <typename V>
-struct Top2 {
-    V b1;        // smallest v
-    V b2;        // second smallest v (over columns other than the argmin)
-    V qb;        // q(w) as read during the scan
-    int w;       // argmin column (lowest index among equal minima)
-};
-
-template <typename V>
-__device__ __forceinline__ void top2_init(Top2<V> &t) {
-    t.b1 = (V)~(V)0;
-    t.b2 = (V)~(V)0;
-    t.qb = 0;
-    t.w = INT_MAX;
-}
-
-template <typename V>
-__device__ __forceinline__ void top2_push(Top2<V> &t, V v, V q, int y) {
-    const V hi = v > t.b1 ? v : t.b1;
-    t.b2 = hi < t.b2 ? hi : t.b2;
-    const bool better = v < t.b1;       // strict: keeps the earliest column
-    t.w = better ? y : t.w;
-    t.qb = better ? q : t.qb;
-    t.b1 = better ? v : t.b1;
-}
-
-template <typename V>
 __device__ __forceinline__ V shfl_xor_v(V v, int m) {
     return __shfl_xor_sync(0xffffffffu, v, m);
-}
-
-// Butterfly merge of 32 lanes' partial results; every lane ends with the
-// row's (b1, b2, w, qb). Equal minima resolve to the lower column index, so
-// the merge is order independent.
-template <typename V>
-__device__ __forceinline__ void top2_warp_reduce(Top2<V> &t) {
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-        const V o1 = shfl_xor_v(t.b1, m);
-        const V o2 = shfl_xor_v(t.b2, m);
-        const V oq = shfl_xor_v(t.qb, m);
-        const int ow = __shfl_xor_sync(0xffffffffu, t.w, m);
-        const V lo2 = o2 < t.b2 ? o2 : t.b2;
-        const V hi1 = o1 > t.b1 ? o1 : t.b1;
-        t.b2 = lo2 < hi1 ? lo2 : hi1;
-        const bool take = (o1 < t.b1) || (o1 == t.b1 && ow < t.w);
-        t.b1 = take ? o1 : t.b1;
-        t.qb = take ? oq : t.qb;
-        t.w = take ? ow : t.w;
-    }
 }
 
 template <typename V>

@@ -130,3 +130,26 @@ def test_empty_batch(la):
     z = torch.zeros(0, dtype=torch.int32, device="cuda")
     sol = la.solve_batched(z, torch.zeros(0, dtype=torch.int64, device="cuda"), z)
     assert sol.costs.numel() == 0
+
+
+def test_instances_that_run_out_of_budget_fail_alone(la):
+    """With one row scan per row and phase (plus a slack of 4096), the large
+    instances run out of budget inside their chains: their rows are given up
+    one by one, each such instance ends with LA_ERR_ITER_LIMIT and frees its
+    slot, while the small instances of the same CTAs are still solved
+    exactly. The same batch then solves cleanly with the default budget."""
+    small = [synth.uniform_costs(n, 0, 50, 100 + n) for n in (3, 8, 16, 24)]
+    large = [synth.uniform_costs(n, 0, (1 << 20) - 1, 200 + n) for n in (400, 512, 640, 700)]
+    inst = [c for pair in zip(small, large) for c in pair]
+    flat, off, ns = pack(inst)
+    sol = run(la, flat, off, ns, budget_factor=1, slots=4, block_threads=128)
+    status = sol.status.cpu().numpy()
+    costs = sol.costs.cpu().numpy()
+    assert sol.stats["rc"] == la.LA_ERR_ITER_LIMIT
+    for i, C in enumerate(inst):
+        if C.shape[0] <= 24:
+            assert status[i] == 0 and costs[i] == oracle.hungarian(C)[0]
+        else:
+            assert status[i] == la.LA_ERR_ITER_LIMIT
+    assert sol.stats["failed"] == len(large)
+    verify(flat, off, ns, run(la, flat, off, ns, slots=4, block_threads=128))
