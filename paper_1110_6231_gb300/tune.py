@@ -1,6 +1,13 @@
-"""Autotuner for batched solves.
+"""Autotuners: alpha for single solves, and the shape of batched solves.
 
-It picks, by measurement on the caller's own batch (or a sample of it):
+``autotune_alpha`` times single solves of sample matrices for a few alphas
+(the divisor of eps between refine phases, Algorithm 5.0; the paper uses
+10) and keeps the fastest. Any alpha gives the same exact optimum; a larger
+one runs fewer phases, and on large instances each phase's end (its last
+displacement chains) costs more than the extra bidding inside a phase.
+
+``autotune_batched`` picks, by measurement on the caller's own batch (or a
+sample of it):
 
 * alpha per size bucket (bucket k holds 2^k <= n < 2^(k+1)). alpha is the
   divisor of eps between refine phases (Algorithm 5.0; the paper uses 10):
@@ -24,6 +31,32 @@ import paper_1110_6231_gb300 as la
 
 DEFAULT_ALPHAS = (4, 6, 8, 10, 16)
 DEFAULT_SHAPES = ((256, 2), (512, 2), (512, 4), (1024, 8))   # (threads per CTA, resident instances)
+
+
+DEFAULT_SINGLE_ALPHAS = (8, 10, 16, 24, 32)
+
+
+def autotune_alpha(samples, *, alphas=DEFAULT_SINGLE_ALPHAS, reps: int = 3) -> dict:
+    """Fastest alpha for ``la.solve`` on the square int32 CUDA matrices in
+    ``samples`` (mean wall time over ``reps`` solves of each, after one
+    untimed solve). Returns ``{"alpha": best, "mean_ms": {alpha: ms}}``."""
+    import time
+
+    import torch
+    mean = {}
+    for a in alphas:
+        for C in samples:
+            la.solve(C, alpha=int(a))
+        total = 0.0
+        for C in samples:
+            for _ in range(reps):
+                torch.cuda.synchronize(C.device)
+                t0 = time.perf_counter()
+                la.solve(C, alpha=int(a))
+                torch.cuda.synchronize(C.device)
+                total += time.perf_counter() - t0
+        mean[int(a)] = 1e3 * total / (reps * len(samples))
+    return {"alpha": min(mean, key=mean.get), "mean_ms": mean}
 
 
 def _bucket(n: int) -> int:
