@@ -1,4 +1,5 @@
-"""CPU oracle for the dense assignment problem (test infrastructure only).
+"""CPU oracle for the assignment problem and maximum flow (test
+infrastructure only).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
 import this package. It shares no code with the CUDA path in

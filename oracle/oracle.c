@@ -1,6 +1,6 @@
 /*
- * Oracle for the dense assignment problem: plain, sequential, slow and
- * obviously correct CPU code.
+ * Oracle for the assignment problem (dense and sparse) and for maximum flow:
+ * plain, sequential, slow and obviously correct CPU code.
  *
  * TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and the CPU
  * baseline legs of bench.py load this library. The CUDA product path shares
@@ -28,7 +28,10 @@
  *                     Goldberg-Kennedy double push (the paper's reference [9]).
  * and certificate checkers for any claimed matching. The same problem on
  * sparse bipartite graphs (arcs in CSR form) has its own brute force,
- * successive-shortest-path solver and checkers (or_sparse_*, below).
+ * successive-shortest-path solver and checkers (or_sparse_*, below), and
+ * the paper's first problem, maximum s-t flow (Sect. 4), has Dinic's
+ * algorithm, a brute-force minimum cut and a cut-capacity checker
+ * (or_maxflow_dinic, or_min_cut_brute, or_cut_capacity, at the end).
  *
  * All arithmetic is exact int64.
  */

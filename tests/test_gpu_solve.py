@@ -312,3 +312,18 @@ def test_phase_cutoff_keeps_the_optimum(la, cut):
     for C in (synth.uniform_costs(1500, 0, (1 << 20) - 1, 12), synth.uniform_costs(4096, 0, (1 << 20) - 1, 1),
               synth.uniform_costs(300, 0, 10**6, 14), np.full((50, 50), 3, np.int32)):
         check(la, C, phase_cutoff=cut)
+
+
+def test_alpha_tuner_picks_a_candidate_and_every_alpha_is_exact(la):
+    """Any alpha gives the same exact optimum (Algorithm 5.0 only changes the
+    eps schedule); the single-solve tuner returns one of its candidates with
+    a time for each."""
+    import torch
+    from paper_1110_6231_gb300 import tune
+    C = synth.uniform_costs(512, 0, (1 << 20) - 1, 77)
+    t = torch.from_numpy(C).cuda()
+    ref = oracle.hungarian(C)[0]
+    res = tune.autotune_alpha([t], alphas=(4, 10, 32, 100), reps=1)
+    assert res["alpha"] in (4, 10, 32, 100) and set(res["mean_ms"]) == {4, 10, 32, 100}
+    for a in (2, 3, 4, 10, 32, 100, 1000):
+        assert la.solve(t, alpha=a).cost == ref
