@@ -17,6 +17,8 @@ builds it with gcc on first use and marshals numpy arrays. Functions:
   push/relabel taken as the Goldberg-Kennedy double push, on costs scaled by
   n + 1.
 * ``check_matching``, ``check_duals``, ``check_eps_cs`` -- certificates.
+* ``certify_optimal(C, match)`` -- optimality of any claimed matching with no
+  duals given (Klein's negative-cycle criterion by Bellman-Ford), at any n.
 * ``sparse_brute_force``, ``sparse_ssp`` and ``sparse_check_*`` -- the same
   problem on a sparse bipartite graph given by its arcs in CSR form
   (``row_ptr, cols, costs``); ``INFEASIBLE`` when it has no perfect matching.
@@ -71,6 +73,7 @@ def _load():
             lib.or_check_matching.argtypes = [P, i32, P, i64]
             lib.or_check_duals.argtypes = [P, i32, P, P, P]
             lib.or_check_eps_cs.argtypes = [P, i32, P, P, i64]
+            lib.or_certify_optimal.argtypes = [P, i32, P, P, P]
             lib.or_sparse_brute_force.argtypes = [i32, P, P, P, P, P]
             lib.or_sparse_ssp.argtypes = [i32, P, P, P, P, P, P, P]
             lib.or_sparse_check_matching.argtypes = [i32, P, P, P, P, i64]
@@ -81,6 +84,7 @@ def _load():
             lib.or_cut_capacity.argtypes = [i32, i32, P, P, P, i32, i32, P, P]
             for f in (lib.or_brute_force, lib.or_hungarian, lib.or_cost_scaling,
                       lib.or_check_matching, lib.or_check_duals, lib.or_check_eps_cs,
+                      lib.or_certify_optimal,
                       lib.or_sparse_brute_force, lib.or_sparse_ssp, lib.or_sparse_check_matching,
                       lib.or_sparse_check_duals, lib.or_sparse_check_eps_cs,
                       lib.or_min_cut_brute, lib.or_maxflow_dinic, lib.or_cut_capacity):
@@ -170,6 +174,22 @@ def check_eps_cs(C, match, prices, eps: int = 1) -> int:
     m = np.ascontiguousarray(match, dtype=np.int32)
     p = np.ascontiguousarray(prices, dtype=np.int64)
     return _load().or_check_eps_cs(_ptr(C), C.shape[0], _ptr(m), _ptr(p), int(eps))
+
+
+def certify_optimal(C, match):
+    """Optimality of a perfect matching by the negative-cycle criterion
+    (Bellman-Ford on the alternating-cycle graph over the columns). Returns
+    ``(rc, u, v)``: rc 0 = optimal, with exact LP duals ``u, v`` tight on the
+    matching; 10 = not a permutation; 16 = a cheaper matching exists."""
+    C = _costs(C)
+    n = C.shape[0]
+    m = np.ascontiguousarray(match, dtype=np.int32)
+    if m.shape != (n,):
+        raise ValueError("match must hold one column per row")
+    u = np.zeros(n, dtype=np.int64)
+    v = np.zeros(n, dtype=np.int64)
+    rc = _load().or_certify_optimal(_ptr(C), n, _ptr(m), _ptr(u), _ptr(v))
+    return rc, u, v
 
 
 def eps_schedule(Ct: int, alpha: int = 10, eps0: int = 0, final_eps: int = 1):

@@ -26,7 +26,9 @@
  *                     of Algorithm 5.2 (unmatch all, p(x) implicit), and the
  *                     push/relabel step of Algorithm 5.4 taken as the
  *                     Goldberg-Kennedy double push (the paper's reference [9]).
- * and certificate checkers for any claimed matching. The same problem on
+ * and certificate checkers for any claimed matching, among them
+ * or_certify_optimal, which proves a matching optimal at any size with no
+ * duals given (Klein's negative-cycle criterion). The same problem on
  * sparse bipartite graphs (arcs in CSR form) has its own brute force,
  * successive-shortest-path solver and checkers (or_sparse_*, below), and
  * the paper's first problem, maximum s-t flow (Sect. 4), has Dinic's
@@ -341,6 +343,55 @@ int or_check_eps_cs(const int32_t *C, int32_t n, const int32_t *match,
         if (mine > mn + eps) return 15;
     }
     return OR_OK;
+}
+
+/* Optimality of a perfect matching with no duals given (the negative-cycle
+ * criterion of Klein 1967: an optimal flow admits no residual cycle of
+ * negative cost, which is the eps = 0 end of the eps-optimality of Sect. 5).
+ * In the assignment problem a residual cycle moves rows x_1..x_k each from
+ * its column M(x_i) to the next row's column, so M is optimal iff the graph
+ * on columns with an arc M(x) -> y of length C[x][y] - C[x][M(x)] for every
+ * row x and column y has no negative cycle. Bellman-Ford from a virtual
+ * source joined to every column by a zero-length arc: n + 1 vertices, so
+ * the distances settle within n sweeps unless a negative cycle exists.
+ * The settled distances d give LP duals v(y) = d(y) and
+ * u(x) = C[x][M(x)] - d(M(x)), tight on M and feasible (that is the
+ * fixpoint), written when u_out / v_out are not NULL.
+ * 0: optimal; 10: not a permutation; 16: a negative cycle (not optimal). */
+int or_certify_optimal(const int32_t *C, int32_t n, const int32_t *match,
+                       int64_t *u_out, int64_t *v_out)
+{
+    if (n < 0) return OR_INVALID;
+    if (n == 0) return OR_OK;
+    char *seen = calloc((size_t)n, 1);
+    int64_t *d = calloc((size_t)n, sizeof(int64_t));
+    if (!seen || !d) { free(seen); free(d); return OR_NOMEM; }
+    int rc = OR_OK;
+    for (int32_t x = 0; x < n && rc == OR_OK; ++x) {
+        const int32_t y = match[x];
+        if (y < 0 || y >= n || seen[y]) rc = 10;
+        else seen[y] = 1;
+    }
+    int changed = rc == OR_OK;
+    for (int32_t sweep = 0; changed && sweep <= n; ++sweep) {
+        changed = 0;
+        for (int32_t x = 0; x < n; ++x) {
+            const int32_t *row = C + (int64_t)x * n;
+            const int64_t from = d[match[x]] - (int64_t)row[match[x]];
+            for (int32_t y = 0; y < n; ++y)
+                if (from + (int64_t)row[y] < d[y]) { d[y] = from + (int64_t)row[y]; changed = 1; }
+        }
+    }
+    if (rc == OR_OK && changed) rc = 16;   /* still relaxing after n + 1 sweeps */
+    if (rc == OR_OK) {
+        for (int32_t x = 0; x < n; ++x) {
+            if (u_out) u_out[x] = (int64_t)C[(int64_t)x * n + match[x]] - d[match[x]];
+            if (v_out) v_out[x] = d[x];
+        }
+    }
+    free(seen);
+    free(d);
+    return rc;
 }
 
 /* ================================================================== */

@@ -69,6 +69,24 @@ def run_all_pins(orc):
             assert st["phases"] == len(orc.eps_schedule(Ct))
 
 
+def run_certify_pins(orc):
+    """The negative-cycle certificate against enumeration: over every
+    permutation of small matrices (heavy ties included) it accepts exactly
+    the optimal ones, and the duals it returns pass the LP check."""
+    rng = np.random.default_rng(11)
+    for t in range(40):
+        n = int(rng.integers(1, 6))
+        C = rng.integers(-6, 6 if t % 2 else 2, size=(n, n)).astype(np.int32)
+        best = _enumerate(C)
+        for p in itertools.permutations(range(n)):
+            m = np.array(p, dtype=np.int32)
+            rc, u, v = orc.certify_optimal(C, m)
+            assert (rc == 0) == (int(C[np.arange(n), m].sum()) == best)
+            if rc == 0:
+                assert orc.check_duals(C, m, u, v) == 0
+    assert orc.certify_optimal(np.zeros((3, 3), np.int32), np.array([0, 0, 1], np.int32))[0] == 10
+
+
 def _sparse_fixture(path):
     lines = [l for l in open(path) if l.strip() and not l.startswith("#")]
     c = lines[0].split()[1]
@@ -171,6 +189,7 @@ def main(argv):
         orc._LIB = os.path.join(tmp, "liboracle.so")
     try:
         run_all_pins(orc)
+        run_certify_pins(orc)
         run_sparse_pins(orc)
         run_maxflow_pins(orc)
     except AssertionError:

@@ -115,6 +115,45 @@ def test_batch_workload_sample_and_graph_replay(la):
     verify(flat2, off2, ns2, s2)
 
 
+def test_full_batch_workload_as_timed_is_certified_optimal(la):
+    """The whole 10,000-instance workload, tuned and launched the way the
+    throughput measurement launches it (autotuned CTA shape, slots and
+    alpha per size bucket; graph capture, then a timed-style replay). For
+    every instance: status 0, a permutation of the claimed cost, and the
+    oracle's negative-cycle certificate proves it optimal at any n. Every
+    250th instance is also solved by the oracle's Hungarian method."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+    from paper_1110_6231_gb300 import tune
+    flat, off, ns = synth.batch(10_000, 0)
+    dc, do, dn = (torch.from_numpy(a).cuda() for a in (flat, off, ns))
+    table = tune.autotune_batched(dc, do, dn, reps=1)
+    opt = tune.options_from_table(table, profile=True)
+    la.solve_batched(dc, do, dn, options=opt)
+    sol = la.solve_batched(dc, do, dn, options=opt)
+    assert sol.stats["rc"] == 0 and sol.stats["graph"] == 1 and sol.stats["failed"] == 0
+    costs = sol.costs.cpu().numpy()
+    match = sol.match.cpu().numpy()
+    status = sol.status.cpu().numpy()
+    mo = np.zeros(len(ns) + 1, dtype=np.int64)
+    mo[1:] = np.cumsum(ns.astype(np.int64))
+
+    def one(i):   # the oracle's C calls release the GIL
+        n = int(ns[i])
+        C = flat[off[i]:off[i] + n * n].reshape(n, n)
+        m = match[mo[i]:mo[i + 1]]
+        res = (int(status[i]), oracle.check_matching(C, m, int(costs[i])), oracle.certify_optimal(C, m)[0])
+        if i % 250 == 0:
+            res += (int(oracle.hungarian(C)[0] != costs[i]),)
+        return i, res
+
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        bad = [(i, r) for i, r in ex.map(one, range(len(ns))) if any(r)]
+    assert not bad, bad[:5]
+
+
 def test_invalid_sizes_flagged_per_instance(la):
     inst = [synth.uniform_costs(20, 0, 9, 1), synth.uniform_costs(40, 0, 9, 2)]
     flat, off, ns = pack(inst)

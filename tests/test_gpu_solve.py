@@ -99,6 +99,34 @@ def test_full_size_uniform_n4096(la):
         assert st["wide"] == 1 and st["phases"] == 10
 
 
+def test_full_size_uniform_n4096_as_timed(la):
+    """All ten stored n = 4096 optima through la_solve_ex the way the
+    throughput loop launches it: profiling on, the matrix resident on the
+    device, the torch stream, and alpha from the single-solve tuner's
+    candidates (32, its usual pick, on every seed; the others on two)."""
+    import torch
+    from paper_1110_6231_gb300 import tune
+    cases = [c for c in json.load(open(os.path.join(GOLDEN, "optimal_costs.json")))["cases"]
+             if c["workload"] == "uniform-n4096-c2^20"]
+    assert len(cases) == 10
+    n = 4096
+    match = torch.empty(n, dtype=torch.int32, device="cuda")
+    cost = torch.empty(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for c in cases:
+        C = synth.instance(c["workload"], c["seed"])
+        t = torch.from_numpy(C).cuda()
+        for a in (tune.DEFAULT_SINGLE_ALPHAS if c["seed"] < 2 else (32,)):
+            opt = la.la_options()
+            opt.profile = 1
+            opt.alpha = a
+            st = la.la_stats()
+            assert la.la_solve_ex(t, n, opt, stream, match, cost, st) == la.LA_OK
+            assert int(cost.item()) == c["cost"], (c["seed"], a)
+            assert oracle.check_matching(C, match.cpu().numpy(), c["cost"]) == 0
+            assert st.wide == 1 and st.scans > 0
+
+
 def test_full_size_geometric_n8192(la):
     """The n = 8192 geometric workload against the oracle's cost scaling."""
     C = synth.instance("geometric-n8192", 0)

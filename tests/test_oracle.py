@@ -213,3 +213,33 @@ def test_certificates_reject_bad_claims():
     worse[[0, 1]] = worse[[1, 0]]
     if oracle.check_matching(C, worse, h) != 0:  # a strictly worse matching
         assert oracle.check_eps_cs(C, worse, p, 1) == 15
+
+
+def test_certificate_without_duals_accepts_exactly_the_optima():
+    """or_certify_optimal (negative-cycle criterion): on every permutation of
+    small matrices it accepts exactly those of least cost (enumeration); on
+    larger instances it accepts the Hungarian optimum with duals that pass
+    the LP check, and rejects a matching one swap away from it."""
+    rng = np.random.default_rng(17)
+    for t in range(60):
+        n = int(rng.integers(1, 6))
+        C = rng.integers(-9, 9 if t % 3 else 2, size=(n, n)).astype(np.int32)
+        best = min(sum(int(C[x, p[x]]) for x in range(n)) for p in itertools.permutations(range(n)))
+        for p in itertools.permutations(range(n)):
+            m = np.array(p, dtype=np.int32)
+            rc, u, v = oracle.certify_optimal(C, m)
+            assert (rc == 0) == (int(C[np.arange(n), m].sum()) == best)
+            if rc == 0:
+                assert oracle.check_duals(C, m, u, v) == 0
+    for C in (synth.uniform_costs(300, 0, 10**6, 3), synth.geometric_costs(256, 4)):
+        cost, m, _, _ = oracle.hungarian(C)
+        rc, u, v = oracle.certify_optimal(C, m)
+        assert rc == 0 and oracle.check_duals(C, m, u, v) == 0
+        # every strictly worse neighbour (two rows swap columns) is rejected
+        for a, b in ((0, 1), (5, 77), (100, 200)):
+            w = m.copy()
+            w[a], w[b] = m[b], m[a]
+            worse = int(C[np.arange(C.shape[0]), w].sum()) > cost
+            assert (oracle.certify_optimal(C, w)[0] == 16) == worse
+    assert oracle.certify_optimal(np.zeros((0, 0), np.int32), np.zeros(0, np.int32))[0] == 0
+    assert oracle.certify_optimal(np.eye(3, dtype=np.int32), np.array([1, 1, 2], np.int32))[0] == 10

@@ -49,6 +49,12 @@ MUTANTS = [
      "res[2 * a + 1] = cap[a];   to[2 * a + 1] = tail[a];"),
     ("min-cut-brute-allows-t-inside", "if (!(mask >> s & 1u) || (mask >> t & 1u)) continue;",
      "if (!(mask >> s & 1u)) continue;"),
+    ("certify-arc-reversed", "const int64_t from = d[match[x]] - (int64_t)row[match[x]];",
+     "const int64_t from = d[match[x]] + (int64_t)row[match[x]];"),
+    ("certify-one-sweep", "for (int32_t sweep = 0; changed && sweep <= n; ++sweep) {",
+     "for (int32_t sweep = 0; changed && sweep < 1; ++sweep) {"),
+    ("certify-dual-from-own-row", "if (u_out) u_out[x] = (int64_t)C[(int64_t)x * n + match[x]] - d[match[x]];",
+     "if (u_out) u_out[x] = (int64_t)C[(int64_t)x * n + x] - d[match[x]];"),
     ("sparse-brute-force-ignores-arcs", "s = w[x][perm[x]] >= OR_INF ? OR_INF : s + w[x][perm[x]];",
      "s = w[x][perm[x]] >= OR_INF ? s : s + w[x][perm[x]];"),
 ]
