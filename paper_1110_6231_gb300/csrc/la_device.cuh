@@ -122,11 +122,6 @@ __device__ __forceinline__ ulonglong2 ld_q2(const unsigned long long *p) {
 // --- best / second best ---------------------------------------------------
 
 template <typename V>
-__device__ __forceinline__ V shfl_xor_v(V v, int m) {
-    return __shfl_xor_sync(0xffffffffu, v, m);
-}
-
-template <typename V>
 struct ScanResult {
     V b1, b2;      // best and second-best value over the row
     V c1;          // scaled cost of the best column
@@ -193,35 +188,63 @@ __device__ __forceinline__ void lanek_push(LaneK<V, K> &t, V v, int y) {
     t.w[0] = lt[0] ? y : t.w[0];
 }
 
-// Butterfly merge of the lanes' (b1, w, c1, b2): every lane ends with the
-// row's best value, its column (lowest index among equal minima), that
-// column's scaled cost and the second-best value.
-template <typename V>
-__device__ __forceinline__ void warp_merge(ScanResult<V> &r) {
+// Insert (v, y) ordering equal values by column: merges lists that were
+// built from interleaved streams, so that the result is the K least pairs in
+// (value, column) order, as one stream in column order would have kept.
+template <typename V, int K>
+__device__ __forceinline__ void lanek_insert(LaneK<V, K> &t, V v, int y) {
+    bool lt[K];
 #pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-        const V o1 = shfl_xor_v(r.b1, m);
-        const V o2 = shfl_xor_v(r.b2, m);
-        const V oc = shfl_xor_v(r.c1, m);
-        const int ow = __shfl_xor_sync(0xffffffffu, r.w, m);
-        const V lo2 = o2 < r.b2 ? o2 : r.b2;
-        const V hi1 = o1 > r.b1 ? o1 : r.b1;
-        r.b2 = lo2 < hi1 ? lo2 : hi1;
-        const bool take = (o1 < r.b1) || (o1 == r.b1 && (unsigned)ow < (unsigned)r.w);
-        r.b1 = take ? o1 : r.b1;
-        r.c1 = take ? oc : r.c1;
-        r.w = take ? ow : r.w;
+    for (int k = 0; k < K; ++k) lt[k] = v < t.b[k] || (v == t.b[k] && (unsigned)y < (unsigned)t.w[k]);
+#pragma unroll
+    for (int k = K - 1; k > 0; --k) {
+        t.b[k] = lt[k - 1] ? t.b[k - 1] : (lt[k] ? v : t.b[k]);
+        t.w[k] = lt[k - 1] ? t.w[k - 1] : (lt[k] ? y : t.w[k]);
+    }
+    t.b[0] = lt[0] ? v : t.b[0];
+    t.w[0] = lt[0] ? y : t.w[0];
+}
+
+__device__ __forceinline__ unsigned lane_id() {
+    unsigned l;
+    asm("mov.u32 %0, %%laneid;" : "=r"(l));
+    return l;
+}
+
+// Warp-wide minimum of an unsigned value by the hardware reduction
+// (redux.sync, 32-bit): a 64-bit value is reduced on its high word, then on
+// its low word over the lanes that hold the least high word. Two or three
+// instructions replace a five-round shuffle butterfly, which matters in the
+// dependent chain of one warp's bid when no other warp hides the latency.
+template <typename V>
+__device__ __forceinline__ V warp_min(V v) {
+    static_assert(sizeof(V) == 4 || sizeof(V) == 8, "32- or 64-bit unsigned values");
+    if constexpr (sizeof(V) == 4) {
+        return (V)__reduce_min_sync(0xffffffffu, (unsigned)v);
+    } else {
+        const unsigned hi = __reduce_min_sync(0xffffffffu, (unsigned)(v >> 32));
+        const unsigned lo = __reduce_min_sync(0xffffffffu, (unsigned)(v >> 32) == hi ? (unsigned)v : 0xffffffffu);
+        return ((V)hi << 32) | (V)lo;
     }
 }
 
+// Merge of the lanes' (b1, w, c1, b2): every lane ends with the row's best
+// value, its column (the lowest index among equal minima), that column's
+// scaled cost and the second-best value, i.e. the least of all the lanes'
+// values once one copy of the best is taken out: the winning lane offers
+// its own second best, every other lane its best.
 template <typename V>
-__device__ __forceinline__ V warp_min(V v) {
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-        const V o = shfl_xor_v(v, m);
-        v = o < v ? o : v;
-    }
-    return v;
+__device__ __forceinline__ void warp_merge(ScanResult<V> &r) {
+    const V m1 = warp_min<V>(r.b1);
+    const unsigned w = __reduce_min_sync(0xffffffffu, r.b1 == m1 ? (unsigned)r.w : 0xffffffffu);
+    const unsigned own = __ballot_sync(0xffffffffu, r.b1 == m1 && (unsigned)r.w == w);
+    const int src = __ffs(own) - 1;
+    const V c1 = __shfl_sync(0xffffffffu, r.c1, src);
+    const V m2 = warp_min<V>((int)lane_id() == src ? r.b2 : r.b1);
+    r.b1 = m1;
+    r.b2 = m2;
+    r.c1 = c1;
+    r.w = (int)w;
 }
 
 }  // namespace la

@@ -33,18 +33,28 @@ struct RowLists {
     unsigned long long *theta;  // [n]: 0 = no list, ~0 = unbounded, else theta + R + 1
 };
 
-// One lane's list entries of row x (two 128-bit loads at L2).
+// One lane's list entries of row x (two 128-bit loads). Lists are written
+// by whichever SM scans the row, so a kernel that runs on many SMs reads
+// them at L2 (.cg). A kernel whose every warp runs on one SM (ONE_SM) may
+// cache them in L1 (.ca): the SM's own stores keep its L1 coherent, and L1
+// holds nothing from earlier kernels, so the rows that its chains keep
+// revisiting are read at L1 latency.
 struct LaneList {
     int y[kListK];
     int c[kListK];
 };
+template <bool ONE_SM>
+__device__ __forceinline__ int4 ld_list4(const int *p) {
+    return ONE_SM ? __ldca(reinterpret_cast<const int4 *>(p)) : __ldcg(reinterpret_cast<const int4 *>(p));
+}
+template <bool ONE_SM = false>
 __device__ __forceinline__ LaneList load_lane_list(const RowLists &L, int row, int lane) {
     const size_t base = (size_t)row * kListLen + kListK * lane;
     LaneList e;
 #pragma unroll
     for (int g = 0; g < kListK / 4; ++g) {
-        const int4 yy = __ldcg(reinterpret_cast<const int4 *>(L.cols + base) + g);
-        const int4 cc = __ldcg(reinterpret_cast<const int4 *>(L.costs + base) + g);
+        const int4 yy = ld_list4<ONE_SM>(L.cols + base + 4 * g);
+        const int4 cc = ld_list4<ONE_SM>(L.costs + base + 4 * g);
         e.y[4 * g] = yy.x; e.y[4 * g + 1] = yy.y; e.y[4 * g + 2] = yy.z; e.y[4 * g + 3] = yy.w;
         e.c[4 * g] = cc.x; e.c[4 * g + 1] = cc.y; e.c[4 * g + 2] = cc.z; e.c[4 * g + 3] = cc.w;
     }
@@ -89,13 +99,21 @@ struct SharedKeyPrices {
 
 // Full scan of row x: v(x,y) = (C[x][y] - cmin)(n+1) + q(y) for every y.
 // Writes x's candidate list when lists are on.
-template <bool WIDE, bool VEC, class P>
+//
+// The insertion network is one long dependent chain per lane. A warp that
+// scans alone on its SM (the end of a phase) has no other warps to overlap
+// it with, so NCH independent chains take interleaved columns of each int4
+// group (chain c the components c, c + NCH, ...) and are merged at the end.
+template <bool WIDE, bool VEC, int NCH, class P>
 __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int row, int n, int cmin,
                                           uint32_t np1, const P &prices, int lane,
                                           const RowLists &L, unsigned long long R) {
+    static_assert(NCH == 1 || NCH == 2 || NCH == 4, "one, two or four chains");
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
-    LaneK<V, kListK> t;
-    lanek_init(t);
+    LaneK<V, kListK> ch[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) lanek_init(ch[c]);
+    LaneK<V, kListK> &t = ch[0];
     int cnt;
     if (VEC) {
         const int4 *r4 = reinterpret_cast<const int4 *>(crow);
@@ -107,11 +125,16 @@ __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int 
             const int y = j << 2;
             V qa, qb, qc, qd;
             prices.q4(y, qa, qb, qc, qd);
-            lanek_push<V, kListK>(t, (V)(uint32_t)(c.x - cmin) * np1 + qa, y);
-            lanek_push<V, kListK>(t, (V)(uint32_t)(c.y - cmin) * np1 + qb, y + 1);
-            lanek_push<V, kListK>(t, (V)(uint32_t)(c.z - cmin) * np1 + qc, y + 2);
-            lanek_push<V, kListK>(t, (V)(uint32_t)(c.w - cmin) * np1 + qd, y + 3);
+            lanek_push<V, kListK>(ch[0], (V)(uint32_t)(c.x - cmin) * np1 + qa, y);
+            lanek_push<V, kListK>(ch[1 % NCH], (V)(uint32_t)(c.y - cmin) * np1 + qb, y + 1);
+            lanek_push<V, kListK>(ch[2 % NCH], (V)(uint32_t)(c.z - cmin) * np1 + qc, y + 2);
+            lanek_push<V, kListK>(ch[3 % NCH], (V)(uint32_t)(c.w - cmin) * np1 + qd, y + 3);
         }
+#pragma unroll
+        for (int c = 1; c < NCH; ++c)
+#pragma unroll
+            for (int k = 0; k < kListK; ++k)   // an empty entry (~0, -1) inserts nothing
+                lanek_insert<V, kListK>(t, ch[c].b[k], ch[c].w[k]);
     } else {
         cnt = lane < n ? ((n - lane + 31) >> 5) : 0;
         for (int y = lane; y < n; y += 32) {
@@ -147,12 +170,12 @@ __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int 
 // Short scan of row x over its candidate list (kListK entries per lane).
 // The list entries and the row's bound theta are loaded in the same round
 // trip; the prices are gathered only when a list exists (theta != 0).
-template <bool WIDE, class P>
+template <bool WIDE, bool ONE_SM, class P>
 __device__ __forceinline__ auto list_scan(int row, int n, int cmin, uint32_t np1, const P &prices, int lane,
                                           const RowLists &L, unsigned long long &theta) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
-    theta = __ldcg(L.theta + row);
-    const LaneList e = load_lane_list(L, row, lane);
+    theta = ONE_SM ? __ldca(L.theta + row) : __ldcg(L.theta + row);
+    const LaneList e = load_lane_list<ONE_SM>(L, row, lane);
     const V inf = (V)~(V)0;
     ScanResult<V> r{inf, inf, 0, INT_MAX};
     if (theta == 0) return r;            // no list for this row yet (uniform across the warp)
@@ -183,7 +206,7 @@ __device__ __forceinline__ auto list_scan(int row, int n, int cmin, uint32_t np1
 // Best and second best of row x for its next bid: from the candidate list
 // when it decides the row (see RowLists), else from a full scan that also
 // rebuilds the list. The second best may be the lower bound theta.
-template <bool WIDE, bool VEC, class P>
+template <bool WIDE, bool VEC, bool ONE_SM, class P>
 __device__ __forceinline__ auto scan_for_bid(const int32_t *__restrict__ C, int row, int n, int cmin,
                                              uint32_t np1, const P &prices, int lane,
                                              const RowLists &L, unsigned long long R, bool &full) {
@@ -192,7 +215,7 @@ __device__ __forceinline__ auto scan_for_bid(const int32_t *__restrict__ C, int 
     bool ok = false;
     if (L.cols) {
         unsigned long long th = 0;
-        t = list_scan<WIDE>(row, n, cmin, np1, prices, lane, L, th);
+        t = list_scan<WIDE, ONE_SM>(row, n, cmin, np1, prices, lane, L, th);
         if (th != 0) {
             // Exact when the list's second best does not exceed theta: every
             // other column is >= theta, so the list holds the row's best and
@@ -204,7 +227,7 @@ __device__ __forceinline__ auto scan_for_bid(const int32_t *__restrict__ C, int 
         }
     }
     full = !ok;
-    if (!ok) t = full_scan<WIDE, VEC>(C + (size_t)row * n, row, n, cmin, np1, prices, lane, L, R);
+    if (!ok) t = full_scan<WIDE, VEC, ONE_SM ? (WIDE ? 4 : 2) : 1>(C + (size_t)row * n, row, n, cmin, np1, prices, lane, L, R);
     return t;
 }
 

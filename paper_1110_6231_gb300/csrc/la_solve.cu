@@ -46,7 +46,10 @@ constexpr int kMaxDevices = 64;
 constexpr int kDefaultBlock = 256;
 constexpr unsigned long long kRangeLimit = 1ull << 40;  // C~ limit (LA_ERR_OVERFLOW)
 constexpr int kTailMaxN = 16384;      // shared-memory keys of the tail kernel (128 KB)
-constexpr int kTailThreads = 1024;
+// Threads of the one-CTA tail kernel: 64-bit values run four insertion
+// chains per full scan and need the registers of a 512-thread CTA.
+template <bool WIDE>
+constexpr int tail_threads() { return WIDE ? 512 : 1024; }
 constexpr int kDefaultTailRows = 32;
 constexpr unsigned kTailGiveUpFull = 64;   // full scans before the tail kernel may give its rows back
 constexpr int kDefaultPuRounds = 0;   // global price updates per phase (off unless asked)
@@ -233,7 +236,7 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
         ++pending;
         ++total;
         bool was_full = false;
-        const auto t = scan_for_bid<WIDE, VEC>(C, row, n, cmin, np1, MirrorPrices<WIDE>{qmv}, lane, L, R, was_full);
+        const auto t = scan_for_bid<WIDE, VEC, false>(C, row, n, cmin, np1, MirrorPrices<WIDE>{qmv}, lane, L, R, was_full);
         if (was_full) ++full;
         else ++hits;
         __syncwarp();
@@ -303,7 +306,7 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
 // row still free goes back to the row queue for a refine launch over the
 // whole grid that follows the tail kernel in every phase.
 template <bool WIDE, bool VEC>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(tail_threads<WIDE>())
 k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
        unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
        Ctrl *__restrict__ ctrl, unsigned long long budget, RowLists L, const int *__restrict__ tail_rows,
@@ -375,13 +378,17 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
         ++pending;
         ++total;
         bool was_full = false;
-        const auto t = scan_for_bid<WIDE, VEC>(C, row, n, cmin, np1, prices, lane, L, R, was_full);
+        const auto t = scan_for_bid<WIDE, VEC, true>(C, row, n, cmin, np1, prices, lane, L, R, was_full);
         if (was_full) ++full;
         else ++hits;
-        if (lane == 0) {
-            const unsigned f = was_full ? atomicAdd(&s_full, 1u) + 1 : s_full;
-            const unsigned h = was_full ? s_hits : atomicAdd(&s_hits, 1u) + 1;
-            if (f >= kTailGiveUpFull && 4 * f > f + h) *stop = 1;
+        if (lane == 0) {   // the share of full scans can only pass 1/4 when a full scan is counted
+            if (was_full) {
+                const unsigned f = atomicAdd(&s_full, 1u) + 1;
+                const unsigned h = *reinterpret_cast<volatile unsigned *>(&s_hits);
+                if (f >= kTailGiveUpFull && 3 * f > h) *stop = 1;
+            } else {
+                atomicAdd(&s_hits, 1u);
+            }
         }
         __syncwarp();
         const unsigned long long nq = (unsigned long long)(t.b1 - t.c1) + (t.b2 - t.b1) + eps;
@@ -851,7 +858,7 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
             cudaError_t e = cudaFuncSetAttribute(k_tail<WIDE, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
         }
-        k_tail<WIDE, VEC><<<1, kTailThreads, smem, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget,
+        k_tail<WIDE, VEC><<<1, tail_threads<WIDE>(), smem, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget,
                                                          L, ws.tail_rows, ws.qlist[0], ws.qlist[1]);
         if (ev_fin) {
             cudaError_t e = cudaEventRecord(ev_fin, s);
