@@ -61,6 +61,19 @@ __device__ __forceinline__ LaneList load_lane_list(const RowLists &L, int row, i
     return e;
 }
 
+// A row's list loaded ahead of its scan (row = -1: nothing loaded).
+struct ListAhead {
+    int row;
+    unsigned long long theta;
+    LaneList e;
+};
+template <bool ONE_SM>
+__device__ __forceinline__ void load_ahead(ListAhead &a, const RowLists &L, int row, int lane) {
+    a.row = row;
+    a.theta = ONE_SM ? __ldca(L.theta + row) : __ldcg(L.theta + row);
+    a.e = load_lane_list<ONE_SM>(L, row, lane);
+}
+
 template <bool WIDE>
 __device__ __forceinline__ auto load_q(const void *qmv, int y) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
@@ -169,13 +182,21 @@ __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int 
 
 // Short scan of row x over its candidate list (kListK entries per lane).
 // The list entries and the row's bound theta are loaded in the same round
-// trip; the prices are gathered only when a list exists (theta != 0).
+// trip, or were loaded ahead (ahead.row == x); the prices are gathered only
+// when a list exists (theta != 0).
 template <bool WIDE, bool ONE_SM, class P>
 __device__ __forceinline__ auto list_scan(int row, int n, int cmin, uint32_t np1, const P &prices, int lane,
-                                          const RowLists &L, unsigned long long &theta) {
+                                          const RowLists &L, const ListAhead &ahead,
+                                          unsigned long long &theta) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
-    theta = ONE_SM ? __ldca(L.theta + row) : __ldcg(L.theta + row);
-    const LaneList e = load_lane_list<ONE_SM>(L, row, lane);
+    LaneList e;
+    if (ahead.row == row) {   // uniform across the warp
+        theta = ahead.theta;
+        e = ahead.e;
+    } else {
+        theta = ONE_SM ? __ldca(L.theta + row) : __ldcg(L.theta + row);
+        e = load_lane_list<ONE_SM>(L, row, lane);
+    }
     const V inf = (V)~(V)0;
     ScanResult<V> r{inf, inf, 0, INT_MAX};
     if (theta == 0) return r;            // no list for this row yet (uniform across the warp)
@@ -209,13 +230,14 @@ __device__ __forceinline__ auto list_scan(int row, int n, int cmin, uint32_t np1
 template <bool WIDE, bool VEC, bool ONE_SM, class P>
 __device__ __forceinline__ auto scan_for_bid(const int32_t *__restrict__ C, int row, int n, int cmin,
                                              uint32_t np1, const P &prices, int lane,
-                                             const RowLists &L, unsigned long long R, bool &full) {
+                                             const RowLists &L, unsigned long long R, bool &full,
+                                             const ListAhead &ahead) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
     ScanResult<V> t;
     bool ok = false;
     if (L.cols) {
         unsigned long long th = 0;
-        t = list_scan<WIDE, ONE_SM>(row, n, cmin, np1, prices, lane, L, th);
+        t = list_scan<WIDE, ONE_SM>(row, n, cmin, np1, prices, lane, L, ahead, th);
         if (th != 0) {
             // Exact when the list's second best does not exceed theta: every
             // other column is >= theta, so the list holds the row's best and

@@ -236,7 +236,8 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
         ++pending;
         ++total;
         bool was_full = false;
-        const auto t = scan_for_bid<WIDE, VEC, false>(C, row, n, cmin, np1, MirrorPrices<WIDE>{qmv}, lane, L, R, was_full);
+        const auto t = scan_for_bid<WIDE, VEC, false>(C, row, n, cmin, np1, MirrorPrices<WIDE>{qmv}, lane, L, R, was_full,
+                                                           ListAhead{-1, 0ull, {}});
         if (was_full) ++full;
         else ++hits;
         __syncwarp();
@@ -344,6 +345,8 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
     const SharedKeyPrices<WIDE> prices{skey};
     volatile int *stop = &s_stop;
     int row = -1;
+    ListAhead ahead;
+    ahead.row = -1;
     unsigned long long wins = 0, displaced = 0, total = 0, full = 0, hits = 0;
     unsigned pending = 0;
     for (;;) {
@@ -378,7 +381,7 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
         ++pending;
         ++total;
         bool was_full = false;
-        const auto t = scan_for_bid<WIDE, VEC, true>(C, row, n, cmin, np1, prices, lane, L, R, was_full);
+        const auto t = scan_for_bid<WIDE, VEC, true>(C, row, n, cmin, np1, prices, lane, L, R, was_full, ahead);
         if (was_full) ++full;
         else ++hits;
         if (lane == 0) {   // the share of full scans can only pass 1/4 when a full scan is counted
@@ -397,9 +400,19 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
             break;
         }
         const unsigned long long nk = pack_key(nq, (uint32_t)row);
+        // The row this bid displaces, as far as the column's key tells now:
+        // its list is loaded here, so that the load overlaps the commit. It
+        // is used only if the commit finds the same key (then that row stayed
+        // matched throughout, and no warp can have been rewriting its list).
+        // Only the 512-thread (64-bit) kernel has the registers for it.
+        const unsigned long long cur = *reinterpret_cast<volatile unsigned long long *>(skey + t.w);
+        ahead.row = -1;
+        if (WIDE && L.cols && cur > nk && key_mate(cur) != kNone)
+            load_ahead<true>(ahead, L, (int)key_mate(cur), lane);
         unsigned long long old = 0;
         if (lane == 0) old = atomicMin(skey + t.w, nk);
         old = __shfl_sync(0xffffffffu, old, 0);
+        if (old != cur) ahead.row = -1;
         if (old > nk) {
             ++wins;
             const uint32_t m = key_mate(old);

@@ -33,7 +33,7 @@ DEFAULT_ALPHAS = (4, 6, 8, 10, 16)
 DEFAULT_SHAPES = ((256, 2), (512, 2), (512, 4), (1024, 8))   # (threads per CTA, resident instances)
 
 
-DEFAULT_SINGLE_ALPHAS = (8, 10, 16, 24, 32)
+DEFAULT_SINGLE_ALPHAS = (8, 10, 16, 24, 32, 48, 64)
 
 
 def autotune_alpha(samples, *, alphas=DEFAULT_SINGLE_ALPHAS, reps: int = 3) -> dict:

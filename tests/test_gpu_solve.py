@@ -102,8 +102,8 @@ def test_full_size_uniform_n4096(la):
 def test_full_size_uniform_n4096_as_timed(la):
     """All ten stored n = 4096 optima through la_solve_ex the way the
     throughput loop launches it: profiling on, the matrix resident on the
-    device, the torch stream, and alpha from the single-solve tuner's
-    candidates (32, its usual pick, on every seed; the others on two)."""
+    device, the torch stream, and every alpha the single-solve tuner may
+    pick."""
     import torch
     from paper_1110_6231_gb300 import tune
     cases = [c for c in json.load(open(os.path.join(GOLDEN, "optimal_costs.json")))["cases"]
@@ -116,7 +116,7 @@ def test_full_size_uniform_n4096_as_timed(la):
     for c in cases:
         C = synth.instance(c["workload"], c["seed"])
         t = torch.from_numpy(C).cuda()
-        for a in (tune.DEFAULT_SINGLE_ALPHAS if c["seed"] < 2 else (32,)):
+        for a in tune.DEFAULT_SINGLE_ALPHAS:
             opt = la.la_options()
             opt.profile = 1
             opt.alpha = a
