@@ -458,6 +458,26 @@ la_status la_maxflow_grid_ex(const int32_t *cap, const int32_t *src, const int32
 la_status la_solve_noalloc(const int32_t *cost, int32_t n, void *stream,
                            int32_t *match_out, int64_t *cost_out);
 
+/*
+ * la_probe_read -- read-bandwidth probe (a measurement utility; no solve
+ * uses it). It supplies the measured peak of the cache level a scan's data
+ * comes from: a 64 MiB cost matrix (n = 4096) stays in the 129 MB L2 across
+ * the phases of a solve, so the refine's arc-scan rate is judged against the
+ * L2 read rate, which no vendor figure states.
+ *   buf    device buffer of `bytes` bytes, 16-byte aligned; read only.
+ *   bytes  a multiple of 16, > 0.
+ *   reps   passes over the buffer in one launch (>= 1); every thread of a
+ *          grid-stride kernel (4 CTAs of 512 threads per SM) reads the same
+ *          addresses in every pass with 128-bit loads cached at L2 only
+ *          (.cg), so passes after the first hit L2 whenever the buffer fits.
+ *   stream a cudaStream_t (NULL: the legacy default stream).
+ *   ms_out host float: the launch's duration by CUDA events on `stream`.
+ * The achieved rate is bytes * reps / time. Blocks until done (it
+ * synchronises on its events). Returns LA_ERR_INVALID on a bad argument
+ * (nothing enqueued) and LA_ERR_CUDA on a CUDA error.
+ */
+la_status la_probe_read(const void *buf, size_t bytes, int32_t reps, void *stream, float *ms_out);
+
 #ifdef __cplusplus
 }
 #endif

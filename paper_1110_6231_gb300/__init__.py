@@ -194,6 +194,8 @@ def lib() -> ctypes.CDLL:
             L.la_solve_warm.argtypes = [P, i32, P, P, P, P, P]
             L.la_dual_certificate.argtypes = [P, i32, P, P, P, P]
             L.la_dual_certificate.restype = ctypes.c_int
+            L.la_probe_read.argtypes = [P, ctypes.c_size_t, i32, P, ctypes.POINTER(ctypes.c_float)]
+            L.la_probe_read.restype = ctypes.c_int
             for f in (L.la_features, L.la_predictor_forward, L.la_predictor_train_step,
                       L.la_predict_prices, L.la_predict_prices_ex, L.la_solve_warm):
                 f.restype = ctypes.c_int
@@ -330,6 +332,22 @@ def dual_certificate(C, match, *, stream=None):
     if rc != LA_OK:
         raise LaError(rc, "la_dual_certificate")
     return u[:n], v[:n]
+
+
+def la_probe_read(buf, nbytes, reps, stream, ms_out) -> int:
+    return lib().la_probe_read(_ptr(buf), int(nbytes), int(reps), _stream(stream), ms_out)
+
+
+def probe_read_gbps(buf, reps: int, *, stream=None) -> float:
+    """Read rate (GB/s) of ``reps`` passes over the CUDA tensor ``buf`` in one
+    launch of the library's probe kernel (128-bit loads cached at L2 only):
+    the L2 rate when ``buf`` fits in L2, the HBM rate when it is far larger."""
+    nbytes = buf.numel() * buf.element_size()
+    ms = ctypes.c_float(0.0)
+    rc = la_probe_read(buf, nbytes, reps, stream, ctypes.byref(ms))
+    if rc != LA_OK:
+        raise LaError(rc, "la_probe_read")
+    return nbytes * reps / (ms.value * 1e-3) / 1e9
 
 
 def la_status_string(status: int) -> str:

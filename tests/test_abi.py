@@ -94,3 +94,16 @@ def test_invalid_arguments_rejected_on_host(libla):
     assert libla.la_solve(None, 4, None, None, ctypes.c_void_p(8)) == 1      # NULL cost
     assert libla.la_solve(ctypes.c_void_p(8), 4, None, None, None) == 1      # NULL cost_out
     assert libla.la_solve(ctypes.c_void_p(8), (1 << 20), None, None, ctypes.c_void_p(8)) == 1
+
+
+def test_probe_rejects_bad_arguments_on_host(libla):
+    f = libla.la_probe_read
+    f.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_void_p,
+                  ctypes.POINTER(ctypes.c_float)]
+    f.restype = ctypes.c_int
+    ms = ctypes.c_float()
+    assert f(None, 16, 1, None, ctypes.byref(ms)) == 1                     # NULL buffer
+    assert f(ctypes.c_void_p(256), 24, 1, None, ctypes.byref(ms)) == 1     # not a multiple of 16
+    assert f(ctypes.c_void_p(256), 16, 0, None, ctypes.byref(ms)) == 1     # no pass
+    assert f(ctypes.c_void_p(264), 16, 1, None, ctypes.byref(ms)) == 1     # misaligned
+    assert f(ctypes.c_void_p(256), 16, 1, None, None) == 1                 # NULL ms_out
