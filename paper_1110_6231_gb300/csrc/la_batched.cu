@@ -610,8 +610,9 @@ la_status ensure_bws(BatchWorkspace &w, int64_t B, int max_n) {
 // per device, so it is set on every call; both are host calls, no GPU work).
 template <int BLOCK>
 int solve_grid(int num_sms, size_t smem) {
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_batch_solve<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // Always set: the kernel's static shared memory (the slot records) and
+    // `smem` together must fit, and 48 KB is the limit without it.
+    cudaFuncSetAttribute(k_batch_solve<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int o = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch_solve<BLOCK>, BLOCK, smem);
     return num_sms * std::max(1, o);

@@ -867,7 +867,8 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
     if (tail_T > 0) {
         ++launches;
         const int smem = (int)(sizeof(unsigned long long) * n);
-        if (smem > 48 * 1024) {   // a per-device attribute: set on every launch (a host call, no GPU work)
+        {   // A per-device attribute, set on every launch (a host call, no GPU work). Without it the
+            // kernel's static shared memory and `smem` together may not pass 48 KB (n near 6144).
             cudaError_t e = cudaFuncSetAttribute(k_tail<WIDE, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
         }

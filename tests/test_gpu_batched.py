@@ -95,6 +95,16 @@ def test_slots_bounded_by_shared_memory(la):
     verify(flat, off, ns, sol)
 
 
+def test_shared_memory_at_exactly_48KB(la):
+    """Six slots of max_n = 1024 keys are exactly 48 KB of dynamic shared
+    memory; with the kernel's slot records the CTA needs more than 48 KB,
+    so the launch must opt in to the larger size."""
+    flat, off, ns = synth.batch(30, 9, lo=16, hi=300)
+    sol = run(la, flat, off, ns, slots=6, max_n=1024)
+    assert sol.stats["rc"] == 0 and sol.stats["slots"] == 6
+    verify(flat, off, ns, sol)
+
+
 def test_batch_workload_sample_and_graph_replay(la):
     """A sample of the 10,000-instance workload (n log-uniform in [16, 1024],
     half uniform [0, 10^4], half geometric), solved twice from the cached

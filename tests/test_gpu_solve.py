@@ -127,6 +127,18 @@ def test_full_size_uniform_n4096_as_timed(la):
             assert st.wide == 1 and st.scans > 0
 
 
+@pytest.mark.parametrize("n", [6139, 6144])
+def test_tail_shared_memory_near_48KB(la, n):
+    """8n bytes of column keys plus the tail kernel's own shared variables
+    pass 48 KB for n = 6139..6144: the launch must opt in to the larger
+    shared memory even though 8n alone does not exceed 48 KB."""
+    C = synth.uniform_costs(n, 0, 50, 11 + n)
+    cost, match, prices, st = gpu_solve(la, C)
+    assert oracle.check_matching(C, match, cost) == 0
+    assert oracle.check_eps_cs(C, match, prices, 1) == 0
+    assert st["tail_phases"] > 0
+
+
 def test_full_size_geometric_n8192(la):
     """The n = 8192 geometric workload against the oracle's cost scaling."""
     C = synth.instance("geometric-n8192", 0)
