@@ -47,6 +47,7 @@ __all__ = [
     "uniform_doubles",
     "normal_pairs",
     "uniform_costs",
+    "uniform_costs_torch",
     "geometric_costs",
     "batch_sizes",
     "batch",
@@ -107,6 +108,42 @@ def uniform_ints(seed: int, tag: int, count: int, lo: int, hi: int,
     z = u64_stream(seed, tag, count, start) >> np.uint64(32)
     with np.errstate(over="ignore"):
         return (np.int64(lo) + ((z * np.uint64(r)) >> np.uint64(32)).astype(np.int64))
+
+
+def _i64(v: int) -> int:
+    """The int64 with the bit pattern of the 64-bit word ``v``."""
+    v &= 0xFFFFFFFFFFFFFFFF
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _t_srl(x, k: int):
+    """Logical right shift of an int64 tensor (``>>`` is arithmetic)."""
+    return (x >> k) & ((1 << (64 - k)) - 1)
+
+
+def _t_mix64(z):
+    z = (z ^ _t_srl(z, 30)) * _i64(int(_M1))
+    z = (z ^ _t_srl(z, 27)) * _i64(int(_M2))
+    return z ^ _t_srl(z, 31)
+
+
+def uniform_costs_torch(n: int, lo: int, hi: int, seed: int, device="cpu"):
+    """``uniform_costs(n, lo, hi, seed)`` drawn with torch on ``device``: the
+    same SplitMix64 stream and multiply-shift map in int64 arithmetic (which
+    wraps modulo 2^64 like the uint64 one), so the int32 result is equal bit
+    for bit. Many large instances can be drawn on the GPU in milliseconds."""
+    import torch
+    r = hi - lo + 1
+    if n < 0 or not (1 <= r <= 1 << 32) or not (-(1 << 31) <= lo <= hi < (1 << 31)):
+        raise ValueError("bad size or range")
+    with np.errstate(over="ignore"):
+        key = int(_mix64(np.array([(seed * 0x100 + _TAG_UNIFORM) & 0xFFFFFFFFFFFFFFFF],
+                                  dtype=np.uint64) * _GAMMA)[0])
+    ctr = torch.arange(1, n * n + 1, dtype=torch.int64, device=device)
+    z = _t_mix64(ctr * _i64(int(_GAMMA)) + _i64(key))
+    z = _t_srl(z, 32)
+    v = _t_srl(z * r, 32) + lo
+    return v.to(torch.int32).view(n, n)
 
 
 def uniform_doubles(seed: int, tag: int, count: int, start: int = 0) -> np.ndarray:

@@ -164,6 +164,35 @@ def test_full_batch_workload_as_timed_is_certified_optimal(la):
     assert not bad, bad[:5]
 
 
+def test_concurrent_n4096_instances_one_per_cta(la):
+    """The ten stored n = 4096 optima (costs in [0, 2^20), 64-bit reduced
+    costs) solved concurrently, one instance per CTA, from matrices drawn on
+    the GPU by the torch twin of the generator (checked against the stored
+    digests first)."""
+    import hashlib
+    import json
+    import os
+
+    import torch
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "optimal_costs.json")
+    cases = [c for c in json.load(open(path))["cases"] if c["workload"] == "uniform-n4096-c2^20"]
+    n = 4096
+    dc = torch.empty(len(cases) * n * n, dtype=torch.int32, device="cuda")
+    for i, c in enumerate(cases):
+        m = synth.uniform_costs_torch(n, 0, (1 << 20) - 1, c["seed"], device="cuda")
+        assert hashlib.sha256(m.cpu().numpy().tobytes()).hexdigest() == c["sha256"]
+        dc[i * n * n:(i + 1) * n * n] = m.view(-1)
+    off = torch.arange(len(cases), dtype=torch.int64, device="cuda") * (n * n)
+    ns = torch.full((len(cases),), n, dtype=torch.int32, device="cuda")
+    sol = la.solve_batched(dc, off, ns, options=la.batch_options(block_threads=512, slots=1, max_n=n,
+                                                                  alpha=[48] * 16))
+    assert sol.stats["rc"] == 0
+    assert sol.costs.cpu().tolist() == [c["cost"] for c in cases]
+    match = sol.match.cpu().numpy()
+    C0 = synth.instance("uniform-n4096-c2^20", cases[0]["seed"])
+    assert oracle.check_matching(C0, match[:n], cases[0]["cost"]) == 0
+
+
 def test_invalid_sizes_flagged_per_instance(la):
     inst = [synth.uniform_costs(20, 0, 9, 1), synth.uniform_costs(40, 0, 9, 2)]
     flat, off, ns = pack(inst)

@@ -6,6 +6,7 @@ import json
 import os
 
 import numpy as np
+import pytest
 
 from paper_1110_6231_gb300 import synth
 
@@ -65,3 +66,14 @@ def test_batch_packing():
         ref = synth.uniform_costs(n, 0, 10000, i) if i % 2 == 0 else synth.geometric_costs(n, i)
         assert np.array_equal(blk, ref)
     assert off[-1] + int(ns[-1]) ** 2 == flat.size
+
+
+def test_torch_twin_of_the_uniform_generator_is_bit_identical():
+    """uniform_costs_torch (int64 torch arithmetic) draws the same int32
+    matrices as the numpy generator, over full int32 ranges too."""
+    torch = pytest.importorskip("torch")
+    for n, lo, hi, seed in ((0, 0, 5, 1), (1, 0, 5, 1), (7, -50, 1000, 3), (64, 0, (1 << 20) - 1, 0),
+                            (129, 0, 10**4, 9), (33, -(1 << 31), (1 << 31) - 1, 5)):
+        a = synth.uniform_costs(n, lo, hi, seed)
+        b = synth.uniform_costs_torch(n, lo, hi, seed, device="cpu").numpy()
+        assert a.dtype == b.dtype and np.array_equal(a, b), (n, lo, hi, seed)
