@@ -233,13 +233,18 @@ typedef struct {
        8 max_n bytes each, would exceed 192 KB of shared memory). The CTA's
        warps take free rows from any resident instance. */
     int32_t slots;
+    /* Candidate lists (the exact lazy scans of la_solve) for the rows of
+       every instance: > 0 on, < 0 off, 0 on when max_n >= 2048 and lists for
+       B * max_n rows (1032 bytes each) fit in 4 GB. They cut the bytes of
+       most row scans of large instances from 4 n to 1032. */
+    int32_t lists;
 } la_batch_options;
 
 typedef struct {
     int64_t instances;
     int64_t failed;
     int64_t scans;          /* row scans over all instances */
-    int64_t scan_bytes;     /* cost bytes those scans read (4 n_i per scan) */
+    int64_t scan_bytes;     /* bytes those scans read: 4 n_i per full scan, 1032 per list scan */
     int64_t wins;
     int64_t displaced;
     int64_t phases;         /* refine phases over all instances */
@@ -249,6 +254,8 @@ typedef struct {
     int32_t graph;          /* 1 if the launch was a CUDA graph replay */
     double device_ms;       /* launch time (profile != 0) */
     int32_t slots;          /* instances resident per CTA */
+    int32_t lists;          /* candidate lists used */
+    int64_t full_scans;     /* scans that read the whole row (all of them without lists) */
 } la_batch_stats;
 
 la_status la_solve_batched(const int32_t *cost, const int64_t *offsets, const int32_t *ns,

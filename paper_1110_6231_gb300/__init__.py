@@ -111,6 +111,7 @@ class la_batch_options(ctypes.Structure):
         ("profile", ctypes.c_int32),
         ("prices_out", ctypes.c_void_p),
         ("slots", ctypes.c_int32),
+        ("lists", ctypes.c_int32),
     ]
 
 
@@ -129,6 +130,8 @@ class la_batch_stats(ctypes.Structure):
         ("graph", ctypes.c_int32),
         ("device_ms", ctypes.c_double),
         ("slots", ctypes.c_int32),
+        ("lists", ctypes.c_int32),
+        ("full_scans", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -495,9 +498,10 @@ class BatchSolution:
 
 def batch_options(block_threads: int = 0, max_n: int = 0, alpha=None, budget_factor: int = 0,
                   no_graph: bool = False, profile: bool = False, prices_out=None,
-                  slots: int = 0) -> la_batch_options:
+                  slots: int = 0, lists: int = 0) -> la_batch_options:
     """Build la_batch_options; ``alpha`` is an int or a per-bucket list
-    (bucket k holds 2^k <= n < 2^(k+1))."""
+    (bucket k holds 2^k <= n < 2^(k+1)); ``lists`` > 0 turns candidate lists
+    on, < 0 off, 0 leaves the choice to the library (on for large n)."""
     o = la_batch_options()
     o.block_threads = block_threads
     o.max_n = max_n
@@ -510,6 +514,7 @@ def batch_options(block_threads: int = 0, max_n: int = 0, alpha=None, budget_fac
     o.profile = int(bool(profile))
     o.prices_out = _ptr(prices_out)
     o.slots = slots
+    o.lists = lists
     return o
 
 

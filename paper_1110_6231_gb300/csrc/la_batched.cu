@@ -27,6 +27,7 @@
 
 #include "la.h"
 #include "la_device.cuh"
+#include "la_lists.cuh"
 
 using namespace la;
 
@@ -36,10 +37,13 @@ constexpr int kPrepThreads = 1024;
 constexpr int kDefaultSlots = 4;                 // instances resident per CTA
 constexpr size_t kSlotSmemBudget = 192 * 1024;   // shared memory for their column keys
 constexpr int kMaxDevices = 64;
+constexpr int kAutoListsN = 2048;                       // default: lists when max_n is at least this
+constexpr size_t kAutoListsBytes = 4ull << 30;          // ... and they fit in this
 
 struct BatchCtrl {
-    unsigned long long scan_bytes;   // 4 n bytes of cost per row scan
+    unsigned long long scan_bytes;   // 4 n bytes per full row scan, kListLen * 8 + 8 per list scan
     unsigned long long scans;
+    unsigned long long full_scans;
     unsigned long long wins;
     unsigned long long displaced;
     unsigned long long phases;
@@ -192,6 +196,8 @@ k_batch_minmax(const int32_t *__restrict__ C, const long long *__restrict__ offs
 struct Slot {
     unsigned long long claim;
     unsigned long long eps, qlim, budget, scans;
+    unsigned long long full;     // full row scans (all of them without lists)
+    unsigned long long rebase;   // sum of the per-phase price shifts (candidate-list bounds)
     long long off;       // element offset of the instance's matrix
     long long moff;      // offset of its rows in match_out / prices_out
     int inst;            // instance index, -1 = empty
@@ -215,6 +221,7 @@ struct BatchArgs {
     int *inst_status;
     BatchCtrl *ctrl;
     long long *prices_out;
+    RowLists lists;   // candidate lists, row g = moff[i] + x of instance i (cols == nullptr: off)
 };
 
 __device__ __forceinline__ void finish_trivial(const BatchArgs &a, int i, int st, long long cost, int ctrl_failed) {
@@ -277,6 +284,10 @@ __device__ void load_next(const BatchArgs &a, Slot &sl, unsigned long long *keys
         const unsigned long long eps1 = max(1ull, Ct / (unsigned long long)alpha);
         const bool wide = 4 * Ct + 2 * eps1 + 16 >= (1ull << 32);
         for (int y = lane; y < n; y += 32) keys[y] = ~0ull;   // q = 0, no mate
+        if (a.lists.cols) {   // no row of this instance has a list yet
+            const long long mo = a.moff[i];
+            for (int y = lane; y < n; y += 32) a.lists.theta[mo + y] = 0ull;
+        }
         if (lane == 0) {
             v.inst = i;
             v.n = n;
@@ -292,6 +303,8 @@ __device__ void load_next(const BatchArgs &a, Slot &sl, unsigned long long *keys
             v.vec = ((a.offsets[i] & 3) == 0) && (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15) == 0);
             v.budget = (unsigned long long)a.P.budget_factor * n * nph + 4096;
             v.scans = 0;
+            v.full = 0;
+            v.rebase = 0;
             v.status = 0;
             v.unmatched = n;
         }
@@ -308,10 +321,16 @@ __device__ void load_next(const BatchArgs &a, Slot &sl, unsigned long long *keys
 // displaced, until a bid lands on a column nobody held. Returns true when
 // that made the slot's last row matched: the phase is over and the caller
 // runs the next one.
-template <bool WIDE>
+//
+// With LISTS, a row is scanned through its candidate list when the list
+// decides its bid, else in full (rebuilding the list), exactly as in the
+// single solve; every warp of the instance runs on this CTA's SM, so the
+// lists may be read through L1.
+template <bool WIDE, bool LISTS>
 __device__ bool run_chain(Slot &sl, unsigned long long *keys, const int32_t *__restrict__ Ci, int row, int n,
                           int cmin, unsigned long long eps, unsigned long long qlim, unsigned long long budget,
-                          bool vec, int lane, unsigned long long &wins, unsigned long long &displaced) {
+                          bool vec, int lane, unsigned long long &wins, unsigned long long &displaced,
+                          const RowLists &Li, unsigned long long R) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
     const volatile unsigned long long *vkey = keys;
     const uint32_t np1 = (uint32_t)n + 1;
@@ -327,7 +346,15 @@ __device__ bool run_chain(Slot &sl, unsigned long long *keys, const int32_t *__r
         bool give_up = st != 0 || s >= budget;
         if (give_up && st == 0 && lane == 0) atomicCAS(&sl.status, 0, (int)LA_ERR_ITER_LIMIT);
         ScanResult<V> r{0, 0, 0, 0};
-        if (!give_up) {
+        if (!give_up && LISTS) {
+            bool full = false;
+            const SharedKeyPrices<WIDE> prices{keys};
+            const ListAhead none{-1, 0ull, {}};
+            r = vec ? scan_for_bid<WIDE, true, true, 1>(Ci, row, n, cmin, np1, prices, lane, Li, R, full, none)
+                    : scan_for_bid<WIDE, false, true, 1>(Ci, row, n, cmin, np1, prices, lane, Li, R, full, none);
+            if (full && lane == 0) atomicAdd(&sl.full, 1ull);
+        } else if (!give_up) {
+            if (lane == 0) atomicAdd(&sl.full, 1ull);
             const int32_t *crow = Ci + (size_t)row * n;
             prefetch_row_l2(crow, n, lane);
             Lane2<V> t;
@@ -410,6 +437,7 @@ __device__ void end_phase(const BatchArgs &a, Slot &sl, unsigned long long *keys
         m = warp_min(m);
         for (int y = lane; y < n; y += 32) keys[y] = pack_key(key_q(keys[y]) - m, kNone);
         if (lane == 0) {
+            v.rebase = v.rebase + m;
             v.eps = max(1ull, v.eps / (unsigned long long)v.alpha);
             v.phase = v.phase + 1;
             v.unmatched = n;
@@ -441,11 +469,13 @@ __device__ void end_phase(const BatchArgs &a, Slot &sl, unsigned long long *keys
         for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     }
     if (lane == 0) {
-        const unsigned long long sc = v.scans;
+        const unsigned long long sc = v.scans, fu = v.full;
         if (a.cost_out) a.cost_out[i] = fst == 0 ? sum : 0;
         if (a.inst_status) a.inst_status[i] = fst;
         atomicAdd(&a.ctrl->scans, sc);
-        atomicAdd(&a.ctrl->scan_bytes, sc * 4ull * (unsigned long long)n);
+        atomicAdd(&a.ctrl->full_scans, fu);
+        atomicAdd(&a.ctrl->scan_bytes, fu * 4ull * (unsigned long long)n +
+                                           (sc > fu ? sc - fu : 0ull) * (unsigned long long)(8 * kListLen + 8));
         if (fst) {
             atomicAdd(&a.ctrl->failed, 1);
             atomicCAS(&a.ctrl->status, 0, fst);
@@ -460,8 +490,11 @@ __device__ void end_phase(const BatchArgs &a, Slot &sl, unsigned long long *keys
 // every warp takes free rows from any slot. A phase of an instance ends when
 // its last row is matched, with no CTA barrier, so warps never wait for
 // another instance's displacement chains.
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
+// Without lists the kernel keeps 64 registers (72 below 256 threads) for two
+// or more CTAs per SM; with lists, the list scan's insertion network gets
+// the registers of one CTA per SM.
+template <int BLOCK, bool LISTS>
+__global__ void __launch_bounds__(BLOCK, LISTS ? 1 : (BLOCK >= 256 ? 1024 / BLOCK : 7 * 128 / BLOCK))
 k_batch_solve(BatchArgs a, int S) {
     extern __shared__ unsigned long long skey[];
     __shared__ Slot s_slot[kMaxSlots];
@@ -522,11 +555,17 @@ k_batch_solve(BatchArgs a, int S) {
         volatile Slot &v = t;
         unsigned long long *keys = skey + (size_t)sl * a.max_n;
         const int n = v.n;
+        RowLists Li{nullptr, nullptr, nullptr};
+        if (LISTS) {
+            const long long mo = v.moff;
+            Li = RowLists{a.lists.cols + mo * kListLen, a.lists.costs + mo * kListLen, a.lists.theta + mo};
+        }
+        const unsigned long long R = v.rebase;
         const bool done = v.wide
-            ? run_chain<true>(t, keys, a.C + v.off, row, n, v.cmin, v.eps, v.qlim, v.budget, v.vec != 0, lane,
-                              wins, displaced)
-            : run_chain<false>(t, keys, a.C + v.off, row, n, v.cmin, v.eps, v.qlim, v.budget, v.vec != 0, lane,
-                               wins, displaced);
+            ? run_chain<true, LISTS>(t, keys, a.C + v.off, row, n, v.cmin, v.eps, v.qlim, v.budget, v.vec != 0,
+                                     lane, wins, displaced, Li, R)
+            : run_chain<false, LISTS>(t, keys, a.C + v.off, row, n, v.cmin, v.eps, v.qlim, v.budget, v.vec != 0,
+                                      lane, wins, displaced, Li, R);
         if (done) end_phase(a, t, keys, lane, phases_run);
         s0 = sl;
     }
@@ -541,7 +580,7 @@ k_batch_solve(BatchArgs a, int S) {
 
 struct GraphKey {
     const void *cost, *offsets, *ns, *match, *costout, *status, *prices;
-    int B, block, max_n, slots;
+    int B, block, max_n, slots, lists;
     cudaStream_t stream;
     BatchParams P;
     bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
@@ -558,6 +597,8 @@ struct BatchWorkspace {
     BatchCtrl *ctrl = nullptr;
     BatchCtrl *h_ctrl = nullptr;
     int num_sms = 0;
+    size_t list_rows = 0;   // rows the candidate lists have room for
+    RowLists lists{nullptr, nullptr, nullptr};
     cudaGraphExec_t exec = nullptr;
     GraphKey key;
     bool have_key = false;
@@ -570,6 +611,28 @@ void drop_graph(BatchWorkspace &w) {
     if (w.exec) cudaGraphExecDestroy(w.exec);
     w.exec = nullptr;
     w.have_key = false;
+}
+
+// Candidate lists for `rows` rows (B * max_n bounds the rows of a batch).
+la_status ensure_lists(BatchWorkspace &w, size_t rows) {
+    if (w.list_rows >= rows) return LA_OK;
+    drop_graph(w);
+    cudaFree(w.lists.cols);
+    cudaFree(w.lists.costs);
+    cudaFree(w.lists.theta);
+    w.lists = RowLists{nullptr, nullptr, nullptr};
+    w.list_rows = 0;
+    if (cudaMalloc(&w.lists.cols, sizeof(int) * kListLen * rows) != cudaSuccess ||
+        cudaMalloc(&w.lists.costs, sizeof(int) * kListLen * rows) != cudaSuccess ||
+        cudaMalloc(&w.lists.theta, sizeof(unsigned long long) * rows) != cudaSuccess) {
+        cudaFree(w.lists.cols);
+        cudaFree(w.lists.costs);
+        cudaFree(w.lists.theta);
+        w.lists = RowLists{nullptr, nullptr, nullptr};
+        return LA_ERR_NOMEM;
+    }
+    w.list_rows = rows;
+    return LA_OK;
 }
 
 la_status ensure_bws(BatchWorkspace &w, int64_t B, int max_n) {
@@ -608,14 +671,36 @@ la_status ensure_bws(BatchWorkspace &w, int64_t B, int max_n) {
 
 // Persistent grid size on the current device (the shared-memory attribute is
 // per device, so it is set on every call; both are host calls, no GPU work).
-template <int BLOCK>
+template <int BLOCK, bool LISTS>
 int solve_grid(int num_sms, size_t smem) {
     // Always set: the kernel's static shared memory (the slot records) and
     // `smem` together must fit, and 48 KB is the limit without it.
-    cudaFuncSetAttribute(k_batch_solve<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_batch_solve<BLOCK, LISTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch_solve<BLOCK>, BLOCK, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch_solve<BLOCK, LISTS>, BLOCK, smem);
     return num_sms * std::max(1, o);
+}
+
+template <bool LISTS>
+int solve_grid_for(int block, int num_sms, size_t smem) {
+    switch (block) {
+    case 64: return solve_grid<64, LISTS>(num_sms, smem);
+    case 128: return solve_grid<128, LISTS>(num_sms, smem);
+    case 256: return solve_grid<256, LISTS>(num_sms, smem);
+    case 512: return solve_grid<512, LISTS>(num_sms, smem);
+    default: return solve_grid<1024, LISTS>(num_sms, smem);
+    }
+}
+
+template <bool LISTS>
+void launch_solve(cudaStream_t s, int block, int grid, size_t smem, int slots, const BatchArgs &args) {
+    switch (block) {
+    case 64: k_batch_solve<64, LISTS><<<grid, 64, smem, s>>>(args, slots); break;
+    case 128: k_batch_solve<128, LISTS><<<grid, 128, smem, s>>>(args, slots); break;
+    case 256: k_batch_solve<256, LISTS><<<grid, 256, smem, s>>>(args, slots); break;
+    case 512: k_batch_solve<512, LISTS><<<grid, 512, smem, s>>>(args, slots); break;
+    default: k_batch_solve<1024, LISTS><<<grid, 1024, smem, s>>>(args, slots); break;
+    }
 }
 
 cudaError_t enqueue(cudaStream_t s, int block, int grid, size_t smem, int slots, const BatchArgs &args,
@@ -629,13 +714,8 @@ cudaError_t enqueue(cudaStream_t s, int block, int grid, size_t smem, int slots,
     k_batch_minmax<<<mm_grid, 256, 0, s>>>(args.C, args.offsets, args.ns, args.B, args.max_n,
                                            const_cast<int2 *>(args.cminmax));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    switch (block) {
-    case 64: k_batch_solve<64><<<grid, 64, smem, s>>>(args, slots); break;
-    case 128: k_batch_solve<128><<<grid, 128, smem, s>>>(args, slots); break;
-    case 256: k_batch_solve<256><<<grid, 256, smem, s>>>(args, slots); break;
-    case 512: k_batch_solve<512><<<grid, 512, smem, s>>>(args, slots); break;
-    default: k_batch_solve<1024><<<grid, 1024, smem, s>>>(args, slots); break;
-    }
+    if (args.lists.cols) launch_solve<true>(s, block, grid, smem, slots, args);
+    else launch_solve<false>(s, block, grid, smem, slots, args);
     return cudaGetLastError();
 }
 
@@ -676,14 +756,19 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
     slots = std::min(slots, kMaxSlots);
     slots = std::max(1, std::min(slots, (int)(kSlotSmemBudget / (sizeof(unsigned long long) * (size_t)max_n))));
     const size_t smem = sizeof(unsigned long long) * (size_t)max_n * slots;
-    int grid = 0;
-    switch (block) {
-    case 64: grid = solve_grid<64>(w.num_sms, smem); break;
-    case 128: grid = solve_grid<128>(w.num_sms, smem); break;
-    case 256: grid = solve_grid<256>(w.num_sms, smem); break;
-    case 512: grid = solve_grid<512>(w.num_sms, smem); break;
-    default: grid = solve_grid<1024>(w.num_sms, smem); break;
-    }
+    // Candidate lists: asked for (lists > 0), or by default when instances may
+    // be large (max_n >= kAutoListsN) and lists for B * max_n rows fit in
+    // kAutoListsBytes.
+    const int lists_opt = opt ? opt->lists : 0;
+    const size_t list_row_bytes = sizeof(int) * 2 * kListLen + sizeof(unsigned long long);
+    const size_t rows = (size_t)B * (size_t)max_n;
+    const bool use_lists = lists_opt > 0 ||
+                           (lists_opt == 0 && max_n >= kAutoListsN && rows * list_row_bytes <= kAutoListsBytes);
+    if (use_lists)
+        if (la_status e = ensure_lists(w, rows)) return e;
+    const int grid_all = use_lists ? solve_grid_for<true>(block, w.num_sms, smem)
+                                   : solve_grid_for<false>(block, w.num_sms, smem);
+    int grid = grid_all;
     grid = std::max(1, std::min(grid, (int)((B + slots - 1) / slots)));
     BatchArgs args;
     args.C = cost;
@@ -700,6 +785,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
     args.inst_status = status;
     args.ctrl = w.ctrl;
     args.prices_out = reinterpret_cast<long long *>(prices);
+    args.lists = use_lists ? w.lists : RowLists{nullptr, nullptr, nullptr};
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool profile = opt && opt->profile;
@@ -723,6 +809,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
         key.block = block;
         key.max_n = max_n;
         key.slots = slots;
+        key.lists = use_lists ? 1 : 0;
         key.stream = s;
         key.P = P;
         if (!(w.have_key && w.key == key && w.exec)) {
@@ -760,6 +847,8 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
         st->failed = c.failed;
         st->scans = (int64_t)c.scans;
         st->scan_bytes = (int64_t)c.scan_bytes;
+        st->full_scans = (int64_t)c.full_scans;
+        st->lists = use_lists ? 1 : 0;
         st->wins = (int64_t)c.wins;
         st->displaced = (int64_t)c.displaced;
         st->phases = (int64_t)c.phases;

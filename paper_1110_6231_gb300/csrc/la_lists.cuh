@@ -113,10 +113,12 @@ struct SharedKeyPrices {
 // Full scan of row x: v(x,y) = (C[x][y] - cmin)(n+1) + q(y) for every y.
 // Writes x's candidate list when lists are on.
 //
-// The insertion network is one long dependent chain per lane. A warp that
-// scans alone on its SM (the end of a phase) has no other warps to overlap
-// it with, so NCH independent chains take interleaved columns of each int4
-// group (chain c the components c, c + NCH, ...) and are merged at the end.
+// NCH independent insertion chains per lane take interleaved columns of each
+// int4 group (chain c the components c, c + NCH, ...) and are merged at the
+// end in (value, column) order, which gives the same lists as one chain. In
+// the one-CTA tail kernel, where a warp often scans alone on its SM, four
+// chains (two on 32-bit values) measured faster; the grid refine and the
+// batched kernel use one, which needs fewer registers.
 template <bool WIDE, bool VEC, int NCH, class P>
 __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int row, int n, int cmin,
                                           uint32_t np1, const P &prices, int lane,
@@ -227,7 +229,7 @@ __device__ __forceinline__ auto list_scan(int row, int n, int cmin, uint32_t np1
 // Best and second best of row x for its next bid: from the candidate list
 // when it decides the row (see RowLists), else from a full scan that also
 // rebuilds the list. The second best may be the lower bound theta.
-template <bool WIDE, bool VEC, bool ONE_SM, class P>
+template <bool WIDE, bool VEC, bool ONE_SM, int NCH, class P>
 __device__ __forceinline__ auto scan_for_bid(const int32_t *__restrict__ C, int row, int n, int cmin,
                                              uint32_t np1, const P &prices, int lane,
                                              const RowLists &L, unsigned long long R, bool &full,
@@ -249,7 +251,7 @@ __device__ __forceinline__ auto scan_for_bid(const int32_t *__restrict__ C, int 
         }
     }
     full = !ok;
-    if (!ok) t = full_scan<WIDE, VEC, ONE_SM ? (WIDE ? 4 : 2) : 1>(C + (size_t)row * n, row, n, cmin, np1, prices, lane, L, R);
+    if (!ok) t = full_scan<WIDE, VEC, NCH>(C + (size_t)row * n, row, n, cmin, np1, prices, lane, L, R);
     return t;
 }
 

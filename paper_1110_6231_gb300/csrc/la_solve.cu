@@ -236,7 +236,7 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
         ++pending;
         ++total;
         bool was_full = false;
-        const auto t = scan_for_bid<WIDE, VEC, false>(C, row, n, cmin, np1, MirrorPrices<WIDE>{qmv}, lane, L, R, was_full,
+        const auto t = scan_for_bid<WIDE, VEC, false, 1>(C, row, n, cmin, np1, MirrorPrices<WIDE>{qmv}, lane, L, R, was_full,
                                                            ListAhead{-1, 0ull, {}});
         if (was_full) ++full;
         else ++hits;
@@ -381,7 +381,8 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
         ++pending;
         ++total;
         bool was_full = false;
-        const auto t = scan_for_bid<WIDE, VEC, true>(C, row, n, cmin, np1, prices, lane, L, R, was_full, ahead);
+        const auto t = scan_for_bid<WIDE, VEC, true, (WIDE ? 4 : 2)>(C, row, n, cmin, np1, prices, lane, L, R, was_full,
+                                                                    ahead);
         if (was_full) ++full;
         else ++hits;
         if (lane == 0) {   // the share of full scans can only pass 1/4 when a full scan is counted

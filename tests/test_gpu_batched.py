@@ -54,7 +54,8 @@ def verify(flat, offsets, ns, sol, expected=None):
         mo += n
 
 
-def test_mixed_small_batch(la):
+@pytest.mark.parametrize("lists", [-1, 1])
+def test_mixed_small_batch(la, lists):
     rng = np.random.default_rng(3)
     inst = []
     for i, n in enumerate([0, 1, 2, 3, 5, 17, 31, 32, 33, 64, 100, 129, 255, 256, 300, 513]):
@@ -65,8 +66,12 @@ def test_mixed_small_batch(la):
         else:
             inst.append(rng.integers(0, 3, size=(n, n)).astype(np.int32))   # heavy ties
     flat, off, ns = pack(inst)
-    sol = run(la, flat, off, ns)
-    assert sol.stats["rc"] == 0
+    sol = run(la, flat, off, ns, lists=lists)
+    assert sol.stats["rc"] == 0 and sol.stats["lists"] == (lists > 0)
+    if lists > 0:
+        assert 0 < sol.stats["full_scans"] < sol.stats["scans"]
+    else:
+        assert sol.stats["full_scans"] == sol.stats["scans"]
     verify(flat, off, ns, sol)
 
 
@@ -184,13 +189,14 @@ def test_concurrent_n4096_instances_one_per_cta(la):
         dc[i * n * n:(i + 1) * n * n] = m.view(-1)
     off = torch.arange(len(cases), dtype=torch.int64, device="cuda") * (n * n)
     ns = torch.full((len(cases),), n, dtype=torch.int32, device="cuda")
-    sol = la.solve_batched(dc, off, ns, options=la.batch_options(block_threads=512, slots=1, max_n=n,
-                                                                  alpha=[48] * 16))
-    assert sol.stats["rc"] == 0
-    assert sol.costs.cpu().tolist() == [c["cost"] for c in cases]
-    match = sol.match.cpu().numpy()
-    C0 = synth.instance("uniform-n4096-c2^20", cases[0]["seed"])
-    assert oracle.check_matching(C0, match[:n], cases[0]["cost"]) == 0
+    for lists in (0, -1):   # 0: the library's choice for n = 4096 is lists on
+        sol = la.solve_batched(dc, off, ns, options=la.batch_options(block_threads=256, slots=1, max_n=n,
+                                                                      alpha=[48] * 16, lists=lists))
+        assert sol.stats["rc"] == 0 and sol.stats["lists"] == (lists == 0)
+        assert sol.costs.cpu().tolist() == [c["cost"] for c in cases]
+        match = sol.match.cpu().numpy()
+        C0 = synth.instance("uniform-n4096-c2^20", cases[0]["seed"])
+        assert oracle.check_matching(C0, match[:n], cases[0]["cost"]) == 0
 
 
 def test_invalid_sizes_flagged_per_instance(la):
