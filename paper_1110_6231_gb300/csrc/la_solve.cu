@@ -298,7 +298,7 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
 // kernel's hand-off), every step of their displacement chains is latency
 // bound; here the column keys live in shared memory, so a step's price reads
 // and its commit (the same packed atomicMin) stay on the SM. The rows handed
-// over, and any still in the queue, are finished by the CTA's 32 warps, then
+// over, and any still in the queue, are finished by the CTA's warps, then
 // the keys go back to global memory.
 //
 // One SM is the right place for chains of list scans, not for full scans:
