@@ -583,6 +583,9 @@ def run_gpu(args):
                            "hbm_read_GBps": hbm_read_gbps, "hbm_buffer": "4 GiB, 2 passes per launch",
                            "kernel": "la_probe_read (128-bit ld.global.cg, 4 CTAs x 512 threads per SM)"},
             "arc_scans_per_solve": scans / max(1, len(stats)),
+            # every phase starts with all n rows free, so n scans per phase is
+            # the least a solve can make; this is that bound over the scans made
+            "scan_efficiency": (sum(s["phases"] for s in stats) * n) / max(1, scans),
             "full_row_scans_per_solve": full / max(1, len(stats)),
             "list_scans_per_solve": listed / max(1, len(stats)),
             "phases": stats[0]["phases"] if stats else None,
