@@ -115,6 +115,15 @@ typedef struct {
 /* la_options.flags: scan every row in full on every bid instead of using
    the exact candidate lists (for measurement and testing). */
 #define LA_FLAG_NO_CANDIDATE_LISTS 1
+/* la_options.flags, a debug mode: at the end of every phase a device pass
+   over C checks the invariants of the refine (Sect. 5.1-5.2): every column
+   has a holder and no row holds two (a perfect assignment; with a phase
+   cutoff, only at the last phase), every holder x of a column y is
+   eps-optimal for the phase's eps (version-2 eps-CS on costs scaled by n+1:
+   c~(x,y) - p(y) <= min_z (c~(x,z) - p(z)) + eps), and no column's price
+   rose during the phase (Lemma 5.2). Violations are counted in
+   la_stats.check_violations and make the solve return LA_ERR_INTERNAL. */
+#define LA_FLAG_CHECK_PHASES 2
 
 /* Phases whose counters la_stats records one by one. */
 #define LA_STATS_PHASES 32
@@ -155,6 +164,8 @@ typedef struct {
     int64_t tail_full_scans; /* of tail_scans, those that read the whole row */
     int32_t tail_giveups;    /* phases whose tail kernel handed its rows back to
                                 the grid (its lists stopped answering) */
+    int32_t checked_phases;  /* LA_FLAG_CHECK_PHASES: phases checked */
+    int64_t check_violations; /* LA_FLAG_CHECK_PHASES: failed checks (0 = all held) */
 } la_stats;
 
 /*

@@ -33,6 +33,7 @@ LA_ERR_INFEASIBLE = 8
 LA_MAX_N = (1 << 20) - 1
 LA_NOALLOC_MAX_N = 16384
 LA_FLAG_NO_CANDIDATE_LISTS = 1
+LA_FLAG_CHECK_PHASES = 2
 
 
 class la_options(ctypes.Structure):
@@ -79,6 +80,8 @@ class la_stats(ctypes.Structure):
         ("tail_ms", ctypes.c_double),
         ("tail_full_scans", ctypes.c_int64),
         ("tail_giveups", ctypes.c_int32),
+        ("checked_phases", ctypes.c_int32),
+        ("check_violations", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -74,6 +74,8 @@ struct Ctrl {
     int colseen_missing;             // sparse graphs: columns without an arc
     unsigned long long tail_full;    // full row scans made by the tail kernel
     int tail_giveups;                // phases whose tail kernel gave its rows back
+    unsigned long long check_violations;   // debug mode: failed phase-end checks
+    int checked_phases;                    // debug mode: phases checked
 };
 
 // Global nanosecond timer (bounds every wait in the kernels).

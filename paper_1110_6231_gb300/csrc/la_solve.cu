@@ -712,6 +712,46 @@ __global__ void k_finalize(const int32_t *__restrict__ C, int n, const unsigned 
         atomicAdd(reinterpret_cast<unsigned long long *>(cost), (unsigned long long)sum);
 }
 
+// Debug mode (LA_FLAG_CHECK_PHASES). The prices q(y) at the start of a phase,
+// after its rebase.
+__global__ void k_check_snapshot(const unsigned long long *__restrict__ key, int n, unsigned long long *q0) {
+    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) q0[y] = key_q(key[y]);
+}
+
+// Debug mode, at the end of a phase: one warp per column y checks that y
+// has a holder x (if `perfect`), that x holds no other column, that x is
+// eps-optimal, (n+1)(C[x][y] - cmin) + q(y) <= min_z ((n+1)(C[x][z] - cmin)
+// + q(z)) + eps (version-2 eps-CS, Sect. 5.1), and that q(y) did not fall
+// during the phase (prices only decrease, Lemma 5.2). Plain 64-bit
+// arithmetic, independent of the refine's narrow and list paths.
+__global__ void k_check_phase(const int32_t *__restrict__ C, int n, int cmin, unsigned long long np1,
+                              const unsigned long long *__restrict__ key, const unsigned long long *__restrict__ q0,
+                              unsigned long long eps, int perfect, int *__restrict__ seen, Ctrl *ctrl) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int y = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); y < n; y += warps) {
+        const unsigned long long k = key[y];
+        const uint32_t x = key_mate(k);
+        unsigned long long bad = key_q(k) < q0[y] ? 1 : 0;
+        if (x >= (uint32_t)n) {
+            bad += (x != kNone || perfect) ? 1 : 0;
+        } else {
+            if (lane == 0 && atomicAdd(&seen[x], 1) != 0) ++bad;
+            const int32_t *row = C + (size_t)x * n;
+            unsigned long long mn = ~0ull;
+            for (int z = lane; z < n; z += 32) {
+                const unsigned long long v = (unsigned long long)(uint32_t)(row[z] - cmin) * np1 + key_q(key[z]);
+                mn = v < mn ? v : mn;
+            }
+            mn = warp_min(mn);
+            const unsigned long long mine = (unsigned long long)(uint32_t)(row[y] - cmin) * np1 + key_q(k);
+            if (mine > mn + eps) ++bad;
+        }
+        if (lane == 0 && bad) atomicAdd(&ctrl->check_violations, bad);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctrl->checked_phases, 1);
+}
+
 // ---------------------------------------------------------------- host side
 
 struct Workspace {
@@ -1012,6 +1052,23 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     else grid = vec ? refine_grid<false, true>(ws.num_sms, block, n) : refine_grid<false, false>(ws.num_sms, block, n);
 
     const int cmin = c0.cmin;
+    // debug mode: scratch for the phase-end checks (allocated per call)
+    const bool check = opt && (opt->flags & LA_FLAG_CHECK_PHASES);
+    unsigned long long *chk_q0 = nullptr;
+    int *chk_seen = nullptr;
+    struct ChkFree {
+        unsigned long long *&q0;
+        int *&seen;
+        ~ChkFree() {
+            cudaFree(q0);
+            cudaFree(seen);
+        }
+    } chk_free{chk_q0, chk_seen};
+    if (check) {
+        if (cudaMalloc(&chk_q0, sizeof(unsigned long long) * n) != cudaSuccess ||
+            cudaMalloc(&chk_seen, sizeof(int) * n) != cudaSuccess)
+            return LA_ERR_NOMEM;
+    }
     int ph = 0;
     for (; ph < (int)sched.size(); ++ph) {
         const int slot = ph & 1;
@@ -1019,6 +1076,10 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         if (wide) k_reset<true><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds);
         else k_reset<false><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds);
         launches += 2;
+        if (check) {
+            k_check_snapshot<<<sg, 256, 0, s>>>(ws.key, n, chk_q0);
+            ++launches;
+        }
         if (profile) LA_CK(cudaEventRecord(ws.ev[4 * ph], s));
         const int sf = ph + 1 < (int)sched.size() ? stop_free : 0;
         cudaEvent_t evt = profile ? ws.ev[4 * ph + 1] : nullptr;
@@ -1031,6 +1092,14 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
             else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt, evf)));
         }
         if (profile) LA_CK(cudaEventRecord(ws.ev[4 * ph + 3], s));
+        if (check) {
+            LA_CK(cudaMemsetAsync(chk_seen, 0, sizeof(int) * n, s));
+            const int cg = std::max(1, std::min((n + 7) / 8, 8 * ws.num_sms));   // 8 warps per block
+            k_check_phase<<<cg, 256, 0, s>>>(cost, n, cmin, np1, ws.key, chk_q0, sched[ph],
+                                             (sf == 0) ? 1 : 0, chk_seen, ws.ctrl);
+            ++launches;
+            LA_CK(cudaGetLastError());
+        }
     }
     const int fslot = ph & 1;
     if (prices_out) {
@@ -1067,6 +1136,8 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         stats.phase_scans[k] = (int64_t)(end - c1.phase_start_scans[k]);
     }
     stats.list_entries = lists ? kListLen : 0;
+    stats.checked_phases = c1.checked_phases;
+    stats.check_violations = (int64_t)c1.check_violations;
     if (profile) {
         double ms = 0, tail_ms = 0;
         for (int k = 0; k < ph; ++k) {
@@ -1081,6 +1152,7 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         stats.tail_ms = tail_ms;
     }
     if (st) *st = stats;
+    if (c1.status == 0 && check && (c1.check_violations != 0 || c1.checked_phases != ph)) return LA_ERR_INTERNAL;
     return (la_status)c1.status;
 }
 

@@ -367,3 +367,43 @@ def test_alpha_tuner_picks_a_candidate_and_every_alpha_is_exact(la):
     assert res["alpha"] in (4, 10, 32, 100) and set(res["mean_ms"]) == {4, 10, 32, 100}
     for a in (2, 3, 4, 10, 32, 100, 1000):
         assert la.solve(t, alpha=a).cost == ref
+
+
+@pytest.mark.parametrize("case", ["narrow", "wide", "geometric", "ties", "price_updates", "cutoff", "no_lists",
+                                  "warm_prices"])
+def test_phase_end_invariants_on_the_device(la, case):
+    """LA_FLAG_CHECK_PHASES: after every phase a device pass checks that the
+    assignment is perfect, that every holder is eps-optimal for the phase's
+    eps and that no price rose during the phase (Sect. 5.1-5.2). Every phase
+    of every configuration must pass, and the optimum must be the oracle's."""
+    import torch
+    kw = {}
+    if case == "narrow":
+        C = synth.uniform_costs(300, 0, 1000, 5)
+    elif case == "wide":
+        C = synth.instance("uniform-n4096-c2^20", 3)
+    elif case == "geometric":
+        C = synth.geometric_costs(2048, 6)
+    elif case == "ties":
+        C = np.random.default_rng(7).integers(0, 3, size=(513, 513)).astype(np.int32)
+    elif case == "price_updates":
+        C = synth.geometric_costs(1024, 8)
+        kw["price_updates"] = 2
+    elif case == "cutoff":
+        C = synth.uniform_costs(1024, 0, 10**5, 9)
+        kw["phase_cutoff"] = 4
+    elif case == "no_lists":
+        C = synth.uniform_costs(512, 0, 10**4, 10)
+        kw["flags"] = la.LA_FLAG_NO_CANDIDATE_LISTS
+    else:
+        C = synth.geometric_costs(1024, 11)
+        _, _, p, _ = oracle.cost_scaling(C)
+        kw["init_prices"] = torch.from_numpy(p - 12345).cuda()
+    kw["flags"] = kw.get("flags", 0) | la.LA_FLAG_CHECK_PHASES
+    t = torch.from_numpy(np.ascontiguousarray(C)).cuda()
+    sol = la.solve(t, want_prices=True, **kw)
+    st = sol.stats
+    assert st["check_violations"] == 0 and st["checked_phases"] == st["phases"] > 0
+    ref = oracle.hungarian(C)[0] if C.shape[0] <= 2048 else oracle.cost_scaling(C)[0]
+    assert sol.cost == ref
+    assert oracle.check_eps_cs(C, sol.match.cpu().numpy(), sol.prices.cpu().numpy(), 1) == 0
