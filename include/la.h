@@ -81,7 +81,8 @@ typedef struct {
     int64_t *prices_out;
     /* Maximum number of row scans over the whole solve; 0 selects
        256 * n * phases + 2^22. Exhausting it returns LA_ERR_ITER_LIMIT with
-       the outputs unspecified. */
+       the matching and cost unspecified; prices_out then holds the prices
+       reached, to resume from (see la_stats.stop_eps). */
     int64_t scan_budget;
     /* Nonzero: record CUDA events around every refine launch and report
        their summed duration in la_stats.refine_ms. */
@@ -166,6 +167,14 @@ typedef struct {
                                 the grid (its lists stopped answering) */
     int32_t checked_phases;  /* LA_FLAG_CHECK_PHASES: phases checked */
     int64_t check_violations; /* LA_FLAG_CHECK_PHASES: failed checks (0 = all held) */
+    /* After a non-OK status: the phase it stopped in and that phase's eps
+       (-1 and 0 after a success). A solve stopped by its scan budget can be
+       resumed: pass the prices it wrote to opt->prices_out (written whenever
+       the phases ran, LA_ERR_ITER_LIMIT included) as opt->init_prices, and
+       stop_eps * alpha as opt->eps0, so that the resumed solve starts at the
+       phase that did not finish; any start prices give the exact optimum. */
+    int32_t stop_phase;
+    int64_t stop_eps;
 } la_stats;
 
 /*

@@ -82,6 +82,8 @@ class la_stats(ctypes.Structure):
         ("tail_giveups", ctypes.c_int32),
         ("checked_phases", ctypes.c_int32),
         ("check_violations", ctypes.c_int64),
+        ("stop_phase", ctypes.c_int32),
+        ("stop_eps", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -76,6 +76,7 @@ struct Ctrl {
     int tail_giveups;                // phases whose tail kernel gave its rows back
     unsigned long long check_violations;   // debug mode: failed phase-end checks
     int checked_phases;                    // debug mode: phases checked
+    int phase_now;                         // the running phase, frozen when the status is set
 };
 
 // Global nanosecond timer (bounds every wait in the kernels).

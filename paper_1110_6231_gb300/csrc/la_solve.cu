@@ -153,6 +153,7 @@ __global__ void k_reset(unsigned long long *__restrict__ key, void *__restrict__
         ctrl->next_row = 0;
         ctrl->qmin[slot ^ 1] = ~0ull;
         ctrl->phase_start_scans[phase & 63] = ctrl->scans;
+        if (*reinterpret_cast<volatile int *>(&ctrl->status) == 0) ctrl->phase_now = phase;
         ctrl->rebase_total += qmin;
         ctrl->free_rows = n;
         ctrl->handoff = 0;
@@ -699,13 +700,14 @@ __global__ void k_finalize(const int32_t *__restrict__ C, int n, const unsigned 
     for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
         const unsigned long long k = key[y];
         const uint32_t m = key_mate(k);
+        // prices first: after a stop (the scan budget) they are the state to resume from
+        if (prices) prices[y] = -(long long)(key_q(k) - qmin);
         if (m >= (uint32_t)n) {
             set_status(ctrl, LA_ERR_INTERNAL);
             continue;
         }
         if (match) match[m] = y;
         sum += C[(size_t)m * n + y];
-        if (prices) prices[y] = -(long long)(key_q(k) - qmin);
     }
     for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if ((threadIdx.x & 31) == 0 && sum != 0)
@@ -1137,6 +1139,8 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     }
     stats.list_entries = lists ? kListLen : 0;
     stats.checked_phases = c1.checked_phases;
+    stats.stop_phase = c1.status ? c1.phase_now : -1;
+    stats.stop_eps = c1.status ? (int64_t)sched[std::min<int>(std::max(c1.phase_now, 0), (int)sched.size() - 1)] : 0;
     stats.check_violations = (int64_t)c1.check_violations;
     if (profile) {
         double ms = 0, tail_ms = 0;

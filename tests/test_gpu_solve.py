@@ -191,6 +191,27 @@ def test_scan_budget_returns_iter_limit_then_recovers(la):
     assert la.solve(t).cost == oracle.hungarian(C)[0]
 
 
+@pytest.mark.parametrize("kind", ["uniform", "geometric"])
+def test_resume_after_the_scan_budget(la, kind):
+    """A solve stopped by its scan budget reports the phase and eps it
+    stopped at and leaves its prices; a second call started from those
+    prices at that eps finishes with the exact optimum, running only the
+    remaining phases."""
+    import torch
+    C = synth.uniform_costs(1024, 0, 10**5, 21) if kind == "uniform" else synth.geometric_costs(1024, 22)
+    t = torch.from_numpy(C).cuda()
+    full = la.solve(t)
+    first = la.solve(t, scan_budget=3 * 1024, want_prices=True, alpha=10, check=False)
+    st = first.stats
+    assert st["status"] == la.LA_ERR_ITER_LIMIT
+    assert 0 <= st["stop_phase"] < full.stats["phases"] and st["stop_eps"] >= 1
+    resumed = la.solve(t, init_prices=first.prices, eps0=st["stop_eps"] * 10, alpha=10, want_prices=True)
+    assert resumed.cost == oracle.hungarian(C)[0]
+    assert oracle.check_eps_cs(C, resumed.match.cpu().numpy(), resumed.prices.cpu().numpy(), 1) == 0
+    assert resumed.stats["eps_first"] == st["stop_eps"]
+    assert resumed.stats["stop_phase"] == -1 and resumed.stats["stop_eps"] == 0
+
+
 def test_alpha_and_eps0_options(la):
     C = synth.geometric_costs(300, 5)
     ref = oracle.hungarian(C)[0]
