@@ -39,6 +39,8 @@ constexpr size_t kSlotSmemBudget = 192 * 1024;   // shared memory for their colu
 constexpr int kMaxDevices = 64;
 constexpr int kAutoListsN = 2048;                       // default: lists when max_n is at least this
 constexpr size_t kAutoListsBytes = 4ull << 30;          // ... and they fit in this
+constexpr bool kStageRows = true;                       // bulk-copy row staging in the list-free kernel
+constexpr size_t kStageSmemBudget = 200 * 1024;         // its shared memory (keys + row buffers) at most
 
 struct BatchCtrl {
     unsigned long long scan_bytes;   // 4 n bytes per full row scan, kListLen * 8 + 8 per list scan
@@ -188,6 +190,56 @@ k_batch_minmax(const int32_t *__restrict__ C, const long long *__restrict__ offs
     }
 }
 
+// Row staging by the bulk-copy engine (list-free kernel): a warp asks for
+// its whole cost row with one cp.async.bulk into its own shared-memory
+// buffer and waits on its own mbarrier, instead of having every lane load
+// its part of the row from L2 in several dependent rounds.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Lane 0: expect `bytes` on the barrier and start the copy (global src and
+// shared dst 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_row(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    unsigned long long g;
+    asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(g), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Every lane waits for the phase `parity` of the barrier to complete; false
+// after 1 s (the copy is then treated as lost).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    const unsigned long long t0 = global_timer_ns();
+    for (unsigned it = 0;; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 255) == 255 && global_timer_ns() - t0 > 1000000000ull) return false;
+    }
+}
+// Ints per warp buffer: a row of max_n ints starting at any 4-byte offset,
+// widened to 16-byte boundaries at both ends.
+__host__ __device__ __forceinline__ int stage_stride(int max_n) { return (max_n + 8 + 3) & ~3; }
+// The keys of S slots in u64 words, rounded up so that the row buffers start 16-byte aligned.
+__host__ __device__ __forceinline__ size_t stage_key_words(int S, int max_n) {
+    return ((size_t)S * (size_t)max_n + 1) & ~(size_t)1;
+}
+__host__ __device__ __forceinline__ size_t stage_smem(int S, int max_n, int warps) {
+    return stage_key_words(S, max_n) * 8 + (size_t)warps * stage_stride(max_n) * 4 + (size_t)warps * 8;
+}
+
 // One instance resident in a CTA. Rows are claimed with one atomicAdd on
 // `claim` = (n << 32) | next row: a claim is valid exactly when the returned
 // index is below the returned n, so no claim can land between two phases or
@@ -326,11 +378,12 @@ __device__ void load_next(const BatchArgs &a, Slot &sl, unsigned long long *keys
 // decides its bid, else in full (rebuilding the list), exactly as in the
 // single solve; every warp of the instance runs on this CTA's SM, so the
 // lists may be read through L1.
-template <bool WIDE, bool LISTS>
+template <bool WIDE, bool LISTS, bool STAGE>
 __device__ bool run_chain(Slot &sl, unsigned long long *keys, const int32_t *__restrict__ Ci, int row, int n,
                           int cmin, unsigned long long eps, unsigned long long qlim, unsigned long long budget,
                           bool vec, int lane, unsigned long long &wins, unsigned long long &displaced,
-                          const RowLists &Li, unsigned long long R) {
+                          const RowLists &Li, unsigned long long R, int *sbuf, unsigned long long *sbar,
+                          unsigned &spar, bool &sok) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
     const volatile unsigned long long *vkey = keys;
     const uint32_t np1 = (uint32_t)n + 1;
@@ -356,9 +409,56 @@ __device__ bool run_chain(Slot &sl, unsigned long long *keys, const int32_t *__r
         } else if (!give_up) {
             if (lane == 0) atomicAdd(&sl.full, 1ull);
             const int32_t *crow = Ci + (size_t)row * n;
-            prefetch_row_l2(crow, n, lane);
             Lane2<V> t;
             lane2_init(t);
+            bool staged = false;
+            int d = 0;
+            if (STAGE && sok) {
+                // the row widened to 16-byte boundaries, if that stays inside the instance
+                const uintptr_t a0 = reinterpret_cast<uintptr_t>(crow), a1 = a0 + 4ull * (unsigned)n;
+                const uintptr_t w0 = a0 & ~(uintptr_t)15, w1 = (a1 + 15) & ~(uintptr_t)15;
+                const uintptr_t lo = reinterpret_cast<uintptr_t>(Ci), hi = lo + 4ull * (unsigned)n * (unsigned)n;
+                if (w0 >= lo && w1 <= hi) {
+                    __syncwarp();   // every lane is done with the previous row in the buffer
+                    if (lane == 0) {
+                        fence_proxy_async();
+                        bulk_row(sbuf, reinterpret_cast<const void *>(w0), (unsigned)(w1 - w0), sbar);
+                    }
+                    const bool ok = __all_sync(0xffffffffu, mbar_wait(sbar, spar));
+                    spar ^= 1u;
+                    if (ok) {
+                        staged = true;
+                        d = (int)((a0 - w0) >> 2);
+                    } else {   // the copy never completed: stop staging on this warp, report it
+                        sok = false;
+                        if (lane == 0) atomicCAS(&sl.status, 0, (int)LA_ERR_INTERNAL);
+                    }
+                }
+            }
+            if (STAGE && staged) {
+                const volatile int *rb = sbuf + d;
+                if (d == 0 && (n & 3) == 0) {
+                    const int4 *r4 = reinterpret_cast<const int4 *>(sbuf);
+                    const int nv = n >> 2;
+#pragma unroll 2
+                    for (int j = lane; j < nv; j += 32) {
+                        const int4 c = r4[j];
+                        const int y = j << 2;
+                        lane2_push<V>(t, (V)(uint32_t)(c.x - cmin) * np1 + (V)key_q(vkey[y]), y);
+                        lane2_push<V>(t, (V)(uint32_t)(c.y - cmin) * np1 + (V)key_q(vkey[y + 1]), y + 1);
+                        lane2_push<V>(t, (V)(uint32_t)(c.z - cmin) * np1 + (V)key_q(vkey[y + 2]), y + 2);
+                        lane2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + (V)key_q(vkey[y + 3]), y + 3);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int y = lane; y < n; y += 32)
+                        lane2_push<V>(t, (V)(uint32_t)(rb[y] - cmin) * np1 + (V)key_q(vkey[y]), y);
+                }
+                const V c1 = t.w1 >= 0 ? (V)(uint32_t)(rb[t.w1] - cmin) * np1 : (V)0;
+                r = ScanResult<V>{t.b1, t.b2, c1, t.w1 < 0 ? INT_MAX : t.w1};
+                warp_merge(r);
+            } else {
+            prefetch_row_l2(crow, n, lane);
             if (vec) {
                 const int4 *r4 = reinterpret_cast<const int4 *>(crow);
                 const int nv = n >> 2;
@@ -381,6 +481,7 @@ __device__ bool run_chain(Slot &sl, unsigned long long *keys, const int32_t *__r
             const V c1 = t.w1 >= 0 ? (V)(uint32_t)(ld_row1(crow + t.w1) - cmin) * np1 : (V)0;
             r = ScanResult<V>{t.b1, t.b2, c1, t.w1 < 0 ? INT_MAX : t.w1};
             warp_merge(r);
+            }
         }
         const unsigned long long nq = give_up ? 0ull : (unsigned long long)(r.b1 - r.c1) + (r.b2 - r.b1) + eps;
         if (!give_up && (r.w >= n || nq > qlim)) {
@@ -493,14 +594,30 @@ __device__ void end_phase(const BatchArgs &a, Slot &sl, unsigned long long *keys
 // Without lists the kernel keeps 64 registers (72 below 256 threads) for two
 // or more CTAs per SM; with lists, the list scan's insertion network gets
 // the registers of one CTA per SM.
-template <int BLOCK, bool LISTS>
+template <int BLOCK, bool LISTS, bool STAGE>
 __global__ void __launch_bounds__(BLOCK, LISTS ? 1 : (BLOCK >= 256 ? 1024 / BLOCK : 7 * 128 / BLOCK))
 k_batch_solve(BatchArgs a, int S) {
-    extern __shared__ unsigned long long skey[];
+    static_assert(!(LISTS && STAGE), "row staging is for the list-free kernel");
+    extern __shared__ __align__(16) unsigned long long skey[];
     __shared__ Slot s_slot[kMaxSlots];
     constexpr int kWarps = BLOCK / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned long long wins = 0, displaced = 0, phases_run = 0;
+    // with STAGE: after the keys, one row buffer per warp, then one mbarrier per warp
+    int *sbuf = nullptr;
+    unsigned long long *sbar = nullptr;
+    unsigned spar = 0;
+    bool sok = true;
+    if (STAGE) {
+        int *rows = reinterpret_cast<int *>(skey + stage_key_words(S, a.max_n));
+        sbuf = rows + (size_t)warp * stage_stride(a.max_n);
+        sbar = reinterpret_cast<unsigned long long *>(rows + (size_t)kWarps * stage_stride(a.max_n)) + warp;
+        if (lane == 0) {
+            mbar_init(sbar);
+            fence_mbar_init();
+        }
+        __syncwarp();
+    }
     for (int s = warp; s < S; s += kWarps) load_next(a, s_slot[s], skey + (size_t)s * a.max_n, lane);
     __syncthreads();
     int s0 = warp % S;
@@ -562,13 +679,14 @@ k_batch_solve(BatchArgs a, int S) {
         }
         const unsigned long long R = v.rebase;
         const bool done = v.wide
-            ? run_chain<true, LISTS>(t, keys, a.C + v.off, row, n, v.cmin, v.eps, v.qlim, v.budget, v.vec != 0,
-                                     lane, wins, displaced, Li, R)
-            : run_chain<false, LISTS>(t, keys, a.C + v.off, row, n, v.cmin, v.eps, v.qlim, v.budget, v.vec != 0,
-                                      lane, wins, displaced, Li, R);
+            ? run_chain<true, LISTS, STAGE>(t, keys, a.C + v.off, row, n, v.cmin, v.eps, v.qlim, v.budget,
+                                            v.vec != 0, lane, wins, displaced, Li, R, sbuf, sbar, spar, sok)
+            : run_chain<false, LISTS, STAGE>(t, keys, a.C + v.off, row, n, v.cmin, v.eps, v.qlim, v.budget,
+                                             v.vec != 0, lane, wins, displaced, Li, R, sbuf, sbar, spar, sok);
         if (done) end_phase(a, t, keys, lane, phases_run);
         s0 = sl;
     }
+    if (STAGE && !sok) mbar_wait(sbar, spar ^ 1u);   // a copy that timed out: wait once more before exiting
     if (lane == 0) {
         atomicAdd(&a.ctrl->wins, wins);
         atomicAdd(&a.ctrl->displaced, displaced);
@@ -671,39 +789,39 @@ la_status ensure_bws(BatchWorkspace &w, int64_t B, int max_n) {
 
 // Persistent grid size on the current device (the shared-memory attribute is
 // per device, so it is set on every call; both are host calls, no GPU work).
-template <int BLOCK, bool LISTS>
+template <int BLOCK, bool LISTS, bool STAGE>
 int solve_grid(int num_sms, size_t smem) {
     // Always set: the kernel's static shared memory (the slot records) and
     // `smem` together must fit, and 48 KB is the limit without it.
-    cudaFuncSetAttribute(k_batch_solve<BLOCK, LISTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_batch_solve<BLOCK, LISTS, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch_solve<BLOCK, LISTS>, BLOCK, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch_solve<BLOCK, LISTS, STAGE>, BLOCK, smem);
     return num_sms * std::max(1, o);
 }
 
-template <bool LISTS>
+template <bool LISTS, bool STAGE>
 int solve_grid_for(int block, int num_sms, size_t smem) {
     switch (block) {
-    case 64: return solve_grid<64, LISTS>(num_sms, smem);
-    case 128: return solve_grid<128, LISTS>(num_sms, smem);
-    case 256: return solve_grid<256, LISTS>(num_sms, smem);
-    case 512: return solve_grid<512, LISTS>(num_sms, smem);
-    default: return solve_grid<1024, LISTS>(num_sms, smem);
+    case 64: return solve_grid<64, LISTS, STAGE>(num_sms, smem);
+    case 128: return solve_grid<128, LISTS, STAGE>(num_sms, smem);
+    case 256: return solve_grid<256, LISTS, STAGE>(num_sms, smem);
+    case 512: return solve_grid<512, LISTS, STAGE>(num_sms, smem);
+    default: return solve_grid<1024, LISTS, STAGE>(num_sms, smem);
     }
 }
 
-template <bool LISTS>
+template <bool LISTS, bool STAGE>
 void launch_solve(cudaStream_t s, int block, int grid, size_t smem, int slots, const BatchArgs &args) {
     switch (block) {
-    case 64: k_batch_solve<64, LISTS><<<grid, 64, smem, s>>>(args, slots); break;
-    case 128: k_batch_solve<128, LISTS><<<grid, 128, smem, s>>>(args, slots); break;
-    case 256: k_batch_solve<256, LISTS><<<grid, 256, smem, s>>>(args, slots); break;
-    case 512: k_batch_solve<512, LISTS><<<grid, 512, smem, s>>>(args, slots); break;
-    default: k_batch_solve<1024, LISTS><<<grid, 1024, smem, s>>>(args, slots); break;
+    case 64: k_batch_solve<64, LISTS, STAGE><<<grid, 64, smem, s>>>(args, slots); break;
+    case 128: k_batch_solve<128, LISTS, STAGE><<<grid, 128, smem, s>>>(args, slots); break;
+    case 256: k_batch_solve<256, LISTS, STAGE><<<grid, 256, smem, s>>>(args, slots); break;
+    case 512: k_batch_solve<512, LISTS, STAGE><<<grid, 512, smem, s>>>(args, slots); break;
+    default: k_batch_solve<1024, LISTS, STAGE><<<grid, 1024, smem, s>>>(args, slots); break;
     }
 }
 
-cudaError_t enqueue(cudaStream_t s, int block, int grid, size_t smem, int slots, const BatchArgs &args,
+cudaError_t enqueue(cudaStream_t s, int block, int grid, size_t smem, int slots, bool stage, const BatchArgs &args,
                     int *hist, int num_sms) {
     cudaError_t e = cudaMemsetAsync(args.ctrl, 0, sizeof(BatchCtrl), s);
     if (e != cudaSuccess) return e;
@@ -714,8 +832,9 @@ cudaError_t enqueue(cudaStream_t s, int block, int grid, size_t smem, int slots,
     k_batch_minmax<<<mm_grid, 256, 0, s>>>(args.C, args.offsets, args.ns, args.B, args.max_n,
                                            const_cast<int2 *>(args.cminmax));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (args.lists.cols) launch_solve<true>(s, block, grid, smem, slots, args);
-    else launch_solve<false>(s, block, grid, smem, slots, args);
+    if (args.lists.cols) launch_solve<true, false>(s, block, grid, smem, slots, args);
+    else if (stage) launch_solve<false, true>(s, block, grid, smem, slots, args);
+    else launch_solve<false, false>(s, block, grid, smem, slots, args);
     return cudaGetLastError();
 }
 
@@ -755,7 +874,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
     int slots = (opt && opt->slots > 0) ? opt->slots : kDefaultSlots;
     slots = std::min(slots, kMaxSlots);
     slots = std::max(1, std::min(slots, (int)(kSlotSmemBudget / (sizeof(unsigned long long) * (size_t)max_n))));
-    const size_t smem = sizeof(unsigned long long) * (size_t)max_n * slots;
+    size_t smem = sizeof(unsigned long long) * (size_t)max_n * slots;
     // Candidate lists: asked for (lists > 0), or by default when instances may
     // be large (max_n >= kAutoListsN) and lists for B * max_n rows fit in
     // kAutoListsBytes.
@@ -766,8 +885,12 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
                            (lists_opt == 0 && max_n >= kAutoListsN && rows * list_row_bytes <= kAutoListsBytes);
     if (use_lists)
         if (la_status e = ensure_lists(w, rows)) return e;
-    const int grid_all = use_lists ? solve_grid_for<true>(block, w.num_sms, smem)
-                                   : solve_grid_for<false>(block, w.num_sms, smem);
+    // Row staging (list-free kernel) when the warps' row buffers fit beside the keys.
+    const bool stage = kStageRows && !use_lists && stage_smem(slots, max_n, block / 32) <= kStageSmemBudget;
+    if (stage) smem = stage_smem(slots, max_n, block / 32);
+    const int grid_all = use_lists ? solve_grid_for<true, false>(block, w.num_sms, smem)
+                                   : (stage ? solve_grid_for<false, true>(block, w.num_sms, smem)
+                                            : solve_grid_for<false, false>(block, w.num_sms, smem));
     int grid = grid_all;
     grid = std::max(1, std::min(grid, (int)((B + slots - 1) / slots)));
     BatchArgs args;
@@ -819,7 +942,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
             cudaGraph_t g = nullptr;
             cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (ce == cudaSuccess) {
-                const cudaError_t le = enqueue(cs, block, grid, smem, slots, args, w.hist, w.num_sms);
+                const cudaError_t le = enqueue(cs, block, grid, smem, slots, stage, args, w.hist, w.num_sms);
                 ce = cudaStreamEndCapture(cs, &g);
                 if (le != cudaSuccess) ce = le;
             }
@@ -836,7 +959,7 @@ static la_status batched_locked(const int32_t *cost, const int64_t *offsets, con
         LA_BCK(cudaGraphLaunch(w.exec, s));
         launched_graph = true;
     } else {
-        LA_BCK(enqueue(s, block, grid, smem, slots, args, w.hist, w.num_sms));
+        LA_BCK(enqueue(s, block, grid, smem, slots, stage, args, w.hist, w.num_sms));
     }
     if (profile) LA_BCK(cudaEventRecord(e1, s));
     LA_BCK(cudaMemcpyAsync(w.h_ctrl, w.ctrl, sizeof(BatchCtrl), cudaMemcpyDeviceToHost, s));
