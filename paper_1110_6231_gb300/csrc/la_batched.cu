@@ -1,19 +1,22 @@
 // la_solve_batched: many independent dense assignments in one persistent
 // launch (captured in a CUDA graph and replayed).
 //
-// Each CTA claims instances from a device work queue, largest first, and
-// runs the whole cost-scaling solve of an instance (Sect. 5.1, Algorithm
-// 5.0's epsilon loop; refine initialisation of Algorithm 5.2; the push /
-// relabel of Algorithm 5.4 as a double push) with the instance's column keys
-// in shared memory:
+// Each CTA keeps up to S instances resident ("slots") and runs the whole
+// cost-scaling solve of each (Sect. 5.1, Algorithm 5.0's epsilon loop;
+// refine initialisation of Algorithm 5.2; the push / relabel of Algorithm
+// 5.4 as a double push) with the instance's column keys in shared memory:
 //   * one 64-bit key per column, (price, mate) packed as in la_solve, so a
 //     bid is one shared-memory atomicMin;
-//   * the CTA's warps are the instance's parallel bidders ("rows per CTA" =
-//     warps per CTA): each takes a free row from a shared counter, scans its
-//     cost row from global memory against the shared prices, bids, and
-//     continues with the row it displaced;
-//   * a phase ends at a CTA barrier once the queue is empty and every warp's
-//     row is matched.
+//   * the CTA's warps take free rows from any resident instance (one
+//     shared-memory atomicAdd on the slot's claim word), scan the row against
+//     the shared prices, bid, and continue with the row they displaced;
+//   * a row is read into the warp's shared-memory buffer by one bulk copy
+//     (cp.async.bulk on a per-warp mbarrier), or, for large instances,
+//     through its exact candidate list as in la_solve;
+//   * an instance's phase ends when its last row is matched, with no CTA
+//     barrier; the warp that matched it starts the next phase or writes the
+//     instance's results and loads the next instance (largest first) from
+//     the device work queue.
 // Prices stay exact integers; per instance, costs are scaled by n + 1 and
 // the last phase runs at eps = 1, so every instance's cost is exact.
 #include <cuda_runtime.h>
