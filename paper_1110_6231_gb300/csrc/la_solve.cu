@@ -19,7 +19,12 @@
 //     push of w's old mate back, all at once. The displaced mate becomes
 //     the warp's next row; a lost bid rescans the same row.
 //   * the phase ends when the queue is empty and every warp's row is
-//     matched (the kernel exits); no host round trip inside a phase.
+//     matched; no host round trip inside a phase.
+// A row is scanned through its exact candidate list when the list decides
+// its bid (la_lists.cuh), and once a phase is down to a few free rows, the
+// refine hands them to k_tail, which finishes their displacement chains on
+// one CTA with the keys in shared memory; a second refine launch takes any
+// rows the tail kernel gives back.
 // Lemma 5.2 (prices never increase) makes stale price reads safe: they can
 // only make a bid lose, and a row holding a column keeps its
 // eps-complementary slackness while other prices fall.
