@@ -406,7 +406,9 @@ __device__ bool run_chain(Slot &sl, unsigned long long *keys, const int32_t *__r
             bool full = false;
             const SharedKeyPrices<WIDE> prices{keys};
             const ListAhead none{-1, 0ull, {}};
-            r = vec ? scan_for_bid<WIDE, true, true, 1>(Ci, row, n, cmin, np1, prices, lane, Li, R, full, none)
+            // two interleaved insertion chains in a full scan (measured 27 % faster than one
+            // on 304 n = 4096 instances; four were no better)
+            r = vec ? scan_for_bid<WIDE, true, true, 2>(Ci, row, n, cmin, np1, prices, lane, Li, R, full, none)
                     : scan_for_bid<WIDE, false, true, 1>(Ci, row, n, cmin, np1, prices, lane, Li, R, full, none);
             if (full && lane == 0) atomicAdd(&sl.full, 1ull);
         } else if (!give_up) {
