@@ -243,6 +243,38 @@ __host__ __device__ __forceinline__ size_t stage_smem(int S, int max_n, int warp
     return stage_key_words(S, max_n) * 8 + (size_t)warps * stage_stride(max_n) * 4 + (size_t)warps * 8;
 }
 
+// Key formats. 64-bit instances, and every instance of the lists kernel, use
+// la_solve's packing, (2^44 - 1 - q) << 20 | mate. 32-bit instances of the
+// list-free kernel use (2^32 - 1 - q) << 32 | mate: a scan then reads a
+// column's price as the key's high word, one 32-bit load and no shifts.
+// Both order keys by price, then holder, so a bid is the same atomicMin.
+constexpr uint32_t kNone32 = 0xFFFFFFFFu;
+__device__ __forceinline__ unsigned long long bkey_pack(bool k32, unsigned long long q, uint32_t mate) {
+    return k32 ? (((0xFFFFFFFFull - q) << 32) | mate) : pack_key(q, mate);
+}
+__device__ __forceinline__ unsigned long long bkey_q(bool k32, unsigned long long k) {
+    return k32 ? (0xFFFFFFFFull - (k >> 32)) : key_q(k);
+}
+__device__ __forceinline__ uint32_t bkey_mate(bool k32, unsigned long long k) {
+    return k32 ? (uint32_t)k : key_mate(k);
+}
+__device__ __forceinline__ uint32_t bkey_none(bool k32) { return k32 ? kNone32 : kNone; }
+
+// v(y) = (c - cmin)(n + 1) + q(y) for a scanned cost c. With 32-bit keys,
+// q(y) = 2^32 - 1 - hi(key(y)) and the constant folds into k2 =
+// -cmin (n + 1) - 1 (mod 2^32): v = c (n + 1) + k2 - hi, exact because a
+// 32-bit instance's values fit in 32 bits.
+template <bool WIDE, bool K32, typename V>
+__device__ __forceinline__ V bval(int c, int y, int cmin, uint32_t np1, uint32_t k2,
+                                  const volatile unsigned long long *vkey) {
+    if (K32) {
+        const volatile uint32_t *hi = reinterpret_cast<const volatile uint32_t *>(vkey);
+        return (V)((uint32_t)c * np1 + k2 - hi[2 * y + 1]);
+    } else {
+        return (V)(uint32_t)(c - cmin) * np1 + (V)key_q(vkey[y]);
+    }
+}
+
 // One instance resident in a CTA. Rows are claimed with one atomicAdd on
 // `claim` = (n << 32) | next row: a claim is valid exactly when the returned
 // index is below the returned n, so no claim can land between two phases or
@@ -257,6 +289,7 @@ struct Slot {
     long long moff;      // offset of its rows in match_out / prices_out
     int inst;            // instance index, -1 = empty
     int n, cmin, phase, nph, alpha, wide, vec;
+    int k32;             // keys in the 32-bit-price format (bkey_*)
     int unmatched;       // rows not yet matched (or given up) in this phase
     int status;
 };
@@ -354,6 +387,7 @@ __device__ void load_next(const BatchArgs &a, Slot &sl, unsigned long long *keys
             v.phase = 0;
             v.eps = eps1;
             v.wide = wide;
+            v.k32 = !wide && !a.lists.cols;
             v.qlim = wide ? (kQMax - 1) : ((1ull << 32) - 2 - Ct);
             v.vec = ((a.offsets[i] & 3) == 0) && (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15) == 0);
             v.budget = (unsigned long long)a.P.budget_factor * n * nph + 4096;
@@ -388,8 +422,10 @@ __device__ bool run_chain(Slot &sl, unsigned long long *keys, const int32_t *__r
                           const RowLists &Li, unsigned long long R, int *sbuf, unsigned long long *sbar,
                           unsigned &spar, bool &sok) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    constexpr bool K32 = !WIDE && !LISTS;
     const volatile unsigned long long *vkey = keys;
     const uint32_t np1 = (uint32_t)n + 1;
+    const uint32_t k2 = (0u - (uint32_t)cmin) * np1 - 1u;
     for (;;) {
         unsigned long long s = 0;
         int st = 0;
@@ -449,15 +485,15 @@ __device__ bool run_chain(Slot &sl, unsigned long long *keys, const int32_t *__r
                     for (int j = lane; j < nv; j += 32) {
                         const int4 c = r4[j];
                         const int y = j << 2;
-                        lane2_push<V>(t, (V)(uint32_t)(c.x - cmin) * np1 + (V)key_q(vkey[y]), y);
-                        lane2_push<V>(t, (V)(uint32_t)(c.y - cmin) * np1 + (V)key_q(vkey[y + 1]), y + 1);
-                        lane2_push<V>(t, (V)(uint32_t)(c.z - cmin) * np1 + (V)key_q(vkey[y + 2]), y + 2);
-                        lane2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + (V)key_q(vkey[y + 3]), y + 3);
+                        lane2_push<V>(t, bval<WIDE, K32, V>(c.x, y, cmin, np1, k2, vkey), y);
+                        lane2_push<V>(t, bval<WIDE, K32, V>(c.y, y + 1, cmin, np1, k2, vkey), y + 1);
+                        lane2_push<V>(t, bval<WIDE, K32, V>(c.z, y + 2, cmin, np1, k2, vkey), y + 2);
+                        lane2_push<V>(t, bval<WIDE, K32, V>(c.w, y + 3, cmin, np1, k2, vkey), y + 3);
                     }
                 } else {
 #pragma unroll 4
                     for (int y = lane; y < n; y += 32)
-                        lane2_push<V>(t, (V)(uint32_t)(rb[y] - cmin) * np1 + (V)key_q(vkey[y]), y);
+                        lane2_push<V>(t, bval<WIDE, K32, V>(rb[y], y, cmin, np1, k2, vkey), y);
                 }
                 const V c1 = t.w1 >= 0 ? (V)(uint32_t)(rb[t.w1] - cmin) * np1 : (V)0;
                 r = ScanResult<V>{t.b1, t.b2, c1, t.w1 < 0 ? INT_MAX : t.w1};
@@ -471,16 +507,16 @@ __device__ bool run_chain(Slot &sl, unsigned long long *keys, const int32_t *__r
                 for (int j = lane; j < nv; j += 32) {
                     const int4 c = ld_row4(r4 + j);
                     const int y = j << 2;
-                    lane2_push<V>(t, (V)(uint32_t)(c.x - cmin) * np1 + (V)key_q(vkey[y]), y);
-                    lane2_push<V>(t, (V)(uint32_t)(c.y - cmin) * np1 + (V)key_q(vkey[y + 1]), y + 1);
-                    lane2_push<V>(t, (V)(uint32_t)(c.z - cmin) * np1 + (V)key_q(vkey[y + 2]), y + 2);
-                    lane2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + (V)key_q(vkey[y + 3]), y + 3);
+                    lane2_push<V>(t, bval<WIDE, K32, V>(c.x, y, cmin, np1, k2, vkey), y);
+                    lane2_push<V>(t, bval<WIDE, K32, V>(c.y, y + 1, cmin, np1, k2, vkey), y + 1);
+                    lane2_push<V>(t, bval<WIDE, K32, V>(c.z, y + 2, cmin, np1, k2, vkey), y + 2);
+                    lane2_push<V>(t, bval<WIDE, K32, V>(c.w, y + 3, cmin, np1, k2, vkey), y + 3);
                 }
             } else {
 #pragma unroll 4
                 for (int y = lane; y < n; y += 32) {
                     const int c = ld_row1(crow + y);
-                    lane2_push<V>(t, (V)(uint32_t)(c - cmin) * np1 + (V)key_q(vkey[y]), y);
+                    lane2_push<V>(t, bval<WIDE, K32, V>(c, y, cmin, np1, k2, vkey), y);
                 }
             }
             const V c1 = t.w1 >= 0 ? (V)(uint32_t)(ld_row1(crow + t.w1) - cmin) * np1 : (V)0;
@@ -502,12 +538,12 @@ __device__ bool run_chain(Slot &sl, unsigned long long *keys, const int32_t *__r
             left = __shfl_sync(0xffffffffu, left, 0);
             return left == 0;
         }
-        const unsigned long long nk = pack_key(nq, (uint32_t)row);
+        const unsigned long long nk = bkey_pack(K32, nq, (uint32_t)row);
         unsigned long long old = 0;
         int left = 1;
         if (lane == 0) {
             old = atomicMin(keys + r.w, nk);
-            if (old > nk && key_mate(old) == kNone) {
+            if (old > nk && bkey_mate(K32, old) == bkey_none(K32)) {
                 __threadfence_block();   // the commit is visible before the count can reach 0
                 left = atomicSub(&sl.unmatched, 1) - 1;
             }
@@ -516,8 +552,8 @@ __device__ bool run_chain(Slot &sl, unsigned long long *keys, const int32_t *__r
         left = __shfl_sync(0xffffffffu, left, 0);
         if (old > nk) {
             ++wins;
-            const uint32_t m = key_mate(old);
-            if (m == kNone) return left == 0;
+            const uint32_t m = bkey_mate(K32, old);
+            if (m == bkey_none(K32)) return left == 0;
             ++displaced;
             row = (int)m;
         }
@@ -539,9 +575,10 @@ __device__ void end_phase(const BatchArgs &a, Slot &sl, unsigned long long *keys
     const int st = v.status;
     if (st == 0 && v.phase + 1 < v.nph) {
         unsigned long long m = ~0ull;
-        for (int y = lane; y < n; y += 32) m = min(m, key_q(keys[y]));
+        const bool k32 = v.k32 != 0;
+        for (int y = lane; y < n; y += 32) m = min(m, bkey_q(k32, keys[y]));
         m = warp_min(m);
-        for (int y = lane; y < n; y += 32) keys[y] = pack_key(key_q(keys[y]) - m, kNone);
+        for (int y = lane; y < n; y += 32) keys[y] = bkey_pack(k32, bkey_q(k32, keys[y]) - m, bkey_none(k32));
         if (lane == 0) {
             v.rebase = v.rebase + m;
             v.eps = max(1ull, v.eps / (unsigned long long)v.alpha);
@@ -562,13 +599,13 @@ __device__ void end_phase(const BatchArgs &a, Slot &sl, unsigned long long *keys
     if (fst == 0) {
         bool bad = false;
         for (int y = lane; y < n; y += 32) {
-            const uint32_t mm = key_mate(keys[y]);
+            const uint32_t mm = bkey_mate(v.k32 != 0, keys[y]);
             if (mm >= (uint32_t)n) {
                 bad = true;
                 continue;
             }
             if (a.match_out) a.match_out[mo + mm] = y;
-            if (a.prices_out) a.prices_out[mo + y] = -(long long)key_q(keys[y]);
+            if (a.prices_out) a.prices_out[mo + y] = -(long long)bkey_q(v.k32 != 0, keys[y]);
             sum += Ci[(size_t)mm * n + y];
         }
         if (__any_sync(0xffffffffu, bad)) fst = LA_ERR_INTERNAL;
