@@ -499,7 +499,9 @@ def run_gpu(args):
                              "traffic": recorded_traffic(WORKLOAD, kname),
                              "algorithmic_bytes_per_launch": kbytes / max(1, phases_run),
                              "avg_launch_ms": kms / max(1, phases_run),
-                             "share_of_refine_time": kms / phase_ms if phase_ms > 0 else None}
+                             "share_of_refine_time": kms / phase_ms if phase_ms > 0 else None,
+                             # what actually bounds these kernels (ncu: DRAM and issue far from their peaks)
+                             "regime": "latency: dependent displacement chains, few warps busy at once"}
     dominant = max(per_kernel, key=lambda k: per_kernel[k]["avg_launch_ms"])
 
     # The 64 MiB matrix stays in L2 across a solve's phases, so the refine
