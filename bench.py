@@ -505,7 +505,7 @@ def run_gpu(args):
     dominant = max(per_kernel, key=lambda k: per_kernel[k]["avg_launch_ms"])
 
     # The 64 MiB matrix stays in L2 across a solve's phases, so the refine
-    # kernels are also judged against the L2 read rate, measured here by the
+    # kernels are also compared with the L2 read rate, measured here by the
     # library's probe on the timed matrix itself (20 passes in one launch
     # after an untimed one), beside its HBM read rate on a 4 GiB buffer.
     la.probe_read_gbps(dmats[0], 1, stream=stream)

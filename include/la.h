@@ -489,7 +489,7 @@ la_status la_solve_noalloc(const int32_t *cost, int32_t n, void *stream,
  * la_probe_read -- read-bandwidth probe (a measurement utility; no solve
  * uses it). It supplies the measured peak of the cache level a scan's data
  * comes from: a 64 MiB cost matrix (n = 4096) stays in the 129 MB L2 across
- * the phases of a solve, so the refine's arc-scan rate is judged against the
+ * the phases of a solve, so the refine's arc-scan rate is compared with the
  * L2 read rate, which no vendor figure states.
  *   buf    device buffer of `bytes` bytes, 16-byte aligned; read only.
  *   bytes  a multiple of 16, > 0.
