@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -113,12 +114,12 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, out_dir=None):
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
         ids = [v.strip() for v in vis.split(",") if v.strip()]
         self.index = ids[index] if index < len(ids) else str(index)
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(out_dir or tempfile.gettempdir(), f"clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
@@ -458,7 +459,7 @@ def run_gpu(args):
         step(i)
     stats = []
     barrier()
-    with Clocks(local) as clk:
+    with Clocks(local, args.clocks_dir) as clk:
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
@@ -625,6 +626,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="batched line with the library defaults, no autotuner")
     ap.add_argument("--warm-n1024", type=int, default=100)
     ap.add_argument("--warm-n8192", type=int, default=4)
+    ap.add_argument("--clocks-dir", default=None,
+                    help="folder for the raw nvidia-smi samples (default: the temp folder)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
