@@ -266,16 +266,28 @@ def bench_concurrent(args, la, synth, dev, stream, alpha):
     resident per CTA, two CTAs per SM): throughput when the caller has many
     instances, beside the single-solve latency of the headline. The distinct
     matrices (seeds 2000, 2001, ...) are drawn on the GPU by the torch twin
-    of the generator."""
+    of the generator. Unless --alpha fixes it, alpha is tuned first on as
+    many other instances (seeds 3000, 3001, ...), which are not timed."""
     import torch
     n, B = 4096, args.concurrent
     dc = torch.empty(B * n * n, dtype=torch.int32, device=dev)
-    for i in range(B):
-        dc[i * n * n:(i + 1) * n * n] = synth.uniform_costs_torch(n, 0, (1 << 20) - 1, 2000 + i, device=dev).view(-1)
+
+    def fill(seed0):
+        for i in range(B):
+            dc[i * n * n:(i + 1) * n * n] = synth.uniform_costs_torch(n, 0, (1 << 20) - 1, seed0 + i,
+                                                                      device=dev).view(-1)
+
     off = torch.arange(B, dtype=torch.int64, device=dev) * (n * n)
     ns = torch.full((B,), n, dtype=torch.int32, device=dev)
-    opt = la.batch_options(block_threads=256, slots=2, max_n=n, alpha=[alpha] * la.LA_ALPHA_BUCKETS, profile=True,
-                           lists=1)
+    shape = dict(block_threads=256, slots=2, max_n=n, lists=1)
+    tuning = None
+    if args.alpha == 0:
+        from paper_1110_6231_gb300 import tune
+        fill(3000)
+        tuning = tune.autotune_batch_alpha(dc, off, ns, **shape)
+        alpha = tuning["alpha"]
+    fill(2000)
+    opt = la.batch_options(alpha=[alpha] * la.LA_ALPHA_BUCKETS, profile=True, **shape)
     la.solve_batched(dc, off, ns, options=opt)           # capture the graph
     best, stats = None, None
     for _ in range(2):
@@ -293,7 +305,10 @@ def bench_concurrent(args, la, synth, dev, stream, alpha):
             "scans_per_instance": stats["scans"] / B,
             "scan_GBps": stats["scan_bytes"] / (stats["device_ms"] * 1e-3) / 1e9,
             "full_scan_fraction": stats["full_scans"] / max(1, stats["scans"]),
-            "shape": {"block_threads": 256, "slots": 2, "grid": stats["grid"], "alpha": alpha, "lists": stats["lists"]}}
+            "shape": {"block_threads": 256, "slots": 2, "grid": stats["grid"], "alpha": alpha, "lists": stats["lists"]},
+            "alpha_tuning": None if tuning is None else
+            {"over": f"{B} other instances (seeds 3000..{3000 + B - 1}), not timed, one launch per alpha",
+             "device_ms": {str(a): round(v, 2) for a, v in tuning["device_ms"].items()}}}
 
 
 def bench_warm(args, la, synth, dev):

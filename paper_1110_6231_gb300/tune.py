@@ -35,6 +35,11 @@ DEFAULT_SHAPES = ((256, 2), (512, 2), (512, 4), (1024, 8))   # (threads per CTA,
 
 DEFAULT_SINGLE_ALPHAS = (8, 10, 16, 24, 32, 48, 64)
 
+# One alpha for a batch of same-size instances that fills the GPU: its time
+# follows the total bidding more than the end of each phase, so larger
+# alphas than a single solve's stay in the running.
+DEFAULT_BATCH_ALPHAS = (32, 64, 128, 256, 1024)
+
 
 def autotune_alpha(samples, *, alphas=DEFAULT_SINGLE_ALPHAS, reps: int = 3) -> dict:
     """Fastest alpha for ``la.solve`` on the square int32 CUDA matrices in
@@ -57,6 +62,39 @@ def autotune_alpha(samples, *, alphas=DEFAULT_SINGLE_ALPHAS, reps: int = 3) -> d
                 total += time.perf_counter() - t0
         mean[int(a)] = 1e3 * total / (reps * len(samples))
     return {"alpha": min(mean, key=mean.get), "mean_ms": mean}
+
+
+def autotune_batch_alpha(costs, offsets, ns, *, alphas=DEFAULT_BATCH_ALPHAS, reps: int = 1,
+                         **options) -> dict:
+    """Fastest single alpha for one batch (CUDA tensors: int32 costs, int64
+    offsets, int32 ns), every other option fixed by ``options`` (keywords of
+    ``la.batch_options``). A candidate under which any instance reports a
+    nonzero status is not eligible. Returns ``{"alpha": best, "device_ms":
+    {alpha: ms}}``."""
+    import torch
+    B = int(ns.numel())
+    total = int(ns.sum().item())
+    match = torch.empty(max(1, total), dtype=torch.int32, device=costs.device)
+    out = torch.empty(max(1, B), dtype=torch.int64, device=costs.device)
+    status = torch.empty(max(1, B), dtype=torch.int32, device=costs.device)
+    ms = {}
+    for a in alphas:
+        opt = la.batch_options(alpha=int(a), no_graph=True, profile=True, **options)
+        best = None
+        for _ in range(reps):
+            st = la.la_batch_stats()
+            rc = la.la_solve_batched_ex(costs, offsets, ns, B, opt, None, match, out, status, st)
+            if rc != la.LA_OK:
+                raise la.LaError(rc, "autotune_batch_alpha")
+            if int((status[:B] != 0).sum().item()):
+                best = None
+                break
+            best = st.device_ms if best is None else min(best, st.device_ms)
+        if best is not None:
+            ms[int(a)] = best
+    if not ms:
+        raise la.LaError(la.LA_ERR_ITER_LIMIT, "autotune_batch_alpha: no alpha solved every instance")
+    return {"alpha": min(ms, key=ms.get), "device_ms": ms}
 
 
 def _bucket(n: int) -> int:

@@ -173,7 +173,8 @@ def test_concurrent_n4096_instances_one_per_cta(la):
     """The ten stored n = 4096 optima (costs in [0, 2^20), 64-bit reduced
     costs) solved concurrently, one instance per CTA, from matrices drawn on
     the GPU by the torch twin of the generator (checked against the stored
-    digests first)."""
+    digests first); then in the throughput line's shape at every alpha its
+    tuner may pick."""
     import hashlib
     import json
     import os
@@ -197,6 +198,15 @@ def test_concurrent_n4096_instances_one_per_cta(la):
         match = sol.match.cpu().numpy()
         C0 = synth.instance("uniform-n4096-c2^20", cases[0]["seed"])
         assert oracle.check_matching(C0, match[:n], cases[0]["cost"]) == 0
+    # the shape and every alpha the throughput line may be tuned to
+    from paper_1110_6231_gb300 import tune
+    shape = dict(block_threads=256, slots=2, max_n=n, lists=1)
+    tuned = tune.autotune_batch_alpha(dc, off, ns, **shape)
+    assert tuned["alpha"] in tune.DEFAULT_BATCH_ALPHAS
+    assert sorted(tuned["device_ms"]) == sorted(tune.DEFAULT_BATCH_ALPHAS)
+    for a in tune.DEFAULT_BATCH_ALPHAS:
+        sol = la.solve_batched(dc, off, ns, options=la.batch_options(alpha=[a] * 16, **shape))
+        assert sol.costs.cpu().tolist() == [c["cost"] for c in cases], a
 
 
 def test_invalid_sizes_flagged_per_instance(la):
