@@ -111,8 +111,9 @@ def test_hall_violations_pass_the_threshold():
     """Two rows whose only arcs go to one column, beside an otherwise
     complete graph: no row or column is empty, yet no perfect matching
     exists, and the two rows outbid each other past 4n + 4."""
-    for n in range(2, 9):
+    for n in range(3, 9):
         rows = [[0], [0]] + [list(range(n)) for _ in range(n - 2)]
+        assert all(any(y in r for r in rows) for y in range(n))
         assert not _feasible(n, rows)
         for s in range(4):
             assert _zero_cost_phase(n, rows, random.Random(s))[0] == "infeasible"
