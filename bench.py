@@ -28,6 +28,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -86,11 +87,21 @@ def peaks():
 SINGLE_SOLVE_SOURCES = ("la_solve.cu", "la_device.cuh", "la_lists.cuh")
 
 
+def code_tokens(text: str) -> str:
+    """C/CUDA source without its comments and with whitespace runs collapsed,
+    so that an edit to a comment leaves the kernel hash unchanged (none of
+    the hashed sources has a comment marker inside a string literal)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash():
+    """Hash of the code (not the comments) of the single-solve kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1110_6231_gb300", "csrc")
     for name in SINGLE_SOLVE_SOURCES:
-        h.update(open(os.path.join(csrc, name), "rb").read())
+        h.update(code_tokens(open(os.path.join(csrc, name)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1038,8 +1038,8 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         if (sched.back() != 1) return LA_ERR_INVALID;
     }
     stats.eps_first = (int64_t)sched[0];
-    // 32-bit reduced costs when every v = c~ + q provably fits (q stays below
-    // S + 3 C~ + 2 eps during a phase; see the range argument in DESIGN).
+    // 32-bit reduced costs when every v = c~ + q provably fits: a phase from
+    // spread S' keeps q <= S' + 2 C~ + 2 eps and ends with S' <= C~ + eps.
     const unsigned long long need32 = S + 4 * Ct + 2 * sched[0] + 16;
     const bool wide = need32 >= (1ull << 32);
     const unsigned long long qlim = wide ? (kQMax - 1) : ((1ull << 32) - 2 - Ct);

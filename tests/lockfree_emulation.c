@@ -41,7 +41,10 @@
  *   out: int64 cost, int64 phases, int64 bids, n int32 matches, n int64
  *        prices (p = -q, paper sign, units of (n+1) C), int64 list scans,
  *        int64 full scans
- * Exit status 0 on success, 1 on a bad input, 2 on an internal error.
+ * Exit status 0 on success, 1 on a bad input, 2 on an internal error, 3
+ * when a price bound that the GPU's 32-bit path relies on is broken: within
+ * a phase every q stays <= S + 2 C~ + 2 eps (S = the largest q after the
+ * phase's shift), and after a phase the spread max q - min q is <= C~ + eps.
  * Compiling with -DLIST_MUTANT=1 (the shift ignored) or 2 (theta taken as the
  * largest bound instead of the least) plants a mistake in the list rule, so
  * that the tests can show that they would see one.
@@ -80,6 +83,7 @@ static uint64_t *ltheta, *lrb;    /* bound (UINT64_MAX: all listed), shift sum a
 static unsigned char *lvalid;
 static uint64_t R_total;          /* sum of the per-phase shifts */
 static _Atomic int64_t list_scans, full_scans;
+static _Atomic uint64_t qpeak;     /* the largest q committed in this phase */
 
 static uint64_t pack(uint64_t q, uint64_t mate) { return ((QMAX - q) << MATE_BITS) | mate; }
 static uint64_t key_q(uint64_t k) { return QMAX - (k >> MATE_BITS); }
@@ -221,6 +225,10 @@ static void chain(int x, uint64_t *tv, int *ty, int32_t *tc, int *seen) {
             }
         }
         if (!won) continue;   /* a lower price got there first: rescan x */
+        uint64_t pk = atomic_load_explicit(&qpeak, memory_order_relaxed);
+        while (nq > pk && !atomic_compare_exchange_weak_explicit(&qpeak, &pk, nq, memory_order_relaxed,
+                                                                 memory_order_relaxed)) {
+        }
         const uint64_t m = key_mate(cur);
         if (m == NONE) {
             atomic_fetch_sub_explicit(&unmatched, 1, memory_order_acq_rel);
@@ -313,12 +321,25 @@ int main(int argc, char **argv) {
         }
         for (int y = 0; y < n; ++y) atomic_store(&key[y], pack(key_q(atomic_load(&key[y])) - qmin, NONE));
         R_total += qmin;
+        uint64_t S = 0;
+        for (int y = 0; y < n; ++y) {
+            const uint64_t q = key_q(atomic_load(&key[y]));
+            if (q > S) S = q;
+        }
+        atomic_store(&qpeak, S);
         atomic_store(&next_row, 0);
         atomic_store(&unmatched, n);
         eps = e;
         ++phases_total;
         pthread_barrier_wait(&bar);   /* start */
         pthread_barrier_wait(&bar);   /* end */
+        uint64_t lo = UINT64_MAX, hi = 0;
+        for (int y = 0; y < n; ++y) {
+            const uint64_t q = key_q(atomic_load(&key[y]));
+            if (q < lo) lo = q;
+            if (q > hi) hi = q;
+        }
+        if (atomic_load(&qpeak) > S + 2 * Ct + 2 * e || hi - lo > Ct + e) return 3;
     } while (e > 1);
     eps = 0;
     pthread_barrier_wait(&bar);

@@ -4,8 +4,11 @@ ThreadSanitizer: no data race may be reported, every run must end, and the
 result must be the exact optimum (the oracle's Hungarian cost, a permutation
 of that cost, and eps-CS at eps = 1 with the final prices). The same holds
 with candidate lists, whose bound must stay sound across the price shifts
-between phases; two planted mistakes in the list rule must be seen. Nothing
-here touches a GPU."""
+between phases; two planted mistakes in the list rule must be seen. Every
+run also checks the price bounds that decide when the GPU may use 32-bit
+values (the emulation exits with status 3 if one breaks), and a sequential
+restatement shows that those bounds are reached. Nothing here touches a
+GPU."""
 
 import os
 import shutil
@@ -149,3 +152,85 @@ def test_a_broken_list_rule_is_seen(tmp_path, mutant):
             r = _run(bad, C, 10, 1, tmp_path, lanes, per_lane)
             seen += not _exact(C, r[0], r[3], r[4])
     assert seen > 0
+
+
+def test_price_bounds_hold_under_concurrency(tmp_path):
+    """The emulation stops with status 3 if a committed price passes
+    S + 2 C~ + 2 eps within a phase or the spread passes C~ + eps after it;
+    many small instances, thread counts and alphas must all finish cleanly."""
+    exe = _build(tmp_path, tsan=False)
+    rng = np.random.default_rng(9)
+    for t in range(40):
+        n = int(rng.integers(1, 41))
+        kind = t % 3
+        if kind == 0:
+            C = synth.uniform_costs(n, 0, int(rng.choice([1, 3, 100, 10**4])), t)
+        elif kind == 1:
+            C = synth.geometric_costs(max(n, 2), t)
+        else:
+            C = rng.integers(-5, 5, size=(n, n)).astype(np.int32)
+        for threads, alpha, lanes, per_lane in ((4, 2, 0, 0), (32, 10, 0, 0), (16, 64, 4, 1)):
+            cost, *_ = _run(exe, C, alpha, threads, tmp_path, lanes, per_lane)
+            assert cost == oracle.hungarian(C)[0]
+
+
+def _sequential_peaks(C, alpha, rng):
+    """Plain sequential double pushes with the free row drawn at random.
+    Returns, over the phases, the largest q / (S + 2 C~ + 2 eps) and the
+    largest spread / (C~ + eps)."""
+    n = C.shape[0]
+    cmin = int(C.min())
+    Ct = (n + 1) * (int(C.max()) - cmin)
+    cs = (C.astype(np.int64) - cmin) * (n + 1)
+    q = [0] * n
+    e = Ct
+    in_phase = after = 0.0
+    while True:
+        e = max(1, e // alpha)
+        m = min(q)
+        q = [v - m for v in q]
+        S = max(q)
+        holder = [-1] * n
+        free = list(range(n))
+        peak = S
+        while free:
+            x = free.pop(rng.randrange(len(free)))
+            b1 = b2 = w = None
+            for y in range(n):
+                v = int(cs[x, y]) + q[y]
+                if b1 is None or v < b1:
+                    b2, b1, w = b1, v, y
+                elif b2 is None or v < b2:
+                    b2 = v
+            if b2 is None:
+                b2 = b1
+            q[w] += (b2 - b1) + e
+            peak = max(peak, q[w])
+            if holder[w] >= 0:
+                free.append(holder[w])
+            holder[w] = x
+        in_phase = max(in_phase, peak / (S + 2 * Ct + 2 * e))
+        after = max(after, (max(q) - min(q)) / (Ct + e))
+        if e == 1:
+            return in_phase, after
+
+
+def test_price_bounds_are_reached():
+    """The two bounds hold on sequential schedules too, and are nearly or
+    exactly attained: the 32-bit test has no slack to spare."""
+    import random
+    rng = random.Random(5)
+    worst_in = worst_after = 0.0
+    for t in range(60):
+        n = rng.randint(1, 16)
+        if t % 3 == 0:
+            C = synth.uniform_costs(n, 0, rng.choice([1, 3, 100]), t)
+        elif t % 3 == 1:
+            C = synth.geometric_costs(max(n, 2), t)
+        else:
+            C = np.random.default_rng(t).integers(-5, 5, size=(n, n)).astype(np.int32)
+        for alpha in (2, 4, 10):
+            a, b = _sequential_peaks(C, alpha, random.Random(31 * t + alpha))
+            assert a <= 1.0 and b <= 1.0, (t, alpha, a, b)
+            worst_in, worst_after = max(worst_in, a), max(worst_after, b)
+    assert worst_in > 0.9 and worst_after == 1.0, (worst_in, worst_after)
