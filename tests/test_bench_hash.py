@@ -1,0 +1,38 @@
+"""bench.py reports the DRAM traffic of the single-solve kernels from a
+committed ncu record only while the kernels' code is the code it was taken
+on. The hash that decides this ignores comments and layout, and must change
+with any change to the code itself (CPU only)."""
+
+import bench
+
+SRC = """// a leading comment
+__global__ void k(int *a, int n) {   /* trailing
+   block comment */
+    int i = threadIdx.x;  // index
+    if (i < n) a[i] = 2 * i;
+}
+"""
+
+
+def test_comments_and_layout_do_not_count():
+    edited = SRC.replace("// index", "// the lane's index").replace("a leading", "another")
+    relaid = SRC.replace("    int i", "\tint  i").replace("\n}", "\n\n}")
+    assert bench.code_tokens(edited) == bench.code_tokens(SRC)
+    assert bench.code_tokens(relaid) == bench.code_tokens(SRC)
+    assert "comment" not in bench.code_tokens(SRC) and "index" not in bench.code_tokens(SRC)
+
+
+def test_code_changes_count():
+    for old, new in (("2 * i", "3 * i"), ("i < n", "i <= n"), ("int *a", "long *a")):
+        assert bench.code_tokens(SRC.replace(old, new)) != bench.code_tokens(SRC)
+
+
+def test_hashed_sources_hold_no_comment_marker_in_a_string():
+    """The stripper does not parse string literals; the hashed files must not
+    need it to."""
+    import os
+    import re
+    csrc = os.path.join(bench.ROOT, "paper_1110_6231_gb300", "csrc")
+    for name in bench.SINGLE_SOLVE_SOURCES:
+        text = open(os.path.join(csrc, name)).read()
+        assert not re.search(r'"[^"\n]*(//|/\*)[^"\n]*"', text), name
