@@ -23,7 +23,10 @@
  * Usage: maxflow_emulation <in> <out>
  *   in:  int32 H, W, threads, cycle, then int32 cap[4][H*W] (directions
  *        right, left, down, up), src[H*W], snk[H*W]
- *   out: int64 flow, int64 rounds
+ *   out: int64 flow, int64 rounds, int64 total excess (the sum of the source
+ *        arcs), int64 stranded excess (held by pixels that cannot reach t
+ *        after the last global relabel), then uint8 side[H*W]: 1 for a pixel
+ *        that cannot reach t (the source side of a minimum cut), else 0
  * Exit status 0 on success, 1 on a bad input, 2 on an internal error.
  */
 #define _POSIX_C_SOURCE 200809L
@@ -177,10 +180,20 @@ int main(int argc, char **argv) {
     atomic_store(&done, 1);
     pthread_barrier_wait(&bar);
     for (int t = 0; t < T; ++t) pthread_join(th[t], NULL);
+    int64_t total = 0, stranded = 0;
+    unsigned char *side = malloc((size_t)N);
+    if (!side) return 2;
+    for (int u = 0; u < N; ++u) {
+        total += buf[(size_t)4 * N + u];
+        side[u] = atomic_load(&h[u]) >= NV;
+        if (side[u]) stranded += atomic_load(&e[u]);
+        else if (atomic_load(&e[u]) != 0) return 2;   /* excess left where t is reachable */
+    }
     FILE *o = fopen(argv[2], "wb");
     if (!o) return 2;
-    const int64_t out[2] = {atomic_load(&e_t), rounds};
-    fwrite(out, sizeof(int64_t), 2, o);
+    const int64_t out[4] = {atomic_load(&e_t), rounds, total, stranded};
+    fwrite(out, sizeof(int64_t), 4, o);
+    fwrite(side, 1, (size_t)N, o);
     fclose(o);
     return 0;
 }

@@ -2,7 +2,10 @@
 with a global relabel between them, Algorithm 4.8), emulated by host threads
 with C11 atomics (tests/maxflow_emulation.c) and run under ThreadSanitizer: no
 data race may be reported, every run must end, and the flow must equal the
-oracle's (Dinic). Nothing here touches a GPU."""
+oracle's (Dinic). Every run also checks the stopping rule's reading: the
+flow plus the excess stranded at pixels that cannot reach t is the total
+excess, and those pixels (with s) are the source side of a cut whose
+capacity is the flow. Nothing here touches a GPU."""
 
 import os
 import shutil
@@ -59,8 +62,20 @@ def _run(exe, cap, src, snk, threads, cycle, tmp_path, timeout=300):
     env = dict(os.environ, TSAN_OPTIONS="halt_on_error=1 exitcode=66")
     r = subprocess.run([exe, str(inp), str(out)], capture_output=True, text=True, timeout=timeout, env=env)
     assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
-    flow, rounds = np.frombuffer(open(out, "rb").read(), dtype=np.int64)
-    return int(flow), int(rounds)
+    raw = open(out, "rb").read()
+    flow, rounds, total, stranded = (int(v) for v in np.frombuffer(raw[:32], dtype=np.int64))
+    side = np.frombuffer(raw[32:32 + H * W], dtype=np.uint8)
+    # the stopping rule's bookkeeping: every unit of excess reached t or is
+    # held by a pixel that cannot reach t (a maximum preflow)
+    assert flow + stranded == total, (flow, stranded, total)
+    # the pixels that cannot reach t, with s, form the source side of a cut
+    # whose capacity is the flow: a minimum cut
+    nn, tail, head, acap, s, t = oracle.grid_arcs(cap, src, snk)
+    full = np.zeros(nn, dtype=np.uint8)
+    full[:H * W] = side
+    full[s] = 1
+    assert oracle.cut_capacity(nn, tail, head, acap, s, t, full) == flow
+    return flow, rounds
 
 
 def _dinic(cap, src, snk):
