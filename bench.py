@@ -588,18 +588,28 @@ def run_gpu(args):
         extra["paper_alpha10"] = {"solves_per_s": ROTATE / dt10, "ms": 1e3 * dt10 / ROTATE,
                                   "steps": ROTATE, "alpha": 10}
     wanted = set() if args.no_extra else set(args.extras.split(","))
+
+    def guarded(fn, *a, **k):
+        # an extra line that fails is reported in its own entry; the headline
+        # line is still printed (extras make no collective calls, so ranks
+        # cannot fall out of step)
+        try:
+            return fn(*a, **k)
+        except Exception as ex:
+            return {"error": f"{type(ex).__name__}: {ex}"[:400]}
+
     if "batched" in wanted:
-        extra["batched"] = bench_batched(args, la, synth, dev, stream)
+        extra["batched"] = guarded(bench_batched, args, la, synth, dev, stream)
     if "concurrent" in wanted:
-        extra["concurrent_n4096"] = bench_concurrent(args, la, synth, dev, stream, alpha)
+        extra["concurrent_n4096"] = guarded(bench_concurrent, args, la, synth, dev, stream, alpha)
     if "warm" in wanted:
-        extra["warm_start"] = bench_warm(args, la, synth, dev)
+        extra["warm_start"] = guarded(bench_warm, args, la, synth, dev)
     if "geometric" in wanted:
-        extra["geometric_n8192"] = bench_single(la, synth, dev, "geometric-n8192", reps=2)
+        extra["geometric_n8192"] = guarded(bench_single, la, synth, dev, "geometric-n8192", reps=2)
     if "sparse" in wanted:
-        extra["sparse"] = bench_sparse(la, synth, dev)
+        extra["sparse"] = guarded(bench_sparse, la, synth, dev)
     if "maxflow" in wanted:
-        extra["maxflow"] = bench_maxflow(la, synth, dev)
+        extra["maxflow"] = guarded(bench_maxflow, la, synth, dev)
 
     line = None
     if rank == 0:
