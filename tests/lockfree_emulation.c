@@ -35,9 +35,19 @@
  *   - only the thread that holds row x writes its list; the next holder reads
  *     it after the compare-and-swap (or the phase barrier) that passed x on.
  *
+ * Price mirror (optional; the single-solve refine's read path): scans read
+ * column prices from a separate array instead of the keys. After every
+ * commit attempt on column w the bidder raises mirror[w] (an atomic
+ * maximum) to the price its compare-and-swap left in the key: its own bid
+ * when it won, the key's price when it lost. So the mirror never exceeds
+ * the key's price, and a scan that reads a stale (lower) price still bids
+ * within eps of every column (prices only grow inside a phase, Lemma 5.2).
+ * At a phase change the mirror is rewritten from the shifted keys.
+ *
  * Usage: lockfree_emulation <in> <out>
  *   in:  int32 n, int32 alpha, int32 threads, int32 lanes, int32 per_lane
- *        (lanes = 0: no lists), then n*n int32 costs (row-major)
+ *        (lanes = 0: no lists), int32 mirror (0: prices read from the keys),
+ *        then n*n int32 costs (row-major)
  *   out: int64 cost, int64 phases, int64 bids, n int32 matches, n int64
  *        prices (p = -q, paper sign, units of (n+1) C), int64 list scans,
  *        int64 full scans
@@ -84,10 +94,18 @@ static unsigned char *lvalid;
 static uint64_t R_total;          /* sum of the per-phase shifts */
 static _Atomic int64_t list_scans, full_scans;
 static _Atomic uint64_t qpeak;     /* the largest q committed in this phase */
+static int use_mirror;
+static _Atomic uint64_t *mirror;   /* per column: a price <= the key's */
 
 static uint64_t pack(uint64_t q, uint64_t mate) { return ((QMAX - q) << MATE_BITS) | mate; }
 static uint64_t key_q(uint64_t k) { return QMAX - (k >> MATE_BITS); }
 static uint64_t key_mate(uint64_t k) { return k & NONE; }
+
+/* the price of column y as a scan reads it */
+static uint64_t price(int y) {
+    return use_mirror ? atomic_load_explicit(&mirror[y], memory_order_relaxed)
+                      : key_q(atomic_load_explicit(&key[y], memory_order_relaxed));
+}
 
 typedef struct {
     uint64_t b1, b2, c1;
@@ -103,7 +121,7 @@ static int list_scan(int x, Bid *r) {
         const int y = lcol[(size_t)x * E + k];
         if (y < 0) continue;
         const uint64_t cs = (uint64_t)(uint32_t)(lcost[(size_t)x * E + k] - cmin) * np1;
-        const uint64_t v = cs + key_q(atomic_load_explicit(&key[y], memory_order_relaxed));
+        const uint64_t v = cs + price(y);
         if (v < b1 || (v == b1 && y < w)) {
             b2 = b1;
             b1 = v;
@@ -138,7 +156,7 @@ static void full_scan(int x, Bid *r, uint64_t *tv, int *ty, int32_t *tc, int *se
     for (int l = 0; l < lanes; ++l) seen[l] = 0;
     for (int y = 0; y < n; ++y) {
         const uint64_t cs = (uint64_t)(uint32_t)(row[y] - cmin) * np1;
-        const uint64_t v = cs + key_q(atomic_load_explicit(&key[y], memory_order_relaxed));
+        const uint64_t v = cs + price(y);
         if (v < b1) {           /* strict: the lowest column wins ties */
             b2 = b1;
             b1 = v;
@@ -224,6 +242,13 @@ static void chain(int x, uint64_t *tv, int *ty, int32_t *tc, int *seen) {
                 break;
             }
         }
+        if (use_mirror) {     /* raise the mirror to the price the key now holds */
+            const uint64_t qnow = won ? nq : key_q(cur);
+            uint64_t mq = atomic_load_explicit(&mirror[w], memory_order_relaxed);
+            while (qnow > mq && !atomic_compare_exchange_weak_explicit(&mirror[w], &mq, qnow, memory_order_relaxed,
+                                                                       memory_order_relaxed)) {
+            }
+        }
         if (!won) continue;   /* a lower price got there first: rescan x */
         uint64_t pk = atomic_load_explicit(&qpeak, memory_order_relaxed);
         while (nq > pk && !atomic_compare_exchange_weak_explicit(&qpeak, &pk, nq, memory_order_relaxed,
@@ -271,19 +296,21 @@ int main(int argc, char **argv) {
     if (argc != 3) return 1;
     FILE *f = fopen(argv[1], "rb");
     if (!f) return 1;
-    int32_t hdr[5];
-    if (fread(hdr, sizeof(int32_t), 5, f) != 5) return 1;
+    int32_t hdr[6];
+    if (fread(hdr, sizeof(int32_t), 6, f) != 6) return 1;
     n = hdr[0];
     alpha = hdr[1];
     nthreads = hdr[2];
     lanes = hdr[3];
     per_lane = hdr[4];
+    use_mirror = hdr[5] != 0;
     if (n < 1 || n >= (int)NONE || alpha < 2 || nthreads < 1 || nthreads > 64) return 1;
     if (lanes < 0 || lanes > 64 || (lanes > 0 && (per_lane < 1 || per_lane > 16))) return 1;
     E = lanes * (lanes > 0 ? per_lane : 0);
     C = malloc(sizeof(int32_t) * (size_t)n * n);
     key = malloc(sizeof(*key) * (size_t)n);
-    if (!C || !key) return 2;
+    mirror = malloc(sizeof(*mirror) * (size_t)n);
+    if (!C || !key || !mirror) return 2;
     if (E > 0) {
         lcol = malloc(sizeof(int32_t) * (size_t)n * E);
         lcost = malloc(sizeof(int32_t) * (size_t)n * E);
@@ -302,7 +329,10 @@ int main(int argc, char **argv) {
     }
     const uint64_t Ct = ((uint64_t)n + 1) * (uint64_t)((int64_t)cmax - cmin);
     if (Ct >= (1ull << 40)) return 1;
-    for (int y = 0; y < n; ++y) atomic_init(&key[y], pack(0, NONE));
+    for (int y = 0; y < n; ++y) {
+        atomic_init(&key[y], pack(0, NONE));
+        atomic_init(&mirror[y], 0);
+    }
     pthread_barrier_init(&bar, NULL, (unsigned)nthreads + 1);
     pthread_t *th = malloc(sizeof(pthread_t) * (size_t)nthreads);
     if (!th) return 2;
@@ -321,6 +351,7 @@ int main(int argc, char **argv) {
         }
         for (int y = 0; y < n; ++y) atomic_store(&key[y], pack(key_q(atomic_load(&key[y])) - qmin, NONE));
         R_total += qmin;
+        for (int y = 0; y < n; ++y) atomic_store(&mirror[y], key_q(atomic_load(&key[y])));
         uint64_t S = 0;
         for (int y = 0; y < n; ++y) {
             const uint64_t q = key_q(atomic_load(&key[y]));

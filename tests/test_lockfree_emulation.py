@@ -4,7 +4,9 @@ ThreadSanitizer: no data race may be reported, every run must end, and the
 result must be the exact optimum (the oracle's Hungarian cost, a permutation
 of that cost, and eps-CS at eps = 1 with the final prices). The same holds
 with candidate lists, whose bound must stay sound across the price shifts
-between phases; two planted mistakes in the list rule must be seen. Every
+between phases (two planted mistakes in the list rule must be seen), and
+when scans read prices from a mirror that lags the keys, as the
+single-solve refine does. Every
 run also checks the price bounds that decide when the GPU may use 32-bit
 values (the emulation exits with status 3 if one breaks), and a sequential
 restatement shows that those bounds are reached. Nothing here touches a
@@ -43,12 +45,12 @@ def _build(tmp_path, tsan, mutant=0):
     return exe
 
 
-def _run(exe, C, alpha, threads, tmp_path, lanes=0, per_lane=0, timeout=120):
+def _run(exe, C, alpha, threads, tmp_path, lanes=0, per_lane=0, mirror=0, timeout=120):
     """Returns cost, phases, bids, match, prices, list scans, full scans."""
     n = C.shape[0]
     inp, out = tmp_path / "in.bin", tmp_path / "out.bin"
     with open(inp, "wb") as f:
-        np.array([n, alpha, threads, lanes, per_lane], dtype=np.int32).tofile(f)
+        np.array([n, alpha, threads, lanes, per_lane, mirror], dtype=np.int32).tofile(f)
         np.ascontiguousarray(C, dtype=np.int32).tofile(f)
     env = dict(os.environ, TSAN_OPTIONS="halt_on_error=1 exitcode=66")
     r = subprocess.run([exe, str(inp), str(out)], capture_output=True, text=True, timeout=timeout, env=env)
@@ -234,3 +236,22 @@ def test_price_bounds_are_reached():
             assert a <= 1.0 and b <= 1.0, (t, alpha, a, b)
             worst_in, worst_after = max(worst_in, a), max(worst_after, b)
     assert worst_in > 0.9 and worst_after == 1.0, (worst_in, worst_after)
+
+
+@pytest.mark.parametrize("lanes,per_lane", [(0, 0), (32, 4), (4, 2)])
+def test_price_mirror_is_race_free_and_exact(tmp_path, lanes, per_lane):
+    """Scans read prices from a mirror raised by an atomic maximum after each
+    commit attempt, so it can lag the key: stale prices are lower, and a bid
+    made from them still keeps its row eps-optimal."""
+    tsan = _build(tmp_path, tsan=True)
+    for C in (synth.uniform_costs(120, 0, 10**5, 6), synth.geometric_costs(96, 2),
+              np.random.default_rng(3).integers(0, 3, size=(65, 65)).astype(np.int32),
+              synth.uniform_costs(1, -5, 5, 4), synth.uniform_costs(2, 0, 9, 5)):
+        cost, phases, bids, match, prices, lists, full = _run(tsan, C, 10, 8, tmp_path, lanes, per_lane, 1)
+        _check(C, cost, match, prices)
+    plain = _build(tmp_path, tsan=False)
+    for threads, alpha in ((1, 10), (16, 4), (32, 64)):
+        for C in (synth.uniform_costs(200, 0, 10**5, 6), synth.geometric_costs(256, 7)):
+            cost, phases, bids, match, prices, lists, full = _run(plain, C, alpha, threads, tmp_path,
+                                                                  lanes, per_lane, 1)
+            _check(C, cost, match, prices)
