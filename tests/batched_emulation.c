@@ -25,7 +25,10 @@
  *   in:  int32 B, int32 S, int32 threads, int32 alpha, then B int32 sizes n_i,
  *        then the B row-major int32 matrices back to back
  *   out: B int64 costs, then the B matchings back to back (int32 per row)
- * Exit status 0 on success, 1 on a bad input, 2 on an internal error.
+ * Exit status 0 on success, 1 on a bad input, 2 on an internal error, 3
+ * when a price bound that the GPU's 32-bit keys rely on is broken: within a
+ * phase every q stays <= S + 2 C~ + 2 eps (S = the largest q after the
+ * phase's shift), and after it the spread max q - min q is <= C~ + eps.
  */
 #define _POSIX_C_SOURCE 200809L
 #include <pthread.h>
@@ -51,7 +54,8 @@ typedef struct {
     /* written by the transition owner before the claim word is republished;
        read only by threads that hold a valid claim */
     int n, phase, nph, cmin;
-    uint64_t eps;
+    uint64_t eps, Ct, S;
+    _Atomic uint64_t qpeak;     /* the largest q committed in this phase */
     const int32_t *C;
     _Atomic uint64_t key[MAXN];
 } Slot;
@@ -94,6 +98,9 @@ static void load_next(Slot *sl) {
             ++nph;
         } while (e > 1);
         for (int y = 0; y < n; ++y) atomic_store(&sl->key[y], pack(0, NONE));
+        sl->Ct = Ct;
+        sl->S = 0;
+        atomic_store(&sl->qpeak, 0);
         sl->n = n;
         sl->C = C;
         sl->cmin = cmin;
@@ -110,6 +117,15 @@ static void load_next(Slot *sl) {
 /* After the slot's last row was matched: the next phase, or the results and the next instance. */
 static void end_phase(Slot *sl) {
     const int n = sl->n;
+    {
+        uint64_t lo = UINT64_MAX, hi = 0;
+        for (int y = 0; y < n; ++y) {
+            const uint64_t q = key_q(atomic_load(&sl->key[y]));
+            if (q < lo) lo = q;
+            if (q > hi) hi = q;
+        }
+        if (atomic_load(&sl->qpeak) > sl->S + 2 * sl->Ct + 2 * sl->eps || hi - lo > sl->Ct + sl->eps) exit(3);
+    }
     if (sl->phase + 1 < sl->nph) {
         uint64_t m = UINT64_MAX;
         for (int y = 0; y < n; ++y) {
@@ -117,6 +133,13 @@ static void end_phase(Slot *sl) {
             if (q < m) m = q;
         }
         for (int y = 0; y < n; ++y) atomic_store(&sl->key[y], pack(key_q(atomic_load(&sl->key[y])) - m, NONE));
+        uint64_t S = 0;
+        for (int y = 0; y < n; ++y) {
+            const uint64_t q = key_q(atomic_load(&sl->key[y]));
+            if (q > S) S = q;
+        }
+        sl->S = S;
+        atomic_store(&sl->qpeak, S);
         sl->eps = sl->eps / (uint64_t)alpha > 1 ? sl->eps / (uint64_t)alpha : 1;
         sl->phase += 1;
         atomic_store(&sl->unmatched, n);
@@ -170,6 +193,10 @@ static int chain(Slot *sl, int x) {
             }
         }
         if (!won) continue;
+        uint64_t pk = atomic_load_explicit(&sl->qpeak, memory_order_relaxed);
+        while (nq > pk && !atomic_compare_exchange_weak_explicit(&sl->qpeak, &pk, nq, memory_order_relaxed,
+                                                                 memory_order_relaxed)) {
+        }
         const uint64_t m = key_mate(cur);
         if (m == NONE) return atomic_fetch_sub_explicit(&sl->unmatched, 1, memory_order_acq_rel) == 1;
         x = (int)m;

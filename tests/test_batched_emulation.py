@@ -2,7 +2,9 @@
 phase transitions, the shared instance queue), emulated by host threads with
 C11 atomics (tests/batched_emulation.c) and run under ThreadSanitizer: no data
 race may be reported, every run must end, and every instance's cost must be
-the oracle's optimum with a matching of that cost. Nothing here touches a GPU."""
+the oracle's optimum with a matching of that cost. Every phase of every slot
+also checks the price bounds behind the GPU's 32-bit keys (the emulation
+exits with status 3 if one breaks). Nothing here touches a GPU."""
 
 import os
 import shutil
