@@ -255,3 +255,19 @@ def test_price_mirror_is_race_free_and_exact(tmp_path, lanes, per_lane):
             cost, phases, bids, match, prices, lists, full = _run(plain, C, alpha, threads, tmp_path,
                                                                   lanes, per_lane, 1)
             _check(C, cost, match, prices)
+
+
+def test_deeper_lists_halve_the_full_scans(tmp_path):
+    """Why 4 entries per lane: each doubling of the entries a lane keeps
+    about halves the share of bids that must scan the full row (the bound
+    theta rises to a higher order statistic of the lane's values). One
+    thread makes the counts deterministic."""
+    exe = _build(tmp_path, tsan=False)
+    C = synth.uniform_costs(1024, 0, (1 << 20) - 1, 1)
+    share = []
+    for per_lane in (2, 4, 8):
+        cost, phases, bids, match, prices, lists, full = _run(exe, C, 10, 1, tmp_path, 32, per_lane)
+        _check(C, cost, match, prices)
+        share.append(full / (lists + full))
+    assert share[0] > 0.3
+    assert share[1] < 0.6 * share[0] and share[2] < 0.6 * share[1], share
