@@ -178,7 +178,10 @@ typedef struct {
 } la_stats;
 
 /*
- * la_solve -- exact minimum-cost perfect matching of a dense n x n matrix.
+ * la_solve -- exact minimum-cost perfect matching of a dense n x n matrix:
+ * the assignment problem of Sect. 2 (as minimisation, see above), solved by
+ * the cost scaling of Sect. 5.1 (Algorithm 5.0's eps loop, Algorithm 5.2's
+ * initialisation) with the lock-free refine of Sect. 5.3 (Algorithm 5.4).
  *   cost      device const int32[n*n], row-major, read only.
  *   n         0 <= n <= LA_MAX_N. n = 0 writes *cost_out = 0.
  *   stream    cudaStream_t as void*.
