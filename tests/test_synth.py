@@ -77,3 +77,22 @@ def test_torch_twin_of_the_uniform_generator_is_bit_identical():
         a = synth.uniform_costs(n, lo, hi, seed)
         b = synth.uniform_costs_torch(n, lo, hi, seed, device="cpu").numpy()
         assert a.dtype == b.dtype and np.array_equal(a, b), (n, lo, hi, seed)
+
+
+def test_geometric_instances_have_their_planted_structure():
+    """The geometric recipe plants a permutation: b_j is a_pi(j) moved by
+    N(0, 0.01^2) per coordinate, so the optimum pairs most rows with their
+    planted partner while the points are sparse next to the jitter, and
+    fewer as they crowd (the mean spacing is about 1/sqrt(n)). A generator
+    that lost the pairing would match almost none."""
+    import oracle
+    rates = []
+    for n, seed in ((256, 1), (512, 2)):
+        a, pi, b = synth.geometric_points(n, seed)
+        C = synth.geometric_costs(n, seed)
+        planted = np.empty(n, dtype=np.int64)
+        planted[pi] = np.arange(n)
+        cost, match, _, _ = oracle.hungarian(C)
+        assert cost <= int(C[np.arange(n), planted].sum())
+        rates.append(float((match == planted).mean()))
+    assert rates[0] > 0.85 and rates[1] > 0.75 and rates[1] < rates[0], rates
