@@ -3,7 +3,7 @@
  *
  * Problem. Given an n x n int32 cost matrix C (row x = left vertex of X,
  * column y = right vertex of Y of a complete bipartite graph), find a perfect
- * matching M that minimises sum_x C[x][M(x)] (Sect. 2 of the paper defines
+ * matching M that minimises sum_x C[x][M(x)] (Sect. 3 of the paper defines
  * matchings, perfect matchings and the assignment problem; Sect. 5 reduces the
  * assignment problem to a min-cost flow with u(x,y) = 1, c(x,y) = w(x,y), and
  * this library solves that minimisation; a maximising caller passes
@@ -43,7 +43,7 @@ extern "C" {
 
 typedef enum {
     LA_OK = 0,
-    LA_ERR_INVALID = 1,     /* bad argument (n < 0, NULL pointer, n too large) */
+    LA_ERR_INVALID = 1,     /* bad argument (n < 0, NULL pointer, n > LA_MAX_N) */
     LA_ERR_CUDA = 2,        /* a CUDA runtime call failed */
     LA_ERR_OVERFLOW = 3,    /* cost range too large for the exact integer
                                price field: (n+1)(max C - min C) >= 2^40 */
@@ -179,7 +179,7 @@ typedef struct {
 
 /*
  * la_solve -- exact minimum-cost perfect matching of a dense n x n matrix:
- * the assignment problem of Sect. 2 (as minimisation, see above), solved by
+ * the assignment problem of Sect. 3 (as minimisation, see above), solved by
  * the cost scaling of Sect. 5.1 (Algorithm 5.0's eps loop, Algorithm 5.2's
  * initialisation) with the lock-free refine of Sect. 5.3 (Algorithm 5.4).
  *   cost      device const int32[n*n], row-major, read only.
@@ -299,7 +299,7 @@ la_status la_solve_batched_ex(const int32_t *cost, const int64_t *offsets, const
  * u(x) + v(y) <= C[x][y] everywhere, equality holds on M and
  * sum u + sum v = cost(M), which proves M optimal (LP duality). These are
  * the paper's prices at eps = 0 (c_p(x,y) = c(x,y) + p(x) - p(y) >= 0 with
- * p(y) = v(y), p(x) = -u(x); Sect. 2, eps-optimality).
+ * p(y) = v(y), p(x) = -u(x); Sect. 3, eps-optimality).
  * Returns LA_ERR_INVALID if M is not a permutation and LA_ERR_INTERNAL if
  * M is not optimal (no such duals exist). Blocks until done.
  */
@@ -465,15 +465,28 @@ la_status la_maxflow_grid_ex(const int32_t *cap, const int32_t *src, const int32
  * latency and implicit device synchronisation of an allocation, or a
  * certified system that forbids dynamic allocation after start-up.
  *
- * Same arguments, results and blocking behaviour as la_solve, with the
- * default options (alpha = 10, eps0 = C~, prices from 0). Instead of the
- * per-device workspace it uses one fixed scratch array that the library
- * declares in device memory (LA_NOALLOC_SCRATCH_BYTES, about 257 KB); every
- * GPU that loads the library holds that array until the process exits. It
- * calls no cudaMalloc, cudaFree or other allocating routine.
+ * Same arguments, exact optimal cost and blocking behaviour as la_solve
+ * (every call returns only once its result is in place), but not the same
+ * configuration: it runs the refine without candidate lists and without the
+ * one-CTA tail kernel, so every bid reads its whole cost row (a full row
+ * scan) in every phase, at alpha = 10 from zero prices. That is la_solve_ex
+ * with LA_FLAG_NO_CANDIDATE_LISTS and tail_threshold = -1; its speed, and the
+ * default scan budget at which it returns LA_ERR_ITER_LIMIT, are that
+ * configuration's. Instead of the per-device workspace it uses one fixed
+ * scratch array that the library declares in device memory: 16 bytes per
+ * column for LA_NOALLOC_MAX_N columns (the column keys and the price mirror)
+ * plus a control block, about 257 KB in all. Every GPU that loads the
+ * library holds that array until the process exits. The call makes no
+ * cudaMalloc, cudaFree or other allocating call.
  *   - n must be <= LA_NOALLOC_MAX_N; larger n returns LA_ERR_TOO_LARGE with
  *     nothing enqueued.
- *   - The first call on a device looks up the array's device address
+ *   - CUDA loads the array, and each kernel, on a device when they are first
+ *     used there (lazy module loading), which takes a little device memory
+ *     once. A caller whose device memory will later be claimed in full by
+ *     another allocator should therefore make a first call at start-up, on
+ *     an instance of the kind it will solve, or run with
+ *     CUDA_MODULE_LOADING=EAGER.
+ *   - The first call on a device also looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current) and caches it; make
  *     that first call before any stream capture on that device.
  *   - All calls on a device share the one array, which keeps the last

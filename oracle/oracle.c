@@ -6,7 +6,7 @@
  * baseline legs of bench.py load this library. The CUDA product path shares
  * no code, header, table or helper with it and never calls it.
  *
- * Problem (Sect. 2, definitions of matching, perfect matching, assignment and
+ * Problem (Sect. 3, definitions of matching, perfect matching, assignment and
  * cost; Sect. 5, reduction of the assignment problem to min-cost flow with
  * u(x,y)=1, c(x,y)=w(x,y)): given an n x n integer matrix C (row x = left
  * vertex, column y = right vertex), find a perfect matching M minimising

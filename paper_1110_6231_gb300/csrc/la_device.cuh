@@ -1,7 +1,7 @@
 // Device-side building blocks of the refine: the packed column key, the
 // row scan (best / second-best part-reduced cost) and the warp reduction.
 //
-// Notation (Sect. 2 and Sect. 5 of the paper): rows x in X, columns y in Y,
+// Notation (Sect. 3 and Sect. 5 of the paper): rows x in X, columns y in Y,
 // scaled cost c~(x,y) = (n+1) C[x][y]. Column prices p(y) are kept as
 // q(y) = -p(y) >= 0 after a per-phase shift (a uniform shift of all prices
 // leaves every reduced cost c_p(x,y) = c(x,y) + p(x) - p(y) unchanged).

@@ -13,7 +13,7 @@ transcendental function the generators need (``log``, ``exp``, ``cos``,
 and ``sqrt`` only, one numpy ufunc per operation (no fused multiply-add), so
 the same seed gives the same matrix bit for bit on x86-64 and on AArch64.
 
-Workload shapes follow the paper's problem statement (Sect. 2 and Sect. 5:
+Workload shapes follow the paper's problem statement (Sect. 3 and Sect. 5:
 complete bipartite graphs ``|X| = |Y| = n`` with integer edge costs) and its
 motivating application, optical flow by assignment (Sect. 1):
 

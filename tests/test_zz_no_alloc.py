@@ -47,7 +47,8 @@ def test_noalloc_matches_la_solve_on_two_calls_in_a_row(la):
     import torch
     instances = [synth.uniform_costs(512, 0, 1000, 21),       # 32-bit path, 128-bit loads
                  synth.geometric_costs(301, 22),              # ragged n: scalar loads
-                 synth.uniform_costs(1024, 0, (1 << 20) - 1, 23)]  # 64-bit path
+                 synth.uniform_costs(1024, 0, (1 << 20) - 1, 23),  # 64-bit path
+                 synth.geometric_costs(4096, 24)]             # full row scans in every phase at n = 4096
     # load the module and its kernels through la_solve first, then measure
     rc, ref0, _ = _run(la, la.la_solve, instances[0])
     assert rc == la.LA_OK
@@ -64,6 +65,34 @@ def test_noalloc_matches_la_solve_on_two_calls_in_a_row(la):
         for m in (m1, m2, ref_match):
             assert oracle.check_matching(C, m, ref) == 0
     assert torch.cuda.mem_get_info()[0] <= free0
+
+
+def test_noalloc_as_the_first_call_in_a_fresh_process(la):
+    """A caller that cannot allocate may make this its very first call:
+    the library, its kernels and the fixed array are then loaded by it."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys, numpy as np, torch\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "import oracle\n"
+        "import paper_1110_6231_gb300 as la\n"
+        "from paper_1110_6231_gb300 import synth\n"
+        "C = synth.uniform_costs(200, 0, 1000, 31)\n"
+        "t = torch.from_numpy(C).cuda()\n"
+        "m = torch.full((200,), -1, dtype=torch.int32, device='cuda')\n"
+        "c = torch.zeros(1, dtype=torch.int64, device='cuda')\n"
+        "rcs = [la.la_solve_noalloc(t, 200, None, m, c) for _ in range(2)]\n"
+        "torch.cuda.synchronize()\n"
+        "want = oracle.hungarian(C)[0]\n"
+        "assert rcs == [la.LA_OK, la.LA_OK], rcs\n"
+        "assert int(c.item()) == want, (int(c.item()), want)\n"
+        "assert oracle.check_matching(C, m.cpu().numpy(), want) == 0\n"
+        "print('fresh ok')\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "fresh ok" in r.stdout, r.stdout[-2000:] + r.stderr[-2000:]
 
 
 def test_noalloc_small_and_degenerate_sizes(la):
