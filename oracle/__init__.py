@@ -12,6 +12,8 @@ builds it with gcc on first use and marshals numpy arrays. Functions:
 * ``brute_force(C)``      -- min over all n! permutations (n <= 10).
 * ``hungarian(C)``        -- shortest-augmenting-path Hungarian method with
   integer duals ``u, v`` (Kuhn 1955 / Munkres 1957; not from the paper).
+* ``cost_scaling_arcfix(C, ...)`` -- the same with the arc fixing of Sect.
+  5.2 (arcs whose reduced cost exceeds 2 n eps after a phase are deleted).
 * ``cost_scaling(C, ...)`` -- the paper's sequential cost scaling: Algorithm
   5.0's epsilon loop, Algorithm 5.2's refine initialisation and Algorithm 5.4's
   push/relabel taken as the Goldberg-Kennedy double push, on costs scaled by
@@ -70,6 +72,7 @@ def _load():
             lib.or_brute_force.argtypes = [P, i32, P, P]
             lib.or_hungarian.argtypes = [P, i32, P, P, P, P]
             lib.or_cost_scaling.argtypes = [P, i32, i32, i64, P, i64, i32, P, P, P, P]
+            lib.or_cost_scaling_arcfix.argtypes = [P, i32, i32, i64, P, P, P, P, P, P]
             lib.or_check_matching.argtypes = [P, i32, P, i64]
             lib.or_check_duals.argtypes = [P, i32, P, P, P]
             lib.or_check_eps_cs.argtypes = [P, i32, P, P, i64]
@@ -153,6 +156,29 @@ def cost_scaling(C, alpha: int = 10, eps0: int = 0, init_prices=None,
     st = dict(phases=int(stats[0]), scans=int(stats[1]), displaced=int(stats[2]),
               eps_first=int(stats[3]))
     return int(cost[0]), match, prices, st
+
+
+def cost_scaling_arcfix(C, alpha: int = 10, eps0: int = 0, init_prices=None):
+    """Sequential cost scaling with the arc fixing of Sect. 5.2: after every
+    phase but the last, arcs with reduced cost above 2 n eps are deleted.
+    Returns ``(cost, match, prices, fixed, stats)``; ``fixed`` is an n x n
+    bool array of the deleted arcs, ``stats`` adds ``deleted`` to the keys of
+    ``cost_scaling``'s."""
+    C = _costs(C)
+    n = C.shape[0]
+    match = np.zeros(n, dtype=np.int32)
+    cost = np.zeros(1, dtype=np.int64)
+    prices = np.zeros(n, dtype=np.int64)
+    fixed = np.zeros((n, n), dtype=np.uint8)
+    stats = np.zeros(5, dtype=np.int64)
+    ip = None if init_prices is None else np.ascontiguousarray(init_prices, dtype=np.int64)
+    rc = _load().or_cost_scaling_arcfix(_ptr(C), n, int(alpha), int(eps0), _ptr(ip), _ptr(match),
+                                        _ptr(cost), _ptr(prices), _ptr(fixed), _ptr(stats))
+    if rc:
+        raise OracleError(f"or_cost_scaling_arcfix returned {rc}")
+    st = dict(phases=int(stats[0]), scans=int(stats[1]), displaced=int(stats[2]),
+              eps_first=int(stats[3]), deleted=int(stats[4]))
+    return int(cost[0]), match, prices, fixed.astype(bool), st
 
 
 def check_matching(C, match, claimed_cost) -> int:

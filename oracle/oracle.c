@@ -26,6 +26,9 @@
  *                     of Algorithm 5.2 (unmatch all, p(x) implicit), and the
  *                     push/relabel step of Algorithm 5.4 taken as the
  *                     Goldberg-Kennedy double push (the paper's reference [9]).
+ *   or_cost_scaling_arcfix - the same, with Sect. 5.2's arc fixing: after
+ *                     every phase but the last, arcs whose reduced cost
+ *                     exceeds 2 n eps are deleted for good.
  * and certificate checkers for any claimed matching, among them
  * or_certify_optimal, which proves a matching optimal at any size with no
  * duals given (Klein's negative-cycle criterion). The same problem on
@@ -275,6 +278,135 @@ int or_cost_scaling(const int32_t *C, int32_t n, int32_t alpha, int64_t eps0,
 done:
     if (stats) { stats[0] = phases; stats[1] = scans; stats[2] = displaced; stats[3] = eps_first; }
     free(p); free(p_start); free(holder); free(col); free(queue);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sequential cost scaling with arc fixing (Sect. 5.2, the arc          */
+/* heuristic taken from the paper's reference [8]).                     */
+/*                                                                     */
+/* The same loop as or_cost_scaling (Alg. 5.0, Alg. 5.2, Alg. 5.4 as a  */
+/* double push), on a graph that loses arcs. When a phase other than   */
+/* the last has ended, f is an eps-optimal flow: a perfect matching,    */
+/* every row x eps-optimal with respect to the column prices p and the  */
+/* row price of Alg. 5.2, p(x) = -min over x's remaining arcs of        */
+/* (c'_p(x,y) + eps). Sect. 5.2: an arc whose reduced cost             */
+/* c_p(x,y) = c~(x,y) + p(x) - p(y) exceeds 2 n eps keeps its flow in   */
+/* every later phase, so it is deleted for good. Later phases scan only */
+/* the remaining arcs of a row. A row left with one arc has no second   */
+/* best; its bid lowers the column's price by eps.                      */
+/*                                                                     */
+/* Why no optimal assignment loses an arc (the reading the paper does  */
+/* not spell out): an optimal assignment M* that used a deleted arc a   */
+/* would differ from f on an alternating cycle through a with k <= n    */
+/* rows. Taken along f's residual arcs, the cycle costs at least        */
+/* c_p(a) - (k-1) eps (prices cancel around a cycle; f's other          */
+/* unmatched arcs have c_p >= -eps and its reversed matched arcs        */
+/* c_p >= 0). Taken the other way it is a cycle of M*'s residual graph, */
+/* which has no negative cycle, so the first direction costs <= 0.      */
+/* Hence c_p(a) <= (k-1) eps < 2 n eps. (An eps-optimal M* in place of  */
+/* the optimum gives c_p(a) <= (2k-1) eps, the paper's 2 n eps bound.)  */
+/*                                                                     */
+/* Arguments as or_cost_scaling (no check mode). fixed_out (optional,  */
+/* n*n bytes) gets 1 for every deleted arc. stats (optional, 5         */
+/* entries): phases, row scans, displacements, eps of the first phase, */
+/* arcs deleted.                                                       */
+/* ------------------------------------------------------------------ */
+int or_cost_scaling_arcfix(const int32_t *C, int32_t n, int32_t alpha, int64_t eps0,
+                           const int64_t *init_prices, int32_t *match, int64_t *cost,
+                           int64_t *prices_out, uint8_t *fixed_out, int64_t *stats)
+{
+    if (n < 0 || alpha < 2 || (n > 0 && (!C || !match)) || !cost) return OR_INVALID;
+    if (stats) for (int k = 0; k < 5; ++k) stats[k] = 0;
+    if (n == 0) { *cost = 0; return OR_OK; }
+    const int64_t np1 = (int64_t)n + 1;
+    int32_t cmin = C[0], cmax = C[0];
+    for (int64_t k = 0; k < (int64_t)n * n; ++k) {
+        if (C[k] < cmin) cmin = C[k];
+        if (C[k] > cmax) cmax = C[k];
+    }
+    int64_t eps = eps0 > 0 ? eps0 : np1 * ((int64_t)cmax - (int64_t)cmin);
+
+    int64_t *p = malloc(sizeof(int64_t) * n);
+    int32_t *holder = malloc(sizeof(int32_t) * n);
+    int32_t *col = malloc(sizeof(int32_t) * n);
+    int32_t *queue = malloc(sizeof(int32_t) * n);
+    uint8_t *gone = calloc((size_t)n * n, 1);         /* 1: arc deleted */
+    if (!p || !holder || !col || !queue || !gone) {
+        free(p); free(holder); free(col); free(queue); free(gone);
+        return OR_NOMEM;
+    }
+    for (int32_t y = 0; y < n; ++y) p[y] = init_prices ? init_prices[y] : 0;
+
+    int rc = OR_OK;
+    int64_t phases = 0, scans = 0, displaced = 0, eps_first = 0, deleted = 0;
+    for (;;) {
+        eps = eps / alpha;
+        if (eps < 1) eps = 1;
+        if (phases == 0) eps_first = eps;
+        for (int32_t y = 0; y < n; ++y) holder[y] = -1;
+        for (int32_t x = 0; x < n; ++x) { col[x] = -1; queue[x] = x; }
+        int64_t head = 0, tail = n;
+        while (head != tail) {
+            const int32_t x = queue[head % n];
+            head++;
+            const int32_t *row = C + (int64_t)x * n;
+            const uint8_t *dead = gone + (int64_t)x * n;
+            int64_t best = OR_INF, second = OR_INF;
+            int32_t w = -1;
+            for (int32_t y = 0; y < n; ++y) {
+                if (dead[y]) continue;
+                const int64_t cp = np1 * (int64_t)row[y] - p[y];   /* c'_p(x,y) */
+                if (cp < best) { second = best; best = cp; w = y; }
+                else if (cp < second) second = cp;
+            }
+            if (w < 0) { rc = OR_INVARIANT; goto done; }      /* a row lost every arc */
+            if (second == OR_INF) second = best;               /* one arc left */
+            scans++;
+            p[w] -= (second - best) + eps;
+            if (p[w] < -(INT64_MAX / 8)) { rc = OR_OVERFLOW; goto done; }
+            const int32_t old = holder[w];
+            holder[w] = x;
+            col[x] = w;
+            if (old >= 0) {
+                col[old] = -1;
+                queue[tail % n] = old;
+                tail++;
+                displaced++;
+            }
+        }
+        phases++;
+        if (eps <= 1) break;
+        /* arc fixing on the eps-optimal flow this phase produced */
+        for (int32_t x = 0; x < n; ++x) {
+            const int32_t *row = C + (int64_t)x * n;
+            uint8_t *dead = gone + (int64_t)x * n;
+            int64_t mn = OR_INF;
+            for (int32_t y = 0; y < n; ++y)
+                if (!dead[y] && np1 * (int64_t)row[y] - p[y] < mn) mn = np1 * (int64_t)row[y] - p[y];
+            const int64_t px = -(mn + eps);                    /* Alg. 5.2's row price */
+            for (int32_t y = 0; y < n; ++y) {
+                if (dead[y]) continue;
+                const int64_t cp = np1 * (int64_t)row[y] + px - p[y];   /* c_p(x,y) */
+                if (cp > 2 * (int64_t)n * eps) { dead[y] = 1; deleted++; }
+            }
+        }
+    }
+    {
+        int64_t total = 0;
+        for (int32_t x = 0; x < n; ++x) {
+            match[x] = col[x];
+            total += C[(int64_t)x * n + col[x]];
+        }
+        *cost = total;
+        if (prices_out) memcpy(prices_out, p, sizeof(int64_t) * n);
+        if (fixed_out) memcpy(fixed_out, gone, (size_t)n * n);
+    }
+done:
+    if (stats) {
+        stats[0] = phases; stats[1] = scans; stats[2] = displaced; stats[3] = eps_first; stats[4] = deleted;
+    }
+    free(p); free(holder); free(col); free(queue); free(gone);
     return rc;
 }
 

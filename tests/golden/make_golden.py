@@ -3,7 +3,7 @@ instances, computed only by the oracle's Hungarian method (with its dual
 certificate checked), plus SHA-256 digests of the generated int32 matrices
 so that a platform whose generator drifted is caught before any parity claim.
 
-Run: python tests/golden/make_golden.py   (about a minute on one core)
+Run: python tests/golden/make_golden.py   (about two minutes on one core)
 """
 
 import hashlib
@@ -22,6 +22,7 @@ CASES = (
     [("uniform-n256-c1000", s, None) for s in range(100)]
     + [("uniform-n4096-c2^20", s, None) for s in range(10)]
     + [("geometric-n8192", s, 1024) for s in range(4)]
+    + [("geometric-n8192", s, None) for s in range(8)]    # the full n = 8192 workload
 )
 
 

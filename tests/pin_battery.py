@@ -69,6 +69,31 @@ def run_all_pins(orc):
             assert st["phases"] == len(orc.eps_schedule(Ct))
 
 
+def run_arcfix_pins(orc):
+    """Arc fixing (Sect. 5.2): the optimum with fixing equals enumeration,
+    and no optimal permutation uses a deleted arc."""
+    from paper_1110_6231_gb300 import synth
+    rng = np.random.default_rng(41)
+    for t in range(160):
+        n = int(rng.integers(2, 8))
+        lo, hi = [(0, 4), (0, 30), (-50, 50), (0, 1000)][t % 4]
+        C = rng.integers(lo, hi, size=(n, n)).astype(np.int32)
+        best, opt = None, []
+        for p in itertools.permutations(range(n)):
+            s = sum(int(C[x, p[x]]) for x in range(n))
+            if best is None or s < best:
+                best, opt = s, [p]
+            elif s == best:
+                opt.append(p)
+        c, m, _, fixed, _ = orc.cost_scaling_arcfix(C, alpha=[2, 3, 4, 10][(t // 4) % 4])
+        assert c == best
+        for p in opt:
+            assert not fixed[np.arange(n), np.array(p)].any()
+    for seed in range(2):
+        for C in (synth.uniform_costs(120, 0, 1000, seed), synth.geometric_costs(120, seed)):
+            assert orc.cost_scaling_arcfix(C)[0] == orc.hungarian(C)[0]
+
+
 def run_certify_pins(orc):
     """The negative-cycle certificate against enumeration: over every
     permutation of small matrices (heavy ties included) it accepts exactly
@@ -189,6 +214,7 @@ def main(argv):
         orc._LIB = os.path.join(tmp, "liboracle.so")
     try:
         run_all_pins(orc)
+        run_arcfix_pins(orc)
         run_certify_pins(orc)
         run_sparse_pins(orc)
         run_maxflow_pins(orc)

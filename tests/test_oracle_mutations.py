@@ -55,6 +55,15 @@ MUTANTS = [
      "for (int32_t sweep = 0; changed && sweep < 1; ++sweep) {"),
     ("certify-dual-from-own-row", "if (u_out) u_out[x] = (int64_t)C[(int64_t)x * n + match[x]] - d[match[x]];",
      "if (u_out) u_out[x] = (int64_t)C[(int64_t)x * n + x] - d[match[x]];"),
+    ("arcfix-threshold-zero", "if (cp > 2 * (int64_t)n * eps) { dead[y] = 1; deleted++; }",
+     "if (cp > 0) { dead[y] = 1; deleted++; }"),
+    ("arcfix-threshold-eps", "if (cp > 2 * (int64_t)n * eps) { dead[y] = 1; deleted++; }",
+     "if (cp > eps) { dead[y] = 1; deleted++; }"),
+    ("arcfix-next-phase-eps", "if (cp > 2 * (int64_t)n * eps) { dead[y] = 1; deleted++; }",
+     "if (cp > 2 * (int64_t)n * (eps / alpha)) { dead[y] = 1; deleted++; }"),
+    ("arcfix-no-row-price", "const int64_t cp = np1 * (int64_t)row[y] + px - p[y];   /* c_p(x,y) */",
+     "const int64_t cp = np1 * (int64_t)row[y] - p[y];"),
+    ("arcfix-row-price-sign", "const int64_t px = -(mn + eps);", "const int64_t px = (mn + eps);"),
     ("sparse-brute-force-ignores-arcs", "s = w[x][perm[x]] >= OR_INF ? OR_INF : s + w[x][perm[x]];",
      "s = w[x][perm[x]] >= OR_INF ? s : s + w[x][perm[x]];"),
 ]
@@ -84,5 +93,5 @@ def test_pins_catch_planted_mistake(name, old, new, tmp_path):
                             "int64_t red = (int64_t)row[(int64_t)j * n] - u[i] - v[j];")
     mutant = tmp_path / "oracle.c"
     mutant.write_text(text.replace(old, new, 1))
-    rc = _run_battery(str(mutant), tmp_path, timeout=15)
+    rc = _run_battery(str(mutant), tmp_path, timeout=30)
     assert rc != 0, f"planted mistake {name} was not caught"
