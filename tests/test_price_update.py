@@ -1,6 +1,7 @@
-"""The global price update (Sect. 5.2, Algorithm 5.3), restated on the CPU
-to pin two readings the GPU kernel rests on. Nothing here touches a GPU or
-shares code with the CUDA path.
+"""The global price update (Sect. 5.2, Algorithm 5.3): the oracle's Dial
+bucket restatement (``oracle/price_update.py``) pinned, and the GPU's form
+restated beside it, to pin the readings the GPU kernel rests on. Nothing
+here touches a GPU or shares code with the CUDA path.
 
 State: inside a refine phase at scale eps, with column values
 v(x, y) = (n + 1)(C[x][y] - min C) + q(y) (q = -p), a partial matching in
@@ -35,75 +36,8 @@ import random
 import numpy as np
 import pytest
 
-INF = 1 << 62
-
-
-def _mid_phase_state(C, alpha, rng):
-    """Sequential cost scaling (double pushes, the free row drawn at random)
-    stopped after a random number of bids inside a random phase. Returns
-    (scaled costs, q, holder of each column, free rows, eps) or None if the
-    chosen phase ended first."""
-    n = C.shape[0]
-    cmin = int(C.min())
-    Ct = (n + 1) * (int(C.max()) - cmin)
-    cs = [[(int(C[x, y]) - cmin) * (n + 1) for y in range(n)] for x in range(n)]
-    sched, e = [], Ct
-    while True:
-        e = max(1, e // alpha)
-        sched.append(e)
-        if e == 1:
-            break
-    stop_phase = rng.randrange(len(sched))
-    q = [0] * n
-    for ph, e in enumerate(sched):
-        m = min(q)
-        q = [v - m for v in q]
-        holder = [-1] * n
-        free = list(range(n))
-        stop_after = rng.randrange(1, 4 * n) if ph == stop_phase else None
-        bids = 0
-        while free:
-            if stop_after is not None and bids >= stop_after:
-                return cs, q, holder, free, e
-            x = free.pop(rng.randrange(len(free)))
-            b1 = b2 = w = None
-            for y in range(n):
-                v = cs[x][y] + q[y]
-                if b1 is None or v < b1:
-                    b2, b1, w = b1, v, y
-                elif b2 is None or v < b2:
-                    b2 = v
-            if b2 is None:
-                b2 = b1
-            q[w] += (b2 - b1) + e
-            if holder[w] >= 0:
-                free.append(holder[w])
-            holder[w] = x
-            bids += 1
-    return None
-
-
-def _eps_optimal(cs, q, holder, e):
-    n = len(q)
-    for w in range(n):
-        x = holder[w]
-        if x >= 0 and any(cs[x][w] + q[w] > cs[x][y] + q[y] + e for y in range(n)):
-            return False
-    return True
-
-
-def _arc_length(cs, q, holder, e):
-    n = len(q)
-    row_col = {holder[w]: w for w in range(n) if holder[w] >= 0}
-
-    def length(x, y):
-        if x in row_col:
-            w = row_col[x]
-            return (cs[x][y] + q[y] + e - (cs[x][w] + q[w])) // e
-        best = min(cs[x][z] + q[z] for z in range(n))
-        return (cs[x][y] + q[y] - best) // e
-
-    return row_col, length
+from oracle.price_update import INF, arc_length as _arc_length, dial_labels as _labels_buckets, \
+    eps_optimal as _eps_optimal, mid_phase_state as _mid_phase_state
 
 
 def _labels_bellman_ford(cs, q, holder, free, e):
@@ -120,45 +54,6 @@ def _labels_bellman_ford(cs, q, holder, free, e):
             break
     K = max(min(lab[y] + length(x, y) for y in range(n)) for x in free) + 1
     return [min(v, K) for v in lab]
-
-
-def _labels_buckets(cs, q, holder, free, e, finish_bucket=True):
-    n = len(q)
-    row_col, length = _arc_length(cs, q, holder, e)
-    lab = {("col", y): 0 for y in range(n) if holder[y] < 0}
-    buckets = {}
-    for node in lab:
-        buckets.setdefault(0, []).append(node)
-    scanned, waiting = set(), set(free)
-    last = i = None
-    while buckets:
-        i = min(buckets)
-        if last is not None and i > last:
-            break
-        node = buckets[i].pop()
-        if not buckets[i]:
-            del buckets[i]
-        if node in scanned or lab[node] != i:
-            continue
-        scanned.add(node)
-        if node[0] == "row":
-            waiting.discard(node[1])
-            if not waiting:
-                last = i
-                if not finish_bucket:
-                    break
-            continue
-        y = node[1]
-        for x in range(n):
-            if row_col.get(x) == y:
-                continue
-            target = ("col", row_col[x]) if x in row_col else ("row", x)
-            d = i + length(x, y)
-            if target not in scanned and d < lab.get(target, INF):
-                lab[target] = d
-                buckets.setdefault(d, []).append(target)
-    K = (last if last is not None else i) + 1
-    return [lab[("col", y)] if ("col", y) in scanned else K for y in range(n)]
 
 
 def _states(count, seed):
