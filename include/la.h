@@ -125,6 +125,20 @@ typedef struct {
    rose during the phase (Lemma 5.2). Violations are counted in
    la_stats.check_violations and make the solve return LA_ERR_INTERNAL. */
 #define LA_FLAG_CHECK_PHASES 2
+/* la_options.flags: no arc fixing. By default, after every phase but the
+   last, arc fixing (Sect. 5.2) drops every arc (x,y) whose reduced cost
+   c_p(x,y) = c~(x,y) + p(x) - p(y), with the row price of Algorithm 5.2,
+   exceeds 2 n eps: such an arc keeps its zero flow in every later phase, so
+   no optimal assignment uses it (an alternating cycle through it would
+   have negative cost in the optimum's residual graph). A row whose
+   remaining arcs fit in its candidate list (128 columns) keeps only those
+   and is never scanned in full again. The optimal cost is unchanged; the
+   final prices certify optimality only over the arcs kept, so arc fixing
+   is off whenever prices_out is requested, and with a phase cutoff (whose
+   intermediate phases do not end with an eps-optimal flow). With
+   LA_FLAG_CHECK_PHASES the eps-CS check of a fixed row covers its kept
+   arcs. */
+#define LA_FLAG_NO_ARC_FIXING 4
 
 /* Phases whose counters la_stats records one by one. */
 #define LA_STATS_PHASES 32
@@ -175,6 +189,23 @@ typedef struct {
        phase that did not finish; any start prices give the exact optimum. */
     int32_t stop_phase;
     int64_t stop_eps;
+    /* Per phase (profile != 0 for the times): the one-CTA tail kernel's
+       share of phase_ms, and the phase's full row scans and tail scans. */
+    double phase_tail_ms[LA_STATS_PHASES];
+    int64_t phase_full_scans[LA_STATS_PHASES];
+    int64_t phase_tail_scans[LA_STATS_PHASES];
+    /* Arc fixing (Sect. 5.2; see LA_FLAG_NO_ARC_FIXING): rows whose arcs
+       were cut down to their candidate list after each phase, and after the
+       last fixing pass those rows and the arcs they keep. */
+    int64_t phase_fixed_rows[LA_STATS_PHASES];
+    int64_t fixed_rows;
+    int64_t fixed_arcs;
+    /* The bulk sweep that opens every phase (each row's first bid, all rows
+       in flight; the displacement chains run in the launches after it): its
+       summed time (profile != 0), row scans and full row scans. */
+    double sweep_ms;
+    int64_t sweep_scans;
+    int64_t sweep_full_scans;
 } la_stats;
 
 /*
@@ -203,6 +234,35 @@ const char *la_status_string(la_status s);
 
 /* Frees the calling device's workspace (the next solve reallocates it). */
 la_status la_release_workspace(void);
+
+/*
+ * la_debug_price_update -- one global price update (Sect. 5.2, Algorithm
+ * 5.3) on a mid-phase state given by the caller: a test hook for the update
+ * the refine runs with la_options.price_updates, through the same kernel.
+ * The state is a phase at scale eps: column prices, a partial matching in
+ * which every matched row x is eps-optimal in the version-2 sense of Sect.
+ * 5.1 ((n+1)C[x][M(x)] - p(M(x)) <= min_y ((n+1)C[x][y] - p(y)) + eps), and
+ * the free rows.
+ *   cost        device const int32[n*n], row-major; 2 <= n <= LA_MAX_N.
+ *   prices      device const int64[n]: p(y), the paper's sign, units of
+ *               (n+1) C.
+ *   row_match   device const int32[n]: the column of row x, or -1 if x is
+ *               free; no column may appear twice (else LA_ERR_INVALID).
+ *   eps         the phase's eps, >= 1.
+ *   labels_out  device int32[n]: each column's label, its distance in
+ *               units of eps to the nearest free column over the residual
+ *               graph, truncated at one more than the largest label of a
+ *               free row (Algorithm 5.3's last + 1), as applied.
+ *   prices_out  device int64[n]: p(y) - eps * label(y).
+ * Each row's arcs are those of its candidate list built at the given
+ * prices (the best 4 columns of each of the 32 lanes; all n columns when
+ * n <= 128); a matched row's label is capped by the bound on its unlisted
+ * columns, which keeps it eps-optimal over every arc. For n <= 128 the
+ * labels are therefore the exact truncated distances. Uses the per-device
+ * workspace. Blocks until done.
+ */
+la_status la_debug_price_update(const int32_t *cost, int32_t n, const int64_t *prices, const int32_t *row_match,
+                                int64_t eps, void *stream, int32_t *labels_out, int64_t *prices_out);
 
 /* Library version as major * 10000 + minor * 100 + patch. */
 int32_t la_version(void);

@@ -34,6 +34,7 @@ LA_MAX_N = (1 << 20) - 1
 LA_NOALLOC_MAX_N = 16384
 LA_FLAG_NO_CANDIDATE_LISTS = 1
 LA_FLAG_CHECK_PHASES = 2
+LA_FLAG_NO_ARC_FIXING = 4
 
 
 class la_options(ctypes.Structure):
@@ -84,6 +85,15 @@ class la_stats(ctypes.Structure):
         ("check_violations", ctypes.c_int64),
         ("stop_phase", ctypes.c_int32),
         ("stop_eps", ctypes.c_int64),
+        ("phase_tail_ms", ctypes.c_double * 32),
+        ("phase_full_scans", ctypes.c_int64 * 32),
+        ("phase_tail_scans", ctypes.c_int64 * 32),
+        ("phase_fixed_rows", ctypes.c_int64 * 32),
+        ("fixed_rows", ctypes.c_int64),
+        ("fixed_arcs", ctypes.c_int64),
+        ("sweep_ms", ctypes.c_double),
+        ("sweep_scans", ctypes.c_int64),
+        ("sweep_full_scans", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -184,6 +194,7 @@ def lib() -> ctypes.CDLL:
             P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
             L.la_solve.argtypes = [P, i32, P, P, P]
             L.la_solve_ex.argtypes = [P, i32, P, P, P, P, P]
+            L.la_debug_price_update.argtypes = [P, i32, P, P, i64, P, P, P]
             L.la_solve_noalloc.argtypes = [P, i32, P, P, P]
             L.la_solve_sparse.argtypes = [P, P, P, i32, i32, P, P, P]
             L.la_solve_sparse_ex.argtypes = [P, P, P, i32, i32, P, P, P, P, P]
@@ -248,6 +259,11 @@ def la_solve_ex(cost, n, opt, stream, match_out, cost_out, stats_out) -> int:
     return lib().la_solve_ex(_ptr(cost), int(n), None if opt is None else ctypes.byref(opt),
                              _stream(stream), _ptr(match_out), _ptr(cost_out),
                              None if stats_out is None else ctypes.byref(stats_out))
+
+
+def la_debug_price_update(cost, n, prices, row_match, eps, stream, labels_out, prices_out) -> int:
+    return lib().la_debug_price_update(_ptr(cost), int(n), _ptr(prices), _ptr(row_match), int(eps),
+                                       _stream(stream), _ptr(labels_out), _ptr(prices_out))
 
 
 def la_solve_noalloc(cost, n, stream, match_out, cost_out) -> int:

@@ -77,6 +77,14 @@ struct Ctrl {
     unsigned long long check_violations;   // debug mode: failed phase-end checks
     int checked_phases;                    // debug mode: phases checked
     int phase_now;                         // the running phase, frozen when the status is set
+    unsigned long long phase_start_full[64];   // full_scans at each phase start
+    unsigned long long phase_start_tail[64];   // tail_scans at each phase start
+    unsigned long long fix_rows[64];           // arc fixing after phase k: rows fixed
+    unsigned long long fix_arcs[64];           // ... and the arcs those rows keep
+    int pend;                                  // sweep: rows queued for the chain launch
+    unsigned sweep_done;                       // sweep: blocks finished (last one switches the queue)
+    unsigned long long sweep_scans;            // row scans made by the sweep launches
+    unsigned long long sweep_full;             // ... of which full row scans
 };
 
 // Global nanosecond timer (bounds every wait in the kernels).

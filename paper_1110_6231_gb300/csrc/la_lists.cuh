@@ -182,6 +182,41 @@ __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int 
     return r;
 }
 
+// Full scan of row x for the best and second best only, without rebuilding
+// its candidate list: for stretches where the lists keep failing (a large
+// eps moves prices past theta after a bid or two), the top-4 insertion
+// network and the list write would be wasted. The list is left as it was
+// (its bound stays a valid lower bound: prices only fall).
+template <bool WIDE, bool VEC, class P>
+__device__ __forceinline__ auto full_scan_top2(const int32_t *__restrict__ crow, int n, int cmin, uint32_t np1,
+                                               const P &prices, int lane) {
+    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    Lane2<V> t;
+    lane2_init(t);
+    if (VEC) {
+        const int4 *r4 = reinterpret_cast<const int4 *>(crow);
+        const int nv = n >> 2;
+#pragma unroll 8
+        for (int j = lane; j < nv; j += 32) {
+            const int4 c = ld_row4(r4 + j);
+            const int y = j << 2;
+            V qa, qb, qc, qd;
+            prices.q4(y, qa, qb, qc, qd);
+            lane2_push<V>(t, (V)(uint32_t)(c.x - cmin) * np1 + qa, y);
+            lane2_push<V>(t, (V)(uint32_t)(c.y - cmin) * np1 + qb, y + 1);
+            lane2_push<V>(t, (V)(uint32_t)(c.z - cmin) * np1 + qc, y + 2);
+            lane2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + qd, y + 3);
+        }
+    } else {
+        for (int y = lane; y < n; y += 32)
+            lane2_push<V>(t, (V)(uint32_t)(ld_row1(crow + y) - cmin) * np1 + prices.q(y), y);
+    }
+    const V c1 = t.w1 >= 0 ? (V)(uint32_t)(ld_row1(crow + t.w1) - cmin) * np1 : (V)0;
+    ScanResult<V> r{t.b1, t.b2, c1, t.w1 < 0 ? INT_MAX : t.w1};
+    warp_merge(r);
+    return r;
+}
+
 // Short scan of row x over its candidate list (kListK entries per lane).
 // The list entries and the row's bound theta are loaded in the same round
 // trip, or were loaded ahead (ahead.row == x); the prices are gathered only
@@ -223,6 +258,9 @@ __device__ __forceinline__ auto list_scan(int row, int n, int cmin, uint32_t np1
         r.b1 = better ? v[k] : r.b1;
     }
     warp_merge(r);
+    // A row whose arcs were cut down to one (arc fixing) has no second
+    // best: any price drop keeps it eps-optimal, and the bid drops by eps.
+    if (r.b2 == inf) r.b2 = r.b1;
     return r;
 }
 
@@ -233,11 +271,17 @@ template <bool WIDE, bool VEC, bool ONE_SM, int NCH, class P>
 __device__ __forceinline__ auto scan_for_bid(const int32_t *__restrict__ C, int row, int n, int cmin,
                                              uint32_t np1, const P &prices, int lane,
                                              const RowLists &L, unsigned long long R, bool &full,
-                                             const ListAhead &ahead) {
+                                             const ListAhead &ahead, bool try_list = true,
+                                             bool prefetch = false, bool top2 = false) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
     ScanResult<V> t;
     bool ok = false;
-    if (L.cols) {
+    if (prefetch && !try_list) prefetch_row_l2(C + (size_t)row * n, n, lane);
+    if (L.cols && !try_list && top2) {
+        full = true;
+        return full_scan_top2<WIDE, VEC>(C + (size_t)row * n, n, cmin, np1, prices, lane);
+    }
+    if (L.cols && try_list) {
         unsigned long long th = 0;
         t = list_scan<WIDE, ONE_SM>(row, n, cmin, np1, prices, lane, L, ahead, th);
         if (th != 0) {
@@ -251,7 +295,10 @@ __device__ __forceinline__ auto scan_for_bid(const int32_t *__restrict__ C, int 
         }
     }
     full = !ok;
-    if (!ok) t = full_scan<WIDE, VEC, NCH>(C + (size_t)row * n, row, n, cmin, np1, prices, lane, L, R);
+    if (!ok) {
+        if (prefetch && try_list) prefetch_row_l2(C + (size_t)row * n, n, lane);
+        t = full_scan<WIDE, VEC, NCH>(C + (size_t)row * n, row, n, cmin, np1, prices, lane, L, R);
+    }
     return t;
 }
 

@@ -158,6 +158,8 @@ __global__ void k_reset(unsigned long long *__restrict__ key, void *__restrict__
         ctrl->next_row = 0;
         ctrl->qmin[slot ^ 1] = ~0ull;
         ctrl->phase_start_scans[phase & 63] = ctrl->scans;
+        ctrl->phase_start_full[phase & 63] = ctrl->full_scans;
+        ctrl->phase_start_tail[phase & 63] = ctrl->tail_scans;
         if (*reinterpret_cast<volatile int *>(&ctrl->status) == 0) ctrl->phase_now = phase;
         ctrl->rebase_total += qmin;
         ctrl->free_rows = n;
@@ -173,18 +175,27 @@ __global__ void k_reset(unsigned long long *__restrict__ key, void *__restrict__
 }
 
 // The refine phase: persistent grid, one warp per free row.
+//
+// With `sweep` set, the launch is the phase's bulk sweep: every row of the
+// queue bids once, and the row its bid leaves free (the displaced mate, or
+// the row itself after a lost bid) is queued for the next launch instead of
+// bidding at once. The last block to finish makes that queue the current
+// one. The sweep is the bandwidth part of a phase (each row's first scan,
+// all rows in flight); the launch after it carries the displacement chains.
 template <bool WIDE, bool VEC>
 __global__ void __launch_bounds__(256)
 k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
          unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
          Ctrl *__restrict__ ctrl, unsigned long long budget, RowLists L, int tail_T,
-         int *__restrict__ tail_rows, int pu_T, const int *__restrict__ qlist0,
-         const int *__restrict__ qlist1, int stop_free) {
+         int *__restrict__ tail_rows, int pu_T, int *__restrict__ qlist0,
+         int *__restrict__ qlist1, int stop_free, int sweep) {
     constexpr unsigned kFlush = 8;       // scans between budget / status / hand-off checks
+    int miss = 0;                        // this warp's consecutive scans that the lists did not answer
     const int lane = threadIdx.x & 31;
     const unsigned long long R = ctrl->rebase_total;
     const int qmode = ctrl->qmode, qlen = ctrl->qlen;
     const int *qlist = ctrl->qsel ? qlist1 : qlist0;
+    int *pend_list = ctrl->qsel ? qlist0 : qlist1;     // sweep: rows left free by its bids
     const bool pu_on = pu_T > 0 && ctrl->pu_left > 0;
     int row = -1;
     unsigned long long wins = 0, displaced = 0, total = 0, full = 0, hits = 0;
@@ -242,10 +253,21 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
         ++pending;
         ++total;
         bool was_full = false;
+        // After three misses in a row the lists are stale for this stretch
+        // of the phase (a large eps moves prices past theta after a bid or
+        // two): go straight to a full scan for the best two only, trying the
+        // list again every 8th scan. A full scan first asks L2 for the whole
+        // row, so that a lone warp's dependent loads do not wait on HBM.
+        const bool try_list = miss < 3 || (total & 7) == 0;
         const auto t = scan_for_bid<WIDE, VEC, false, 1>(C, row, n, cmin, np1, MirrorPrices<WIDE>{qmv}, lane, L, R, was_full,
-                                                           ListAhead{-1, 0ull, {}});
-        if (was_full) ++full;
-        else ++hits;
+                                                           ListAhead{-1, 0ull, {}}, try_list, true, true);
+        if (was_full) {
+            ++full;
+            ++miss;
+        } else {
+            ++hits;
+            miss = 0;
+        }
         __syncwarp();
         // double push: x -> w, relabel w, w's old mate becomes free
         const unsigned long long qw = (unsigned long long)(t.b1 - t.c1);
@@ -263,6 +285,24 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
             else atomicMax(static_cast<uint32_t *>(qmv) + t.w, (uint32_t)qnow);
         }
         old = __shfl_sync(0xffffffffu, old, 0);
+        if (sweep) {   // one bid per row: the row left free waits for the chain launch
+            int left = -1;
+            if (old > nk) {
+                ++wins;
+                const uint32_t m = key_mate(old);
+                if (m != kNone) {
+                    ++displaced;
+                    left = (int)m;
+                } else if (lane == 0) {
+                    atomicSub(&ctrl->free_rows, 1);
+                }
+            } else {
+                left = row;
+            }
+            if (lane == 0 && left >= 0) pend_list[atomicAdd(&ctrl->pend, 1)] = left;
+            row = -1;
+            continue;
+        }
         if (old > nk) {
             ++wins;
             const uint32_t m = key_mate(old);
@@ -297,6 +337,28 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
         atomicAdd(&ctrl->full_scans, full);
         atomicAdd(&ctrl->list_scans, hits);
         atomicMax(&ctrl->max_chain, total);
+        if (sweep) {
+            atomicAdd(&ctrl->sweep_scans, total);
+            atomicAdd(&ctrl->sweep_full, full);
+        }
+    }
+    if (sweep) {
+        // The last block to finish makes the rows left free the current
+        // queue (the next launch reads it; the launch boundary orders the
+        // writes). Every warp of every block reaches this point.
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(&ctrl->sweep_done, 1u) == gridDim.x - 1) {
+                __threadfence();
+                ctrl->qsel ^= 1;
+                ctrl->qmode = 1;
+                ctrl->qlen = *reinterpret_cast<volatile int *>(&ctrl->pend);
+                ctrl->next_row = 0;
+                ctrl->pend = 0;
+                ctrl->sweep_done = 0;
+            }
+        }
     }
 }
 
@@ -697,6 +759,126 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
     }
 }
 
+// Arc fixing (Sect. 5.2), run when a phase other than the last has ended
+// with an eps-optimal flow. Sect. 5.2 drops every arc whose reduced cost
+// c_p(x,y) exceeds 2 n eps: its flow stays zero in every later phase, so no
+// optimal assignment uses it. With the row price of Algorithm 5.2,
+// c_p(x,y) = v(x,y) - min_z v(x,z) - eps, the rule drops y from x's arcs when
+// v(x,y) - min_z v(x,z) > T = (2n+1) eps. Any upper bound m of the row's
+// minimum may stand in for it: the test then keeps more arcs, never fewer.
+//
+// A row is fixed when everything outside its candidate list can go: its
+// list then holds exactly its remaining arcs and theta = ~0 ("every arc is
+// listed"), so each later bid of the row is a list scan and none reads the
+// row again. One warp per row:
+//   * a fixed row drops the listed arcs that the rule removes;
+//   * a row with a list is fixed when its unlisted columns, all worth at
+//     least theta (see RowLists), are beyond the least listed value m by T;
+//   * otherwise, if `full_pass`, the row is read whole (the exact minimum,
+//     then its arcs within T of it); if no more than kListLen remain, they
+//     become the row's list.
+// Rows that are not fixed keep every arc. The kernel runs between the
+// phase's last refine launch and the next phase's initialisation, so no
+// other kernel reads the lists meanwhile.
+template <bool VEC>
+__global__ void __launch_bounds__(256)
+k_fix(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long T,
+      const unsigned long long *__restrict__ key, RowLists L, Ctrl *__restrict__ ctrl, int full_pass, int phase) {
+    if (*reinterpret_cast<volatile int *>(&ctrl->status) != 0) return;
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+    const unsigned long long R = ctrl->rebase_total;
+    unsigned long long rows = 0, arcs = 0;
+    for (int x = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); x < n; x += warps) {
+        const unsigned long long th = __ldcg(L.theta + x);
+        if (th == 0) continue;
+        const size_t base = (size_t)x * kListLen + kListK * lane;
+        const LaneList e = load_lane_list<false>(L, x, lane);
+        unsigned long long v[kListK], m = ~0ull;
+#pragma unroll
+        for (int k = 0; k < kListK; ++k) {
+            const bool ok = e.y[k] >= 0 && e.y[k] < n;
+            v[k] = ok ? (unsigned long long)(uint32_t)(e.c[k] - cmin) * np1 + key_q(__ldcg(key + e.y[k])) : ~0ull;
+            m = min(m, v[k]);
+        }
+        m = warp_min(m);
+        // every unlisted value is >= this (0: no bound left after the shifts)
+        const unsigned long long unlisted = th > R + 1 ? th - R - 1 : 0;
+        if (th == ~0ull || (unlisted > m && unlisted - m > T)) {
+            int keep[kListK];
+            int kept = 0;
+#pragma unroll
+            for (int k = 0; k < kListK; ++k) {
+                keep[k] = (v[k] != ~0ull && v[k] - m <= T) ? e.y[k] : -1;
+                kept += keep[k] >= 0;
+            }
+#pragma unroll
+            for (int g = 0; g < kListK / 4; ++g)
+                reinterpret_cast<int4 *>(L.cols + base)[g] =
+                    make_int4(keep[4 * g], keep[4 * g + 1], keep[4 * g + 2], keep[4 * g + 3]);
+            kept = __reduce_add_sync(0xffffffffu, kept);
+            if (lane == 0) {
+                L.theta[x] = ~0ull;
+                ++rows;
+                arcs += (unsigned long long)kept;
+            }
+            continue;
+        }
+        if (!full_pass) continue;
+        // the whole row: exact minimum, then the arcs within T of it
+        const int32_t *crow = C + (size_t)x * n;
+        unsigned long long mn = ~0ull;
+        if (VEC) {
+            const int4 *r4 = reinterpret_cast<const int4 *>(crow);
+            for (int j = lane; j < (n >> 2); j += 32) {
+                const int4 c = ld_row4(r4 + j);
+                const int y = j << 2;
+                mn = min(mn, (unsigned long long)(uint32_t)(c.x - cmin) * np1 + key_q(__ldcg(key + y)));
+                mn = min(mn, (unsigned long long)(uint32_t)(c.y - cmin) * np1 + key_q(__ldcg(key + y + 1)));
+                mn = min(mn, (unsigned long long)(uint32_t)(c.z - cmin) * np1 + key_q(__ldcg(key + y + 2)));
+                mn = min(mn, (unsigned long long)(uint32_t)(c.w - cmin) * np1 + key_q(__ldcg(key + y + 3)));
+            }
+        } else {
+            for (int y = lane; y < n; y += 32)
+                mn = min(mn, (unsigned long long)(uint32_t)(ld_row1(crow + y) - cmin) * np1 + key_q(__ldcg(key + y)));
+        }
+        mn = warp_min(mn);
+        int cnt = 0;
+        for (int y = lane; y < n; y += 32)
+            cnt += (unsigned long long)(uint32_t)(ld_row1(crow + y) - cmin) * np1 + key_q(__ldcg(key + y)) - mn <= T;
+        const int total = __reduce_add_sync(0xffffffffu, cnt);
+        if (total > kListLen) continue;
+        // lane l writes its arcs at the flat positions after lanes 0..l-1's
+        int off = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, off, o);
+            if (lane >= o) off += t;
+        }
+        off -= cnt;
+        int *cols = L.cols + (size_t)x * kListLen;
+        int *costs = L.costs + (size_t)x * kListLen;
+        for (int y = lane; y < n; y += 32) {
+            const int c = ld_row1(crow + y);
+            if ((unsigned long long)(uint32_t)(c - cmin) * np1 + key_q(__ldcg(key + y)) - mn <= T) {
+                cols[off] = y;
+                costs[off] = c;
+                ++off;
+            }
+        }
+        for (int k = total + lane; k < kListLen; k += 32) cols[k] = -1;
+        if (lane == 0) {
+            L.theta[x] = ~0ull;
+            ++rows;
+            arcs += (unsigned long long)total;
+        }
+    }
+    if (lane == 0 && rows) {
+        atomicAdd(&ctrl->fix_rows[phase & 63], rows);
+        atomicAdd(&ctrl->fix_arcs[phase & 63], arcs);
+    }
+}
+
 // Read the matching out of the column keys; exact int64 cost.
 __global__ void k_finalize(const int32_t *__restrict__ C, int n, const unsigned long long *__restrict__ key,
                            int32_t *match, long long *cost, long long *prices, Ctrl *ctrl, int slot) {
@@ -730,10 +912,13 @@ __global__ void k_check_snapshot(const unsigned long long *__restrict__ key, int
 // eps-optimal, (n+1)(C[x][y] - cmin) + q(y) <= min_z ((n+1)(C[x][z] - cmin)
 // + q(z)) + eps (version-2 eps-CS, Sect. 5.1), and that q(y) did not fall
 // during the phase (prices only decrease, Lemma 5.2). Plain 64-bit
-// arithmetic, independent of the refine's narrow and list paths.
+// arithmetic, independent of the refine's narrow and list paths. For a row
+// that arc fixing cut down to its list (theta = ~0), z ranges over the
+// listed columns, its remaining arcs, with the costs read from C.
 __global__ void k_check_phase(const int32_t *__restrict__ C, int n, int cmin, unsigned long long np1,
                               const unsigned long long *__restrict__ key, const unsigned long long *__restrict__ q0,
-                              unsigned long long eps, int perfect, int *__restrict__ seen, Ctrl *ctrl) {
+                              unsigned long long eps, int perfect, int *__restrict__ seen, Ctrl *ctrl,
+                              RowLists L) {
     const int lane = threadIdx.x & 31;
     const int warps = (int)((gridDim.x * blockDim.x) >> 5);
     for (int y = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); y < n; y += warps) {
@@ -746,9 +931,18 @@ __global__ void k_check_phase(const int32_t *__restrict__ C, int n, int cmin, un
             if (lane == 0 && atomicAdd(&seen[x], 1) != 0) ++bad;
             const int32_t *row = C + (size_t)x * n;
             unsigned long long mn = ~0ull;
-            for (int z = lane; z < n; z += 32) {
-                const unsigned long long v = (unsigned long long)(uint32_t)(row[z] - cmin) * np1 + key_q(key[z]);
-                mn = v < mn ? v : mn;
+            if (L.cols && L.theta[x] == ~0ull) {
+                for (int k = lane; k < kListLen; k += 32) {
+                    const int z = L.cols[(size_t)x * kListLen + k];
+                    if (z < 0 || z >= n) continue;
+                    const unsigned long long v = (unsigned long long)(uint32_t)(row[z] - cmin) * np1 + key_q(key[z]);
+                    mn = v < mn ? v : mn;
+                }
+            } else {
+                for (int z = lane; z < n; z += 32) {
+                    const unsigned long long v = (unsigned long long)(uint32_t)(row[z] - cmin) * np1 + key_q(key[z]);
+                    mn = v < mn ? v : mn;
+                }
             }
             mn = warp_min(mn);
             const unsigned long long mine = (unsigned long long)(uint32_t)(row[y] - cmin) * np1 + key_q(k);
@@ -779,7 +973,7 @@ struct Workspace {
     Ctrl *h_ctrl = nullptr;
     int num_sms = 0;
     bool events = false;
-    cudaEvent_t ev[4 * kMaxPhases];   // per phase: refine start, tail start, tail end, end
+    cudaEvent_t ev[5 * kMaxPhases];   // per phase: start, sweep end, tail start, tail end, end
 };
 
 std::mutex g_mu;
@@ -895,7 +1089,17 @@ template <bool WIDE, bool VEC>
 cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C, int n, int cmin, uint32_t np1,
                           unsigned long long eps, unsigned long long qlim, Workspace &ws,
                           unsigned long long budget, const RowLists &L, int tail_T, int pu_T, int pu_rounds,
-                          int64_t &launches, int stop_free, cudaEvent_t ev_tail, cudaEvent_t ev_fin) {
+                          int64_t &launches, int stop_free, cudaEvent_t ev_sweep, cudaEvent_t ev_tail,
+                          cudaEvent_t ev_fin, bool sweep) {
+    if (sweep) {   // the phase's bulk sweep: every row bids once
+        k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L,
+                                                   0, ws.tail_rows, 0, ws.qlist[0], ws.qlist[1], 0, 1);
+        ++launches;
+    }
+    if (ev_sweep) {
+        cudaError_t e = cudaEventRecord(ev_sweep, s);
+        if (e != cudaSuccess) return e;
+    }
     for (int r = 0; r <= pu_rounds; ++r) {
         if (r > 0) {
             cudaError_t e = launch_pu<WIDE>(s, C, n, cmin, np1, eps, qlim, ws, L);
@@ -905,7 +1109,7 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
         // the last refine of a phase never stops for a price update
         k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L,
                                                    tail_T, ws.tail_rows, r < pu_rounds ? pu_T : 0,
-                                                   ws.qlist[0], ws.qlist[1], stop_free);
+                                                   ws.qlist[0], ws.qlist[1], stop_free, 0);
         ++launches;
     }
     if (ev_tail) {
@@ -928,7 +1132,7 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
         }
         // rows the tail kernel gave back, if any (an empty queue otherwise)
         k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L,
-                                                   0, ws.tail_rows, 0, ws.qlist[0], ws.qlist[1], stop_free);
+                                                   0, ws.tail_rows, 0, ws.qlist[0], ws.qlist[1], stop_free, 0);
         ++launches;
     } else if (ev_fin) {
         cudaError_t e = cudaEventRecord(ev_fin, s);
@@ -948,6 +1152,126 @@ inline int small_grid(int n, int block, int num_sms) {
         if ((call) != cudaSuccess) return LA_ERR_CUDA; \
     } while (0)
 
+// ------------------------------------------------------------------------
+// la_debug_price_update: one global price update (Algorithm 5.3, the same
+// k_pu the refine launches) on a mid-phase state given by the caller, so
+// that its labels and new prices can be checked one by one.
+
+// Mates of the given partial matching, and the price mirror.
+template <bool WIDE>
+__global__ void k_dbg_state(const int32_t *__restrict__ row_match, int n, unsigned long long *__restrict__ key,
+                            void *__restrict__ qmv, Ctrl *ctrl) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        const int y = row_match[x];
+        if (y < 0) continue;
+        if (y >= n) {
+            set_status(ctrl, LA_ERR_INVALID);
+            continue;
+        }
+        const unsigned long long k = key[y];
+        // a column claimed by two rows is an invalid state
+        if (atomicCAS(key + y, k, pack_key(key_q(k), (uint32_t)x)) != k || key_mate(k) != kNone)
+            set_status(ctrl, LA_ERR_INVALID);
+    }
+}
+
+template <bool WIDE>
+__global__ void k_dbg_mirror(const unsigned long long *__restrict__ key, int n, void *__restrict__ qmv, Ctrl *ctrl) {
+    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
+        const unsigned long long q = key_q(key[y]);
+        if (WIDE) static_cast<unsigned long long *>(qmv)[y] = q;
+        else static_cast<uint32_t *>(qmv)[y] = (uint32_t)q;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // the state k_pu starts from: no queue, one update
+        ctrl->handoff = 2;
+        ctrl->qmode = 1;
+        ctrl->qlen = 0;
+        ctrl->qsel = 0;
+        ctrl->next_row = 0;
+        ctrl->tail_count = 0;
+        ctrl->rebase_total = 0;
+        ctrl->pu_left = 1;
+    }
+}
+
+// Candidate lists of every row at the given prices (one full scan each).
+template <bool WIDE, bool VEC>
+__global__ void __launch_bounds__(256)
+k_dbg_lists(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, const void *__restrict__ qmv, RowLists L) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int x = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); x < n; x += warps)
+        (void)full_scan<WIDE, VEC, 1>(C + (size_t)x * n, x, n, cmin, np1, MirrorPrices<WIDE>{qmv}, lane, L, 0ull);
+}
+
+// Truncated labels and the new prices in the caller's sign and units.
+__global__ void k_dbg_out(const unsigned long long *__restrict__ key, const unsigned *__restrict__ lab, int n,
+                          const Ctrl *ctrl, int32_t *labels_out, int64_t *prices_out) {
+    const unsigned long long K = ctrl->pu_levels;   // the truncation level applied (0: no update)
+    const long long pm = ctrl->pmax;
+    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
+        labels_out[y] = (int32_t)min((unsigned long long)lab[y], K);
+        prices_out[y] = pm - (long long)key_q(key[y]);
+    }
+}
+
+static la_status debug_price_update_locked(const int32_t *cost, int32_t n, const int64_t *prices,
+                                           const int32_t *row_match, int64_t eps, cudaStream_t s,
+                                           int32_t *labels_out, int64_t *prices_out) {
+    int dev = 0;
+    LA_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return LA_ERR_INVALID;
+    Workspace &ws = g_ws[dev];
+    if (la_status e = ensure_ws(ws, n)) return e;
+    Ctrl init;
+    std::memset(&init, 0, sizeof(init));
+    init.cmin = INT_MAX;
+    init.cmax = INT_MIN;
+    init.qmin[0] = init.qmin[1] = ~0ull;
+    init.pmax = LLONG_MIN;
+    *ws.h_ctrl = init;
+    LA_CK(cudaMemcpyAsync(ws.ctrl, ws.h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+    const long long total = (long long)n * n;
+    const int mm_grid = (int)std::max<long long>(1, std::min<long long>((total / 4 + 255) / 256, 8LL * ws.num_sms));
+    const int sg = small_grid(n, 256, ws.num_sms);
+    k_minmax<<<mm_grid, 256, 0, s>>>(cost, total, ws.ctrl);
+    k_warm_pmax<<<sg, 256, 0, s>>>(reinterpret_cast<const long long *>(prices), n, ws.ctrl);
+    k_warm_init<<<sg, 256, 0, s>>>(reinterpret_cast<const long long *>(prices), n, ws.key, ws.ctrl);
+    LA_CK(cudaGetLastError());
+    LA_CK(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    LA_CK(cudaStreamSynchronize(s));
+    const Ctrl c0 = *ws.h_ctrl;
+    const unsigned long long np1 = (unsigned long long)n + 1;
+    const unsigned long long Ct = np1 * (unsigned long long)((long long)c0.cmax - (long long)c0.cmin);
+    if (Ct >= kRangeLimit || c0.qspread >= (1ull << 42)) return LA_ERR_OVERFLOW;
+    // the solver's choice of value width, for a phase at this eps
+    const bool wide = c0.qspread + 4 * Ct + 2 * (unsigned long long)eps + 16 >= (1ull << 32);
+    const unsigned long long qlim = wide ? (kQMax - 1) : ((1ull << 32) - 2 - Ct);
+    const bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(cost) & 15) == 0);
+    const RowLists L{ws.lcols, ws.lcosts, ws.ltheta};
+    const int lg = std::max(1, std::min((n + 7) / 8, 8 * ws.num_sms));   // 8 warps per block
+    if (wide) {
+        k_dbg_state<true><<<sg, 256, 0, s>>>(row_match, n, ws.key, ws.qm, ws.ctrl);
+        k_dbg_mirror<true><<<sg, 256, 0, s>>>(ws.key, n, ws.qm, ws.ctrl);
+        if (vec) k_dbg_lists<true, true><<<lg, 256, 0, s>>>(cost, n, c0.cmin, (uint32_t)np1, ws.qm, L);
+        else k_dbg_lists<true, false><<<lg, 256, 0, s>>>(cost, n, c0.cmin, (uint32_t)np1, ws.qm, L);
+        LA_CK(launch_pu<true>(s, cost, n, c0.cmin, (uint32_t)np1, (unsigned long long)eps, qlim, ws, L));
+    } else {
+        k_dbg_state<false><<<sg, 256, 0, s>>>(row_match, n, ws.key, ws.qm, ws.ctrl);
+        k_dbg_mirror<false><<<sg, 256, 0, s>>>(ws.key, n, ws.qm, ws.ctrl);
+        if (vec) k_dbg_lists<false, true><<<lg, 256, 0, s>>>(cost, n, c0.cmin, (uint32_t)np1, ws.qm, L);
+        else k_dbg_lists<false, false><<<lg, 256, 0, s>>>(cost, n, c0.cmin, (uint32_t)np1, ws.qm, L);
+        LA_CK(launch_pu<false>(s, cost, n, c0.cmin, (uint32_t)np1, (unsigned long long)eps, qlim, ws, L));
+    }
+    k_dbg_out<<<sg, 256, 0, s>>>(ws.key, ws.pu_lab, n, ws.ctrl, labels_out, prices_out);
+    LA_CK(cudaGetLastError());
+    LA_CK(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    LA_CK(cudaStreamSynchronize(s));
+    return (la_status)ws.h_ctrl->status;
+}
+
+
+
 static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *opt, cudaStream_t s,
                               int32_t *match_out, int64_t *cost_out, la_stats *st) {
     const int alpha = (opt && opt->alpha) ? opt->alpha : 10;
@@ -965,6 +1289,11 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     // intermediate phases stop at this many free rows (the last phase never does)
     // (off unless asked: see la_options.phase_cutoff)
     const int stop_free = (opt && opt->phase_cutoff > 0) ? opt->phase_cutoff : 0;
+    const bool sweep = true;   // every phase opens with its bulk sweep
+    // arc fixing needs an eps-optimal flow at every phase end (no cutoff);
+    // the final prices certify only the arcs kept, so not with prices_out
+    const bool arcfix = lists && !(opt && (opt->flags & LA_FLAG_NO_ARC_FIXING)) && stop_free == 0 &&
+                        !(opt && opt->prices_out);
     if (alpha < 2 || eps0 < 0 || block < 32 || block > 256 || block % 32) return LA_ERR_INVALID;
     if (opt && opt->scan_budget < 0) return LA_ERR_INVALID;
 
@@ -1087,25 +1416,38 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
             k_check_snapshot<<<sg, 256, 0, s>>>(ws.key, n, chk_q0);
             ++launches;
         }
-        if (profile) LA_CK(cudaEventRecord(ws.ev[4 * ph], s));
+        if (profile) LA_CK(cudaEventRecord(ws.ev[5 * ph], s));
         const int sf = ph + 1 < (int)sched.size() ? stop_free : 0;
-        cudaEvent_t evt = profile ? ws.ev[4 * ph + 1] : nullptr;
-        cudaEvent_t evf = profile ? ws.ev[4 * ph + 2] : nullptr;
+        cudaEvent_t evs = profile ? ws.ev[5 * ph + 1] : nullptr;
+        cudaEvent_t evt = profile ? ws.ev[5 * ph + 2] : nullptr;
+        cudaEvent_t evf = profile ? ws.ev[5 * ph + 3] : nullptr;
         if (wide) {
-            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt, evf)));
-            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt, evf)));
+            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep)));
+            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep)));
         } else {
-            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt, evf)));
-            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evt, evf)));
+            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep)));
+            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep)));
         }
-        if (profile) LA_CK(cudaEventRecord(ws.ev[4 * ph + 3], s));
+        if (profile) LA_CK(cudaEventRecord(ws.ev[5 * ph + 4], s));
         if (check) {
             LA_CK(cudaMemsetAsync(chk_seen, 0, sizeof(int) * n, s));
             const int cg = std::max(1, std::min((n + 7) / 8, 8 * ws.num_sms));   // 8 warps per block
             k_check_phase<<<cg, 256, 0, s>>>(cost, n, cmin, np1, ws.key, chk_q0, sched[ph],
-                                             (sf == 0) ? 1 : 0, chk_seen, ws.ctrl);
+                                             (sf == 0) ? 1 : 0, chk_seen, ws.ctrl, L);
             ++launches;
             LA_CK(cudaGetLastError());
+        }
+        if (arcfix && ph + 1 < (int)sched.size()) {
+            const unsigned long long T = (2ull * (unsigned long long)n + 1) * sched[ph];
+            // T <= C~ / 16 leaves rows with a few arcs each: worth a full pass
+            const int full_pass = T <= Ct / 16 ? 1 : 0;
+            if (T < Ct) {   // otherwise no arc can go
+                const int fg = std::max(1, std::min((n + 7) / 8, 8 * ws.num_sms));   // 8 warps per block
+                if (vec) k_fix<true><<<fg, 256, 0, s>>>(cost, n, cmin, (uint32_t)np1, T, ws.key, L, ws.ctrl, full_pass, ph);
+                else k_fix<false><<<fg, 256, 0, s>>>(cost, n, cmin, (uint32_t)np1, T, ws.key, L, ws.ctrl, full_pass, ph);
+                ++launches;
+                LA_CK(cudaGetLastError());
+            }
         }
     }
     const int fslot = ph & 1;
@@ -1127,7 +1469,7 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.wins = (int64_t)c1.wins;
     stats.displaced = (int64_t)c1.displaced;
     stats.launches = launches;
-    stats.refine_launches = (int64_t)sched.size() * (1 + pu_rounds + (tail_T > 0 ? 1 : 0));
+    stats.refine_launches = (int64_t)sched.size() * (1 + pu_rounds + (tail_T > 0 ? 1 : 0) + (sweep ? 1 : 0));
     stats.price_updates = (int64_t)c1.pu_updates;
     stats.price_update_sweeps = (int64_t)c1.pu_iters;
     stats.price_update_levels = (int64_t)c1.pu_levels;
@@ -1137,10 +1479,21 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.tail_scans = (int64_t)c1.tail_scans;
     stats.tail_full_scans = (int64_t)c1.tail_full;
     stats.tail_giveups = c1.tail_giveups;
+    stats.sweep_scans = (int64_t)c1.sweep_scans;
+    stats.sweep_full_scans = (int64_t)c1.sweep_full;
     stats.tail_phases = c1.tail_phases;
     for (int k = 0; k < ph && k < LA_STATS_PHASES; ++k) {
-        const unsigned long long end = (k + 1 < ph) ? c1.phase_start_scans[k + 1] : c1.scans;
-        stats.phase_scans[k] = (int64_t)(end - c1.phase_start_scans[k]);
+        const bool last = k + 1 >= ph;
+        stats.phase_scans[k] = (int64_t)((last ? c1.scans : c1.phase_start_scans[k + 1]) - c1.phase_start_scans[k]);
+        stats.phase_full_scans[k] =
+            (int64_t)((last ? c1.full_scans : c1.phase_start_full[k + 1]) - c1.phase_start_full[k]);
+        stats.phase_tail_scans[k] =
+            (int64_t)((last ? c1.tail_scans : c1.phase_start_tail[k + 1]) - c1.phase_start_tail[k]);
+        stats.phase_fixed_rows[k] = (int64_t)c1.fix_rows[k];
+        if (c1.fix_rows[k]) {
+            stats.fixed_rows = (int64_t)c1.fix_rows[k];
+            stats.fixed_arcs = (int64_t)c1.fix_arcs[k];
+        }
     }
     stats.list_entries = lists ? kListLen : 0;
     stats.checked_phases = c1.checked_phases;
@@ -1148,17 +1501,24 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.stop_eps = c1.status ? (int64_t)sched[std::min<int>(std::max(c1.phase_now, 0), (int)sched.size() - 1)] : 0;
     stats.check_violations = (int64_t)c1.check_violations;
     if (profile) {
-        double ms = 0, tail_ms = 0;
+        double ms = 0, tail_ms = 0, sweep_ms = 0;
         for (int k = 0; k < ph; ++k) {
             float t = 0, tt = 0;
-            LA_CK(cudaEventElapsedTime(&t, ws.ev[4 * k], ws.ev[4 * k + 3]));
-            LA_CK(cudaEventElapsedTime(&tt, ws.ev[4 * k + 1], ws.ev[4 * k + 2]));
+            float ts = 0;
+            LA_CK(cudaEventElapsedTime(&t, ws.ev[5 * k], ws.ev[5 * k + 4]));
+            LA_CK(cudaEventElapsedTime(&tt, ws.ev[5 * k + 2], ws.ev[5 * k + 3]));
+            LA_CK(cudaEventElapsedTime(&ts, ws.ev[5 * k], ws.ev[5 * k + 1]));
+            sweep_ms += ts;
             ms += t;
             tail_ms += tt;
-            if (k < LA_STATS_PHASES) stats.phase_ms[k] = t;
+            if (k < LA_STATS_PHASES) {
+                stats.phase_ms[k] = t;
+                stats.phase_tail_ms[k] = tt;
+            }
         }
         stats.refine_ms = ms;
         stats.tail_ms = tail_ms;
+        stats.sweep_ms = sweep_ms;
     }
     if (st) *st = stats;
     if (c1.status == 0 && check && (c1.check_violations != 0 || c1.checked_phases != ph)) return LA_ERR_INTERNAL;
@@ -1191,6 +1551,15 @@ const char *la_status_string(la_status s) {
     case LA_ERR_INFEASIBLE: return "LA_ERR_INFEASIBLE: the graph has no perfect matching";
     }
     return "unknown la_status";
+}
+
+la_status la_debug_price_update(const int32_t *cost, int32_t n, const int64_t *prices, const int32_t *row_match,
+                                int64_t eps, void *stream, int32_t *labels_out, int64_t *prices_out) {
+    if (n < 2 || n > LA_MAX_N || eps < 1 || !cost || !prices || !row_match || !labels_out || !prices_out)
+        return LA_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(g_mu);
+    return debug_price_update_locked(cost, n, prices, row_match, eps, static_cast<cudaStream_t>(stream),
+                                     labels_out, prices_out);
 }
 
 la_status la_release_workspace(void) {
@@ -1313,11 +1682,11 @@ la_status solve_noalloc_locked(const int32_t *cost, int32_t n, cudaStream_t s, i
         if (wide) k_reset<true><<<sg, 256, 0, s>>>(key, qm, n, qlim, ctrl, slot, ph, 0);
         else k_reset<false><<<sg, 256, 0, s>>>(key, qm, n, qlim, ctrl, slot, ph, 0);
         if (wide) {
-            if (vec) k_refine<true, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr, 0, nullptr, nullptr, 0);
-            else k_refine<true, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr, 0, nullptr, nullptr, 0);
+            if (vec) k_refine<true, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr, 0, nullptr, nullptr, 0, 0);
+            else k_refine<true, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr, 0, nullptr, nullptr, 0, 0);
         } else {
-            if (vec) k_refine<false, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr, 0, nullptr, nullptr, 0);
-            else k_refine<false, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr, 0, nullptr, nullptr, 0);
+            if (vec) k_refine<false, true><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr, 0, nullptr, nullptr, 0, 0);
+            else k_refine<false, false><<<grid, block, 0, s>>>(cost, n, cmin, (uint32_t)np1, sched[ph], qlim, key, qm, ctrl, budget, RowLists{nullptr, nullptr, nullptr}, 0, nullptr, 0, nullptr, nullptr, 0, 0);
         }
     }
     LA_CK(cudaMemsetAsync(cost_out, 0, sizeof(int64_t), s));

@@ -271,9 +271,13 @@ def test_profile_counts(la):
     C = synth.uniform_costs(1024, 0, 1000, 1)
     st = check(la, C, profile=True)
     assert st["phases"] == 6
-    # per phase: the refine grid and, after the one-CTA tail kernel, a refine
-    # launch for any rows the tail gives back (no price-update rounds by default)
-    assert st["refine_launches"] == 2 * st["phases"]
+    # per phase: the bulk sweep, the refine grid that carries the chains and,
+    # after the one-CTA tail kernel, a refine launch for any rows the tail
+    # gives back (no price-update rounds by default)
+    assert st["refine_launches"] == 3 * st["phases"]
+    # the sweep makes exactly one bid per row in every phase
+    assert st["sweep_scans"] == 1024 * st["phases"]
+    assert 0 <= st["sweep_full_scans"] <= st["sweep_scans"] and st["sweep_ms"] > 0
     assert 0 <= st["tail_giveups"] <= st["tail_phases"] <= st["phases"]
     assert st["refine_ms"] > 0
     assert st["scans"] >= 1024 * 6
