@@ -1,6 +1,6 @@
 """`bench.py --impl reference` times the oracle on the host cores and prints
 one JSON line with the bench contract's keys; it needs no GPU, so the line's
-shape is checked here (one timed solve of the n = 4096 workload)."""
+shape is checked here (one timed solve of the n = 8192 geometric workload)."""
 
 import json
 import os
@@ -23,7 +23,7 @@ def test_reference_arm_prints_one_contract_line():
         assert key in d, key
     assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 3
     assert d["value"] > 0 and d["higher_is_better"] is True
-    assert d["config"]["workload"] == "uniform-n4096-c2^20"
+    assert d["config"]["workload"] == "geometric-n8192" and d["config"]["alpha"] == 10
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
