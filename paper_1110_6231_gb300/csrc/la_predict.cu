@@ -13,8 +13,14 @@
 //   c     = mean_j h1_j                         set pooling
 //   h2_j  = relu(W2^T [h1_j ; c] + b2)
 //   y_j   = W3^T h2_j + b3                      predicted (v(j) - mean v) / T
-// Every matrix product runs on the tensor cores: BF16 operands staged in
-// shared memory, mma.sync m16n8k16, FP32 accumulation and FP32 storage.
+// Every matrix product runs on the Blackwell tensor cores (tcgen05): the
+// operands are BF16 in global memory (activations written in BF16 by the
+// kernel that produces them, the weights converted to BF16 once per call),
+// loaded by TMA into shared memory with the 128-byte swizzle, multiplied by
+// tcgen05.mma into FP32 accumulators in tensor memory and read back by
+// tcgen05.ld in the epilogue (bias, ReLU, FP32 and BF16 stores, split-K
+// atomics). The master weights and the optimiser state stay FP32.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -27,8 +33,11 @@
 
 #include "la.h"
 #include "la_device.cuh"
+#include "la_tc.cuh"
 
 namespace {
+
+namespace tc = la::tc;
 
 constexpr int F = LA_PRED_FEATURES_PADDED;   // 16
 constexpr int H = LA_PRED_WIDTH;             // 128
@@ -161,108 +170,186 @@ k_features(int n, int rb, const float *__restrict__ part, const int *__restrict_
     }
 }
 
-// ------------------------------------------------------------ GEMM on tensor cores
+// ------------------------------------------------------------ GEMM on tcgen05
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&v);
-}
+// C[M x N] = A[M x K] * B[N x K]^T. A and B are K-major BF16 in global
+// memory, described by TMA tensor maps with 64-element (128-byte) boxes and
+// the 128-byte swizzle. One CTA of 128 threads computes 128 rows of C
+// (TMEM lanes) by BN columns over the K range of its split (gridDim.y):
+// thread 0 streams K in chunks of 64 through two shared-memory stages (TMA
+// completes on a per-stage mbarrier) and issues four 128 x BN x 16 MMAs
+// per chunk (fewer in a last, partial chunk); tcgen05.commit frees a stage
+// once its MMAs are done and signals the end. Then every warp reads its 32
+// TMEM lanes (rows) back 16 columns at a time for the epilogue. Every wait
+// is bounded (1 s): on a timeout the kernel sets *err and still frees its
+// TMEM.
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128;
+enum { EP_BIAS = 1, EP_RELU = 2, EP_ATOMIC = 4, EP_BF16 = 8, EP_TRANS = 16, EP_NOSTORE = 32 };
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
+template <int BN>
+constexpr int tc_stage_bytes() { return TC_BM * TC_BK * 2 + BN * TC_BK * 2; }
+template <int BN>
+constexpr int tc_smem_bytes() { return 1024 + 2 * tc_stage_bytes<BN>() + 64; }
+template <int BN>
+constexpr uint32_t tc_tmem_cols() { return BN <= 32 ? 32u : (uint32_t)BN; }
 
-enum { EPI_STORE = 0, EPI_BIAS_RELU = 1, EPI_BIAS = 2, EPI_ATOMIC = 3 };
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS)
+k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int K,
+          int k_per_split, float *__restrict__ out, int ldo, int ncols, __nv_bfloat16 *__restrict__ outb, int ldb,
+          const float *__restrict__ bias, int ep, int *__restrict__ err) {
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "N of a 128-row tcgen05 MMA");
+    extern __shared__ uint8_t tc_raw[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t raw = tc::smem_addr(tc_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;      // the swizzled tiles need 1024-byte alignment
+    uint8_t *sm = tc_raw + (base - raw);
+    constexpr int SA = TC_BM * TC_BK * 2, ST = tc_stage_bytes<BN>();
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + 2 * ST);   // [2] a stage's TMA bytes landed
+    uint64_t *freed = full + 2;                                    // [2] a stage's MMAs are done
+    uint64_t *done = full + 4;                                     // every MMA is done
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(full + 5);
+    const int m0 = blockIdx.x * TC_BM;
+    const int k0 = blockIdx.y * k_per_split;
+    const int k1 = min(K, k0 + k_per_split);
+    const int nk = k1 > k0 ? (k1 - k0 + TC_BK - 1) / TC_BK : 0;
+    constexpr unsigned long long kLimit = 1000000000ull;
 
-// C[M x N] (op)= op(A)[M x K] * op(B)[K x N], FP32 in global memory.
-// op(A)[m][k] = transA ? A[k * lda + m] : A[m * lda + k]; same for B.
-// Block tile 64 x 64, K step 32, 4 warps (each 16 rows x 64 columns).
-// Operands are rounded to BF16 when staged; accumulation is FP32.
-// gridDim.z splits K (EPI_ATOMIC adds partial products into C).
-constexpr int TM = 64, TN = 64, TK = 32;
-
-__global__ void __launch_bounds__(128)
-k_gemm(const float *__restrict__ A, int lda, int transA, const float *__restrict__ B, int ldb, int transB,
-       float *__restrict__ Cout, int ldc, int M, int N, int K, int epi, const float *__restrict__ bias,
-       int k_per_split) {
-    __shared__ uint32_t sA[TM][TK / 2 + 4];     // bf16 pairs along k
-    __shared__ uint32_t sB[TN][TK / 2 + 4];     // B stored n-major: pairs along k
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
-    const int kbeg = blockIdx.z * k_per_split;
-    const int kend = min(K, kbeg + k_per_split);
-    const int g = lane >> 2, t = lane & 3;
-    float acc[8][4];
-    for (int i = 0; i < 8; ++i)
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int k0 = kbeg; k0 < kend; k0 += TK) {
-        // stage A tile [64 x 32] and B tile [32 x 64] as bf16 pairs
-        for (int e = tid; e < TM * (TK / 2); e += 128) {
-            const int r = e / (TK / 2), kp = e % (TK / 2);
-            const int m = m0 + r, k = k0 + 2 * kp;
-            float x0 = 0.f, x1 = 0.f;
-            if (m < M) {
-                if (k < kend) x0 = transA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
-                if (k + 1 < kend) x1 = transA ? A[(size_t)(k + 1) * lda + m] : A[(size_t)m * lda + k + 1];
-            }
-            sA[r][kp] = pack_bf16x2(x0, x1);
-        }
-        for (int e = tid; e < TN * (TK / 2); e += 128) {
-            const int c = e / (TK / 2), kp = e % (TK / 2);
-            const int nn = n0 + c, k = k0 + 2 * kp;
-            float x0 = 0.f, x1 = 0.f;
-            if (nn < N) {
-                if (k < kend) x0 = transB ? B[(size_t)nn * ldb + k] : B[(size_t)k * ldb + nn];
-                if (k + 1 < kend) x1 = transB ? B[(size_t)nn * ldb + k + 1] : B[(size_t)(k + 1) * ldb + nn];
-            }
-            sB[c][kp] = pack_bf16x2(x0, x1);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < TK / 16; ++ks) {
-            const int kb = ks * 8;   // in pairs
-            uint32_t a[4];
-            const int r = warp * 16 + g;
-            a[0] = sA[r][kb + t];
-            a[1] = sA[r + 8][kb + t];
-            a[2] = sA[r][kb + 4 + t];
-            a[3] = sA[r + 8][kb + 4 + t];
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                uint32_t b[2];
-                b[0] = sB[nt * 8 + g][kb + t];
-                b[1] = sB[nt * 8 + g][kb + 4 + t];
-                mma_bf16(acc[nt], a, b);
-            }
-        }
-        __syncthreads();
+    if (warp == 0) tc::tmem_alloc(tslot, tc_tmem_cols<BN>());
+    if (tid == 0) {
+        for (int i = 0; i < 5; ++i) tc::mbar_init(full + i, 1);
+        tc::fence_mbar_init();
     }
-    // epilogue: acc[nt][0..1] -> row g, cols 2t, 2t+1; acc[nt][2..3] -> row g+8
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int m = m0 + warp * 16 + g + 8 * h;
-            if (m >= M) continue;
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int nn = n0 + nt * 8 + 2 * t + c;
-                if (nn >= N) continue;
-                float v = acc[nt][2 * h + c];
-                float *dst = Cout + (size_t)m * ldc + nn;
-                if (epi == EPI_ATOMIC) {
-                    atomicAdd(dst, v);
-                } else {
-                    if (epi == EPI_BIAS_RELU || epi == EPI_BIAS) v += bias[nn];
-                    if (epi == EPI_BIAS_RELU) v = fmaxf(v, 0.f);
-                    *dst = v;
-                }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    if (tid == 0) {
+        constexpr uint32_t idesc = tc::idesc_bf16(TC_BM, BN);
+        int issued = 0, consumed = 0;
+        bool ok = true;
+        for (; issued < nk && issued < 2; ++issued) {
+            const int s = issued & 1;
+            tc::mbar_expect_tx(full + s, ST);
+            tc::tma_load_2d(sm + s * ST, &mapA, full + s, k0 + issued * TC_BK, m0);
+            tc::tma_load_2d(sm + s * ST + SA, &mapB, full + s, k0 + issued * TC_BK, 0);
+        }
+        for (int c = 0; c < nk; ++c) {
+            const int s = c & 1;
+            if (!(ok = tc::mbar_wait(full + s, (c >> 1) & 1, kLimit))) break;
+            consumed = c + 1;
+            tc::fence_after_sync();
+            const int ksteps = (min(TC_BK, k1 - (k0 + c * TC_BK)) + 15) / 16;
+            const uint32_t sa = base + s * ST, sb = sa + SA;
+            for (int kk = 0; kk < ksteps; ++kk)
+                tc::mma_bf16(tmem, tc::desc_k128(sa + 32 * kk), tc::desc_k128(sb + 32 * kk), idesc,
+                             (c > 0 || kk > 0) ? 1u : 0u);
+            tc::mma_commit(freed + s);
+            if (issued < nk) {   // refill this stage once its MMAs have read it
+                if (!(ok = tc::mbar_wait(freed + s, (c >> 1) & 1, kLimit))) break;
+                tc::mbar_expect_tx(full + s, ST);
+                tc::tma_load_2d(sm + s * ST, &mapA, full + s, k0 + issued * TC_BK, m0);
+                tc::tma_load_2d(sm + s * ST + SA, &mapB, full + s, k0 + issued * TC_BK, 0);
+                ++issued;
             }
         }
+        tc::mma_commit(done);
+        if (!ok) {
+            atomicExch(err, 1);
+            // let copies still in flight land before the CTA leaves (bounded)
+            for (int c = consumed; c < issued; ++c) (void)tc::mbar_wait(full + (c & 1), (c >> 1) & 1, kLimit);
+        }
+    }
+    const bool fin = tc::mbar_wait(done, 0, kLimit);
+    tc::fence_after_sync();
+    if (!fin) {
+        if (lane == 0) atomicExch(err, 2);
+    } else if (nk > 0) {
+        __syncwarp();   // tcgen05.ld is warp-collective
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (row >= M) continue;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int col = c0 + i;
+                if (col >= ncols) break;
+                float x = v[i];
+                if (ep & EP_BIAS) x += bias[col];
+                if (ep & EP_RELU) x = fmaxf(x, 0.f);
+                const size_t o = (ep & EP_TRANS) ? (size_t)col * ldo + row : (size_t)row * ldo + col;
+                if (ep & EP_ATOMIC) atomicAdd(out + o, x);
+                else if (!(ep & EP_NOSTORE)) out[o] = x;
+                if (ep & EP_BF16) outb[(size_t)row * ldb + col] = __float2bfloat16_rn(x);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tmem, tc_tmem_cols<BN>());
+}
+
+// ------------------------------------------------------------ BF16 operands
+
+// X [N x 16] FP32 -> Xb [N x 64] BF16 (columns 16..63 zero: the TMA box is
+// 64 wide) and its transpose XT [16 x ldt].
+__global__ void k_conv_x(const float *__restrict__ X, int N, __nv_bfloat16 *__restrict__ Xb) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)N * 64) return;
+    const int r = (int)(e / 64), k = (int)(e % 64);
+    Xb[e] = __float2bfloat16_rn(k < F ? X[(size_t)r * F + k] : 0.f);
+}
+
+// dst[c][r] = bf16(src[r][c]) for an FP32 [rows x cols] source (leading
+// dimension lds) into a BF16 [cols x ldd] destination, through 32 x 32
+// shared-memory tiles so that both sides are coalesced.
+__global__ void k_transpose_bf16(const float *__restrict__ src, int lds, int rows, int cols,
+                                 __nv_bfloat16 *__restrict__ dst, int ldd) {
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(size_t)r * lds + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) dst[(size_t)c * ldd + r] = __float2bfloat16_rn(tile[threadIdx.x][i]);
+    }
+}
+
+// FP32 [rows x cols] -> BF16, same layout
+__global__ void k_to_bf16(const float *__restrict__ src, size_t count, __nv_bfloat16 *__restrict__ dst) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < count) dst[e] = __float2bfloat16_rn(src[e]);
+}
+
+// BF16 copies of the weights, in the K-major layouts the products read:
+//   W1t [128 x 64]  = W1^T, K padded from 16 to 64 with zeros (layer 1)
+//   W2t [128 x 256] = W2^T                                      (layer 2)
+//   W2n [256 x 128] = W2                                        (dZ = dH2 W2^T)
+//   W3t [16 x 128]  = W3^T, rows 8..15 zero                     (layer 3)
+constexpr int WB_W1T = 0, WB_W2T = WB_W1T + H * 64, WB_W2N = WB_W2T + H * 2 * H, WB_W3T = WB_W2N + 2 * H * H,
+              WB_TOTAL = WB_W3T + 16 * H;
+__global__ void k_weights_bf16(const float *__restrict__ P, __nv_bfloat16 *__restrict__ wb) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < WB_TOTAL; e += gridDim.x * blockDim.x) {
+        float v;
+        if (e < WB_W2T) {
+            const int j = (e - WB_W1T) / 64, f = (e - WB_W1T) % 64;
+            v = f < F ? P[OFF_W1 + f * H + j] : 0.f;
+        } else if (e < WB_W2N) {
+            const int j = (e - WB_W2T) / (2 * H), i = (e - WB_W2T) % (2 * H);
+            v = P[OFF_W2 + i * H + j];
+        } else if (e < WB_W3T) {
+            v = P[OFF_W2 + (e - WB_W2N)];
+        } else {
+            const int o = (e - WB_W3T) / H, k = (e - WB_W3T) % H;
+            v = o < 8 ? P[OFF_W3 + k * 8 + o] : 0.f;
+        }
+        wb[e] = __float2bfloat16_rn(v);
     }
 }
 
@@ -277,13 +364,15 @@ __global__ void k_segment_mean(const float *__restrict__ Hm, const int *__restri
     ctx[(size_t)i * H + k] = r1 > r0 ? s / (float)(r1 - r0) : 0.f;
 }
 
-// Z[r] = [H1[r] ; ctx[segment of r]]
+// Z[r] = [H1[r] ; ctx[segment of r]], in FP32 and in BF16 (layer 2's operand)
 __global__ void k_concat(const float *__restrict__ H1, const float *__restrict__ ctx, const int *__restrict__ rowseg,
-                         int N, float *__restrict__ Z) {
+                         int N, float *__restrict__ Z, __nv_bfloat16 *__restrict__ Zb) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (size_t)N * 2 * H) return;
     const int r = (int)(e / (2 * H)), k = (int)(e % (2 * H));
-    Z[e] = k < H ? H1[(size_t)r * H + k] : ctx[(size_t)rowseg[r] * H + (k - H)];
+    const float v = k < H ? H1[(size_t)r * H + k] : ctx[(size_t)rowseg[r] * H + (k - H)];
+    Z[e] = v;
+    Zb[e] = __float2bfloat16_rn(v);
 }
 
 // row -> segment index
@@ -416,6 +505,15 @@ struct PredWorkspace {
     int *pop = nullptr, *seg = nullptr, *rowseg = nullptr;
     long long *prices = nullptr;   // la_solve_warm's predicted prices
     float *h_loss = nullptr;
+    // BF16 operands of the tensor-core products (row-major [rows x K], or
+    // transposed [K-dim x ldt] with ldt = cap_n rounded up to 64)
+    __nv_bfloat16 *Xb = nullptr, *Zb = nullptr, *H2b = nullptr, *dH2b = nullptr;
+    __nv_bfloat16 *XT = nullptr, *ZT = nullptr, *H2T = nullptr, *dYT = nullptr, *dH2T = nullptr, *dH1T = nullptr;
+    __nv_bfloat16 *wb = nullptr;   // BF16 weight copies (k_weights_bf16)
+    int *err = nullptr;            // set by a tensor-core kernel whose wait timed out
+    int *h_err = nullptr;
+    size_t ldt = 0;
+    int num_sms = 0;
 };
 
 std::mutex g_pmu;
@@ -430,17 +528,24 @@ bool grow(T *&p, size_t count) {
 
 la_status ensure_pws(PredWorkspace &w, size_t nrows, size_t ninst, int nmat) {
     if (!w.h_loss && cudaMallocHost(&w.h_loss, sizeof(float)) != cudaSuccess) return LA_ERR_NOMEM;
+    if (!w.h_err && cudaMallocHost(&w.h_err, sizeof(int)) != cudaSuccess) return LA_ERR_NOMEM;
     if (!w.grad && !grow(w.grad, NPARAM)) return LA_ERR_NOMEM;
     if (!w.loss && !grow(w.loss, 1)) return LA_ERR_NOMEM;
     if (!w.inst && !grow(w.inst, 4)) return LA_ERR_NOMEM;
+    if (!w.err && !grow(w.err, 1)) return LA_ERR_NOMEM;
+    if (!w.wb && !grow(w.wb, WB_TOTAL)) return LA_ERR_NOMEM;
     if (nrows > w.cap_n) {
         const size_t c = std::max(nrows, (size_t)1024);
+        const size_t t = (c + 63) / 64 * 64;
         if (!grow(w.feats, c * F) || !grow(w.H1, c * H) || !grow(w.Z, c * 2 * H) || !grow(w.H2, c * H) ||
             !grow(w.Y, c * 8) || !grow(w.dY, c * 8) || !grow(w.dH2, c * H) || !grow(w.dZ, c * 2 * H) ||
             !grow(w.dH1, c * H) || !grow(w.rowseg, c) || !grow(w.rowmin, c) || !grow(w.pop, c) ||
-            !grow(w.colbuf, c * 5) || !grow(w.prices, c))
+            !grow(w.colbuf, c * 5) || !grow(w.prices, c) || !grow(w.Xb, c * 64) || !grow(w.Zb, c * 2 * H) ||
+            !grow(w.H2b, c * H) || !grow(w.dH2b, c * H) || !grow(w.XT, F * t) || !grow(w.ZT, 2 * H * t) ||
+            !grow(w.H2T, H * t) || !grow(w.dYT, 8 * t) || !grow(w.dH2T, H * t) || !grow(w.dH1T, H * t))
             return LA_ERR_NOMEM;
         w.cap_n = c;
+        w.ldt = t;
         // column-pass partials for a single matrix of this size
         if (!grow(w.part, c * 5 * (size_t)((c + 255) / 256))) return LA_ERR_NOMEM;
     }
@@ -453,15 +558,72 @@ la_status ensure_pws(PredWorkspace &w, size_t nrows, size_t ninst, int nmat) {
     return LA_OK;
 }
 
-cudaError_t gemm(cudaStream_t s, const float *A, int lda, int transA, const float *B, int ldb, int transB,
-                 float *C, int ldc, int M, int N, int K, int epi, const float *bias, int splits = 1) {
-    splits = std::max(1, std::min(splits, (K + TK - 1) / TK));
-    int kps = (K + splits - 1) / splits;
-    kps = ((kps + TK - 1) / TK) * TK;
-    splits = (K + kps - 1) / kps;
-    dim3 grid((M + TM - 1) / TM, (N + TN - 1) / TN, splits);
-    k_gemm<<<grid, 128, 0, s>>>(A, lda, transA, B, ldb, transB, C, ldc, M, N, K, epi, bias, kps);
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link
+// against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a K-major BF16 matrix [rows x k] with row pitch ld
+// elements (a multiple of 8): boxes of 64 x box_rows, 128-byte swizzle,
+// zeros outside the matrix.
+bool kmajor_map(CUtensorMap *m, const __nv_bfloat16 *ptr, int k, int rows, size_t ld, int box_rows) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || k <= 0 || rows <= 0 || (ld * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1u, 1u};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(ptr), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// C[M x N] = A[M x K] * B[N x K]^T on the tensor cores (k_tc_gemm): A with
+// row pitch lda, B with row pitch ldbm (elements), split over K in `splits`
+// parts (EP_ATOMIC then adds the partial products).
+template <int BN>
+cudaError_t tc_gemm(cudaStream_t s, const __nv_bfloat16 *A, size_t lda, const __nv_bfloat16 *B, size_t ldbm,
+                    int bn_rows, int M, int K, int splits, float *out, int ldo, int ncols, __nv_bfloat16 *outb,
+                    int ldb, const float *bias, int ep, int *err, int kext = 0) {
+    // kext: the stored K extent when the rows are padded beyond K (zeros)
+    CUtensorMap ma, mb;
+    const int ke = std::max(K, kext);
+    if (!kmajor_map(&ma, A, ke, M, lda, TC_BM) || !kmajor_map(&mb, B, ke, bn_rows, ldbm, BN))
+        return cudaErrorInvalidValue;
+    const int chunks = (K + TC_BK - 1) / TC_BK;
+    splits = std::max(1, std::min(splits, chunks));
+    const int cps = (chunks + splits - 1) / splits;   // chunks per split; no split is left empty
+    splits = (chunks + cps - 1) / cps;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes<BN>());
+    if (e != cudaSuccess) return e;
+    dim3 grid((M + TC_BM - 1) / TC_BM, splits);
+    k_tc_gemm<BN><<<grid, TC_THREADS, tc_smem_bytes<BN>(), s>>>(ma, mb, M, K, cps * TC_BK, out, ldo, ncols, outb, ldb,
+                                                                 bias, ep, err);
     return cudaGetLastError();
+}
+
+// split count for a product whose K is the row count N (weight gradients)
+int k_splits(int N, int mtiles, int num_sms) {
+    return std::max(1, std::min((N + TC_BK - 1) / TC_BK / 2, 2 * num_sms / std::max(1, mtiles)));
+}
+
+inline void transpose(cudaStream_t s, const float *src, int lds, int rows, int cols, __nv_bfloat16 *dst, size_t ldd) {
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    k_transpose_bf16<<<grid, dim3(32, 8), 0, s>>>(src, lds, rows, cols, dst, (int)ldd);
 }
 
 // features of one n x n matrix into feats (n rows of F) and inst
@@ -479,31 +641,58 @@ la_status features_one(cudaStream_t s, const int32_t *C, int n, PredWorkspace &w
 // forward over N rows in I segments; Y [N x 8] (column 0 is the output)
 cudaError_t forward(cudaStream_t s, const float *P, const float *X, int N, int I, const int *seg, PredWorkspace &w) {
     cudaError_t e;
+    k_weights_bf16<<<64, 256, 0, s>>>(P, w.wb);
+    k_conv_x<<<(unsigned)(((size_t)N * 64 + 255) / 256), 256, 0, s>>>(X, N, w.Xb);
     k_rowseg<<<I, 256, 0, s>>>(seg, I, w.rowseg);
-    if ((e = gemm(s, X, F, 0, P + OFF_W1, H, 0, w.H1, H, N, H, F, EPI_BIAS_RELU, P + OFF_B1)) != cudaSuccess) return e;
+    // layer 1: H1 = relu(X W1 + b1)   (K = 16 real features)
+    if ((e = tc_gemm<128>(s, w.Xb, 64, w.wb + WB_W1T, 64, H, N, F, 1, w.H1, H, H, nullptr, 0, P + OFF_B1,
+                          EP_BIAS | EP_RELU, w.err, 64)) != cudaSuccess)
+        return e;
     k_segment_mean<<<I, H, 0, s>>>(w.H1, seg, w.ctx);
-    k_concat<<<(unsigned)(((size_t)N * 2 * H + 255) / 256), 256, 0, s>>>(w.H1, w.ctx, w.rowseg, N, w.Z);
-    if ((e = gemm(s, w.Z, 2 * H, 0, P + OFF_W2, H, 0, w.H2, H, N, H, 2 * H, EPI_BIAS_RELU, P + OFF_B2)) != cudaSuccess) return e;
-    if ((e = gemm(s, w.H2, H, 0, P + OFF_W3, 8, 0, w.Y, 8, N, 8, H, EPI_BIAS, P + OFF_B3)) != cudaSuccess) return e;
+    k_concat<<<(unsigned)(((size_t)N * 2 * H + 255) / 256), 256, 0, s>>>(w.H1, w.ctx, w.rowseg, N, w.Z, w.Zb);
+    // layer 2: H2 = relu(Z W2 + b2), also in BF16 for layer 3
+    if ((e = tc_gemm<128>(s, w.Zb, 2 * H, w.wb + WB_W2T, 2 * H, H, N, 2 * H, 1, w.H2, H, H, w.H2b, H, P + OFF_B2,
+                          EP_BIAS | EP_RELU | EP_BF16, w.err)) != cudaSuccess)
+        return e;
+    // layer 3: Y = H2 W3 + b3 (8 outputs; the MMA's N is 16)
+    if ((e = tc_gemm<16>(s, w.H2b, H, w.wb + WB_W3T, H, 16, N, H, 1, w.Y, 8, 8, nullptr, 0, P + OFF_B3, EP_BIAS,
+                         w.err)) != cudaSuccess)
+        return e;
     return cudaGetLastError();
 }
 
 // backward from dY into w.grad (zeroed here)
-cudaError_t backward(cudaStream_t s, const float *P, const float *X, int N, int I, const int *seg, PredWorkspace &w) {
+cudaError_t backward(cudaStream_t s, const float *P, const float *X, int N, int I, const int *seg, PredWorkspace &w,
+                     int num_sms) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.grad, 0, sizeof(float) * NPARAM, s)) != cudaSuccess) return e;
-    const int splits = std::max(1, std::min(64, N / 1024));
+    const size_t ldt = w.ldt;
     // layer 3: dW3 = H2^T dY, db3 = sum dY
-    if ((e = gemm(s, w.H2, H, 1, w.dY, 8, 0, w.grad + OFF_W3, 8, H, 8, N, EPI_ATOMIC, nullptr, splits)) != cudaSuccess) return e;
+    transpose(s, w.H2, H, N, H, w.H2T, ldt);
+    transpose(s, w.dY, 8, N, 8, w.dYT, ldt);
+    if ((e = tc_gemm<16>(s, w.H2T, ldt, w.dYT, ldt, 8, H, N, k_splits(N, 1, num_sms), w.grad + OFF_W3, 8, 8,
+                         nullptr, 0, nullptr, EP_ATOMIC, w.err)) != cudaSuccess)
+        return e;
     k_colsum<<<1, dim3(32, 8), 0, s>>>(w.dY, 8, N, 8, w.grad + OFF_B3);
     k_dh2<<<(unsigned)(((size_t)N * H + 255) / 256), 256, 0, s>>>(w.dY, 8, P + OFF_W3, w.H2, N, w.dH2);
     // layer 2: dW2 = Z^T dH2, db2, dZ = dH2 W2^T
-    if ((e = gemm(s, w.Z, 2 * H, 1, w.dH2, H, 0, w.grad + OFF_W2, H, 2 * H, H, N, EPI_ATOMIC, nullptr, splits)) != cudaSuccess) return e;
+    transpose(s, w.Z, 2 * H, N, 2 * H, w.ZT, ldt);
+    transpose(s, w.dH2, H, N, H, w.dH2T, ldt);
+    k_to_bf16<<<(unsigned)(((size_t)N * H + 255) / 256), 256, 0, s>>>(w.dH2, (size_t)N * H, w.dH2b);
+    if ((e = tc_gemm<128>(s, w.ZT, ldt, w.dH2T, ldt, H, 2 * H, N, k_splits(N, 2, num_sms), w.grad + OFF_W2, H, H,
+                          nullptr, 0, nullptr, EP_ATOMIC, w.err)) != cudaSuccess)
+        return e;
     k_colsum<<<H / 8, dim3(32, 8), 0, s>>>(w.dH2, H, N, H, w.grad + OFF_B2);
-    if ((e = gemm(s, w.dH2, H, 0, P + OFF_W2, H, 1, w.dZ, 2 * H, N, 2 * H, H, EPI_STORE, nullptr)) != cudaSuccess) return e;
-    // pooling and layer 1
+    if ((e = tc_gemm<256>(s, w.dH2b, H, w.wb + WB_W2N, H, 2 * H, N, H, 1, w.dZ, 2 * H, 2 * H, nullptr, 0, nullptr, 0,
+                          w.err)) != cudaSuccess)
+        return e;
+    // pooling and layer 1: dW1^T = dH1^T X (stored transposed into W1's slots)
     k_dh1<<<I, H, 0, s>>>(w.dZ, w.H1, seg, w.dH1);
-    if ((e = gemm(s, X, F, 1, w.dH1, H, 0, w.grad + OFF_W1, H, F, H, N, EPI_ATOMIC, nullptr, splits)) != cudaSuccess) return e;
+    transpose(s, w.dH1, H, N, H, w.dH1T, ldt);
+    transpose(s, X, F, N, F, w.XT, ldt);
+    if ((e = tc_gemm<16>(s, w.dH1T, ldt, w.XT, ldt, F, H, N, k_splits(N, 1, num_sms), w.grad + OFF_W1, H, F, nullptr,
+                         0, nullptr, EP_ATOMIC | EP_TRANS, w.err)) != cudaSuccess)
+        return e;
     k_colsum<<<H / 8, dim3(32, 8), 0, s>>>(w.dH1, H, N, H, w.grad + OFF_B1);
     return cudaGetLastError();
 }
@@ -525,7 +714,21 @@ static la_status get_ws(PredWorkspace *&w, size_t nrows, size_t ninst) {
     if (cudaGetDevice(&dev) != cudaSuccess) return LA_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return LA_ERR_INVALID;
     w = &g_pws[dev];
+    if (!w->num_sms && cudaDeviceGetAttribute(&w->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return LA_ERR_CUDA;
+    if (!encode_tiled()) return LA_ERR_CUDA;   // the driver offers no TMA tensor maps
     return ensure_pws(*w, nrows, ninst, 1);
+}
+
+// The tensor-core kernels' error flag: cleared before a call's kernels,
+// read after them (LA_ERR_INTERNAL if a bounded wait gave up).
+static la_status clear_err(PredWorkspace &w, cudaStream_t s) {
+    return cudaMemsetAsync(w.err, 0, sizeof(int), s) == cudaSuccess ? LA_OK : LA_ERR_CUDA;
+}
+static la_status read_err(PredWorkspace &w, cudaStream_t s) {
+    if (cudaMemcpyAsync(w.h_err, w.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LA_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LA_ERR_CUDA;
+    return *w.h_err ? LA_ERR_INTERNAL : LA_OK;
 }
 
 static la_status check_header(const float *params, cudaStream_t s) {
@@ -557,11 +760,11 @@ la_status la_predictor_forward(const float *params, const float *feats, const in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PredWorkspace *w = nullptr;
     if (la_status e = get_ws(w, N, I)) return e;
+    if (la_status e = clear_err(*w, s)) return e;
     LA_PCK(forward(s, params, feats, N, I, seg, *w));
     LA_PCK(cudaMemcpy2DAsync(y_out, sizeof(float), w->Y, 8 * sizeof(float), sizeof(float), N,
                              cudaMemcpyDeviceToDevice, s));
-    LA_PCK(cudaStreamSynchronize(s));
-    return LA_OK;
+    return read_err(*w, s);
 }
 
 la_status la_predictor_train_step(float *params, float *adam_m, float *adam_v, const float *feats,
@@ -573,11 +776,12 @@ la_status la_predictor_train_step(float *params, float *adam_m, float *adam_v, c
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PredWorkspace *w = nullptr;
     if (la_status e = get_ws(w, N, I)) return e;
+    if (la_status e = clear_err(*w, s)) return e;
     LA_PCK(cudaMemsetAsync(w->loss, 0, sizeof(float), s));
     LA_PCK(forward(s, params, feats, N, I, seg, *w));
     LA_PCK(cudaMemsetAsync(w->dY, 0, sizeof(float) * 8 * (size_t)N, s));
     k_loss_grad<<<I, 256, 0, s>>>(w->Y, 8, targets, seg, I, w->dY, 8, w->loss);
-    LA_PCK(backward(s, params, feats, N, I, seg, *w));
+    LA_PCK(backward(s, params, feats, N, I, seg, *w, w->num_sms));
     if (grad_out) LA_PCK(cudaMemcpyAsync(grad_out, w->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, s));
     if (adam_m && adam_v && lr > 0.f) {
         const float b1 = 0.9f, b2 = 0.999f;
@@ -586,7 +790,7 @@ la_status la_predictor_train_step(float *params, float *adam_m, float *adam_v, c
                                                    c1, c2, weight_decay);
     }
     LA_PCK(cudaMemcpyAsync(w->h_loss, w->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
-    LA_PCK(cudaStreamSynchronize(s));
+    if (la_status e = read_err(*w, s)) return e;
     if (loss_out) *loss_out = *w->h_loss;
     return LA_OK;
 }
@@ -606,6 +810,7 @@ la_status la_predict_prices_ex(const int32_t *cost, int32_t n, const void *weigh
     if (la_status e = get_ws(w, n, 1)) return e;
     if (la_status e = features_one(s, cost, n, *w, w->feats, w->inst)) return e;
     const int seg_h[2] = {0, n};
+    if (la_status e = clear_err(*w, s)) return e;
     LA_PCK(cudaMemcpyAsync(w->seg, seg_h, sizeof(seg_h), cudaMemcpyHostToDevice, s));
     LA_PCK(forward(s, P, w->feats, n, 1, w->seg, *w));
     k_prices<<<1, 1024, 0, s>>>(w->Y, 8, n, w->inst, reinterpret_cast<long long *>(prices_out));
@@ -613,7 +818,7 @@ la_status la_predict_prices_ex(const int32_t *cost, int32_t n, const void *weigh
     float inst_h[2] = {0, 0}, calib[2] = {0, 0};
     LA_PCK(cudaMemcpyAsync(inst_h, w->inst, sizeof(inst_h), cudaMemcpyDeviceToHost, s));
     LA_PCK(cudaMemcpyAsync(calib, P + 4, sizeof(calib), cudaMemcpyDeviceToHost, s));
-    LA_PCK(cudaStreamSynchronize(s));
+    if (la_status e = read_err(*w, s)) return e;
     if (eps0_out) {
         // eps0 = (n+1) * T * (calibrated error quantile), at least 1
         const double e = (double)(n + 1) * (double)inst_h[0] * (double)calib[0];
