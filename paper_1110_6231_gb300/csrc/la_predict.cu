@@ -102,7 +102,8 @@ __global__ void k_col_stats(const int32_t *__restrict__ C, int n, const float *_
 // unit), inst[1] = mean of the column minima.
 __global__ void __launch_bounds__(1024)
 k_features(int n, int rb, const float *__restrict__ part, const int *__restrict__ pop,
-           float *__restrict__ colbuf, float *__restrict__ feats, float *__restrict__ inst) {
+           float *__restrict__ colbuf, float *__restrict__ feats, float *__restrict__ inst,
+           __nv_bfloat16 *__restrict__ xb) {
     __shared__ float red[4][32];
     __shared__ float s_mean[4];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -167,6 +168,10 @@ k_features(int n, int rb, const float *__restrict__ part, const int *__restrict_
         f[6] = lt;
         f[7] = ln;
         for (int k = 8; k < F; ++k) f[k] = 0.f;
+        if (xb) {   // layer 1's operand: BF16, rows padded to the 64-wide TMA box
+            __nv_bfloat16 *o = xb + (size_t)y * 64;
+            for (int k = 0; k < 64; ++k) o[k] = __float2bfloat16_rn(k < 8 ? f[k] : 0.f);
+        }
     }
 }
 
@@ -353,6 +358,211 @@ __global__ void k_weights_bf16(const float *__restrict__ P, __nv_bfloat16 *__res
     }
 }
 
+// ------------------------------------------------------------ fused inference
+
+// The whole network for one instance in one launch, on one CTA of 128
+// threads: layer 1, the set pooling, layers 2 and 3 and the rounding of
+// the predicted prices. Every product runs on tcgen05 with operands in
+// shared memory and FP32 accumulators in TMEM:
+//   pass 1, per 128-row tile: X (TMA) * W1^T -> relu(+ b1) = H1; H1 goes
+//     to global memory in BF16 and its column sums to shared memory;
+//   the pooled context enters layer 2 as a bias: [H1 ; c] W2 = H1 W2_top +
+//     c W2_bottom, so b2' = b2 + c W2_bottom is formed once (CUDA cores,
+//     BF16 operands and FP32 sums, as the products round them);
+//   pass 2, per tile: H1 (TMA) * W2_top^T -> relu(+ b2') = H2, written into
+//     shared memory in the swizzled K-major layout the next MMA reads;
+//     H2 * W3^T + b3 = y (TMEM columns 128..143);
+//   prices: p_j = round((n+1) T (y_j - max y)), the paper's sign with
+//     max 0 (a uniform shift of all prices changes nothing).
+// Shared memory (1024-aligned): W1^T 16 KB, W2_top^T 2 x 16 KB, W3^T
+// 2 x 2 KB, X tile 16 KB, H1 tile 2 x 16 KB, H2 tile 2 x 16 KB.
+constexpr int INF_W1 = 0, INF_W2 = INF_W1 + 16384, INF_W3 = INF_W2 + 32768, INF_X = INF_W3 + 4096,
+              INF_H1 = INF_X + 16384, INF_H2 = INF_H1 + 32768, INF_BYTES = INF_H2 + 32768;
+constexpr int INF_SMEM = 1024 + INF_BYTES + 2048;
+
+__device__ __forceinline__ int float_order(float x) {   // order-preserving float -> int
+    const int i = __float_as_int(x);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float order_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__global__ void __launch_bounds__(TC_THREADS)
+k_infer(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapW1,
+        const __grid_constant__ CUtensorMap mapH1, const __grid_constant__ CUtensorMap mapW2,
+        const __grid_constant__ CUtensorMap mapW3, const float *__restrict__ P, const __nv_bfloat16 *__restrict__ wb,
+        int n, const float *__restrict__ inst, __nv_bfloat16 *__restrict__ h1g, float *__restrict__ Y,
+        long long *__restrict__ prices, int *__restrict__ err) {
+    extern __shared__ uint8_t in_raw[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t raw = tc::smem_addr(in_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *sm = in_raw + (base - raw);
+    float *colsum = reinterpret_cast<float *>(sm + INF_BYTES);          // [128]
+    float *bias2 = colsum + H;                                           // [128]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(bias2 + H);            // weights, X, H1, MMA
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
+    int *ymax = reinterpret_cast<int *>(tslot + 1);
+    constexpr unsigned long long kLimit = 1000000000ull;
+    const int tiles = (n + TC_BM - 1) / TC_BM;
+
+    if (warp == 0) tc::tmem_alloc(tslot, 256);
+    colsum[tid] = 0.f;
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) tc::mbar_init(bars + i, 1);
+        *ymax = float_order(-INFINITY);
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    int ok = 1;                     // thread 0's view; shared through s_ok below
+    __shared__ int s_ok;
+    uint32_t mph = 0;               // MMA barrier phase (every thread waits on every use)
+    if (tid == 0) {
+        s_ok = 1;
+        tc::mbar_expect_tx(bars + 0, 16384 + 32768 + 4096);
+        tc::tma_load_2d(sm + INF_W1, &mapW1, bars + 0, 0, 0);
+        tc::tma_load_2d(sm + INF_W2, &mapW2, bars + 0, 0, 0);
+        tc::tma_load_2d(sm + INF_W2 + 16384, &mapW2, bars + 0, 64, 0);
+        tc::tma_load_2d(sm + INF_W3, &mapW3, bars + 0, 0, 0);
+        tc::tma_load_2d(sm + INF_W3 + 2048, &mapW3, bars + 0, 64, 0);
+        ok = tc::mbar_wait(bars + 0, 0, kLimit);
+    }
+    // MMA issue by thread 0, completion seen by everyone (bounded)
+    auto wait_mma = [&]() {
+        const bool d = tc::mbar_wait(bars + 3, mph, kLimit);
+        mph ^= 1;
+        if (!d) atomicExch(&s_ok, 0);
+        tc::fence_after_sync();
+    };
+    const float *b1 = P + OFF_B1, *b2 = P + OFF_B2, *b3 = P + OFF_B3;
+
+    // pass 1: layer 1 and the column sums of H1
+    for (int t = 0; t < tiles; ++t) {
+        if (tid == 0) {
+            if (ok) {
+                tc::mbar_expect_tx(bars + 1, 16384);
+                tc::tma_load_2d(sm + INF_X, &mapX, bars + 1, 0, t * TC_BM);
+                ok = tc::mbar_wait(bars + 1, t & 1, kLimit);
+            }
+            if (ok) {
+                tc::fence_after_sync();
+                tc::mma_bf16(tmem, tc::desc_k128(base + INF_X), tc::desc_k128(base + INF_W1), tc::idesc_bf16(TC_BM, H), 0u);
+            }
+            tc::mma_commit(bars + 3);   // arrives at once when nothing was issued
+            if (!ok) s_ok = 0;
+        }
+        wait_mma();
+        __syncwarp();
+        const int row = t * TC_BM + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < H; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float h = row < n ? fmaxf(v[i] + b1[c0 + i], 0.f) : 0.f;
+                if (row < n) h1g[(size_t)row * H + c0 + i] = __float2bfloat16_rn(h);
+                float sum = h;
+                for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                if (lane == 0) atomicAdd(colsum + c0 + i, sum);
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    // H1 is read back by TMA (the async proxy) in pass 2
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    // the pooled context as a bias of layer 2: b2'[j] = b2[j] + sum_i bf16(c_i) W2[128 + i][j]
+    {
+        const __nv_bfloat16 *w2b = wb + WB_W2N + (size_t)H * H;   // rows 128..255 of W2
+        float acc = b2[tid];
+        for (int i = 0; i < H; ++i)
+            acc += __bfloat162float(__float2bfloat16_rn(colsum[i] / (float)n)) * __bfloat162float(w2b[(size_t)i * H + tid]);
+        bias2[tid] = acc;
+    }
+    __syncthreads();
+
+    // pass 2: layers 2 and 3
+    for (int t = 0; t < tiles; ++t) {
+        if (tid == 0) {
+            if (ok) {
+                tc::mbar_expect_tx(bars + 2, 32768);
+                tc::tma_load_2d(sm + INF_H1, &mapH1, bars + 2, 0, t * TC_BM);
+                tc::tma_load_2d(sm + INF_H1 + 16384, &mapH1, bars + 2, 64, t * TC_BM);
+                ok = tc::mbar_wait(bars + 2, t & 1, kLimit);
+            }
+            if (ok) {
+                tc::fence_after_sync();
+                for (int ch = 0; ch < 2; ++ch)
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc::mma_bf16(tmem, tc::desc_k128(base + INF_H1 + ch * 16384 + 32 * kk),
+                                     tc::desc_k128(base + INF_W2 + ch * 16384 + 32 * kk), tc::idesc_bf16(TC_BM, H),
+                                     (ch | kk) ? 1u : 0u);
+            }
+            tc::mma_commit(bars + 3);
+            if (!ok) s_ok = 0;
+        }
+        wait_mma();
+        __syncwarp();
+        const int r = warp * 32 + lane;   // row within the tile
+#pragma unroll 1
+        for (int c0 = 0; c0 < H; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            uint32_t p[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const __nv_bfloat162 pr = __floats2bfloat162_rn(fmaxf(v[2 * i] + bias2[c0 + 2 * i], 0.f),
+                                                                 fmaxf(v[2 * i + 1] + bias2[c0 + 2 * i + 1], 0.f));
+                p[i] = *reinterpret_cast<const uint32_t *>(&pr);
+            }
+            // K-major, 128-byte swizzle: 16-byte unit u of row r sits at unit u ^ (r % 8)
+            const int ch = c0 / 64, u = (c0 % 64) / 8;
+            uint8_t *rowp = sm + INF_H2 + ch * 16384 + r * 128;
+            *reinterpret_cast<uint4 *>(rowp + ((u ^ (r & 7)) * 16)) = make_uint4(p[0], p[1], p[2], p[3]);
+            *reinterpret_cast<uint4 *>(rowp + (((u + 1) ^ (r & 7)) * 16)) = make_uint4(p[4], p[5], p[6], p[7]);
+        }
+        tc::fence_proxy_async();   // H2 written by this thread, read next by the MMA (async proxy)
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            if (ok)
+                for (int ch = 0; ch < 2; ++ch)
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc::mma_bf16(tmem + 128, tc::desc_k128(base + INF_H2 + ch * 16384 + 32 * kk),
+                                     tc::desc_k128(base + INF_W3 + ch * 2048 + 32 * kk), tc::idesc_bf16(TC_BM, 16),
+                                     (ch | kk) ? 1u : 0u);
+            tc::mma_commit(bars + 3);
+        }
+        wait_mma();
+        __syncwarp();
+        {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 128u, v);
+            const int row = t * TC_BM + r;
+            const float y = v[0] + b3[0];
+            int m = row < n ? float_order(y) : float_order(-INFINITY);
+            if (row < n) Y[row] = y;
+            m = __reduce_max_sync(0xffffffffu, m);
+            if (lane == 0) atomicMax(ymax, m);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    // prices in the paper's sign, max 0 (a uniform shift changes nothing)
+    const double top = (double)order_float(*ymax), T = inst[0];
+    for (int j = tid; j < n; j += TC_THREADS) prices[j] = (long long)llround(((double)Y[j] - top) * T * (double)(n + 1));
+    if (tid == 0 && !s_ok) atomicExch(err, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tmem, 256);
+}
+
 // ------------------------------------------------------------ set pooling and glue
 
 // ctx[i][:] = mean over the rows of segment i of H1 (seg: [I+1] row offsets).
@@ -466,30 +676,6 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
     m[i] = mi;
     v[i] = vi;
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-}
-
-// prices_out[j] = round(-(n+1) * (T * y_j)) shifted so that max = 0 (paper
-// sign; a uniform shift of all prices changes nothing).
-__global__ void k_prices(const float *__restrict__ Y, int ldy, int n, const float *__restrict__ inst,
-                         long long *__restrict__ prices) {
-    __shared__ float red[32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float mx = -INFINITY;
-    for (int j = tid; j < n; j += blockDim.x) mx = fmaxf(mx, Y[(size_t)j * ldy]);
-    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) red[warp] = mx;
-    __syncthreads();
-    if (tid == 0) {
-        float t = -INFINITY;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
-        red[0] = t;
-    }
-    __syncthreads();
-    const double T = inst[0], top = red[0];
-    for (int j = tid; j < n; j += blockDim.x) {
-        const double v = ((double)Y[(size_t)j * ldy] - top) * T;   // <= 0, cost units
-        prices[j] = (long long)llround(v * (double)(n + 1));
-    }
 }
 
 // ------------------------------------------------------------ host side
@@ -627,14 +813,15 @@ inline void transpose(cudaStream_t s, const float *src, int lds, int rows, int c
 }
 
 // features of one n x n matrix into feats (n rows of F) and inst
-la_status features_one(cudaStream_t s, const int32_t *C, int n, PredWorkspace &w, float *feats, float *inst) {
+la_status features_one(cudaStream_t s, const int32_t *C, int n, PredWorkspace &w, float *feats, float *inst,
+                       __nv_bfloat16 *xb = nullptr) {
     if (cudaMemsetAsync(w.pop, 0, sizeof(int) * n, s) != cudaSuccess) return LA_ERR_CUDA;
     k_row_stats<<<(n * 32 + 255) / 256, 256, 0, s>>>(C, n, w.rowmin, w.pop);
     const int rpb = 256;
     const int rb = (n + rpb - 1) / rpb;
     dim3 grid((n + 127) / 128, rb);
     k_col_stats<<<grid, 128, 0, s>>>(C, n, w.rowmin, w.part, rpb);
-    k_features<<<1, 1024, 0, s>>>(n, rb, w.part, w.pop, w.colbuf, feats, inst);
+    k_features<<<1, 1024, 0, s>>>(n, rb, w.part, w.pop, w.colbuf, feats, inst, xb);
     return cudaGetLastError() == cudaSuccess ? LA_OK : LA_ERR_CUDA;
 }
 
@@ -808,12 +995,20 @@ la_status la_predict_prices_ex(const int32_t *cost, int32_t n, const void *weigh
     std::lock_guard<std::mutex> lock(g_pmu);
     PredWorkspace *w = nullptr;
     if (la_status e = get_ws(w, n, 1)) return e;
-    if (la_status e = features_one(s, cost, n, *w, w->feats, w->inst)) return e;
-    const int seg_h[2] = {0, n};
     if (la_status e = clear_err(*w, s)) return e;
-    LA_PCK(cudaMemcpyAsync(w->seg, seg_h, sizeof(seg_h), cudaMemcpyHostToDevice, s));
-    LA_PCK(forward(s, P, w->feats, n, 1, w->seg, *w));
-    k_prices<<<1, 1024, 0, s>>>(w->Y, 8, n, w->inst, reinterpret_cast<long long *>(prices_out));
+    // features (three launches; the last also writes layer 1's BF16 operand),
+    // the BF16 weights, then the whole network and the price rounding in one
+    // launch (k_infer)
+    if (la_status e = features_one(s, cost, n, *w, w->feats, w->inst, w->Xb)) return e;
+    k_weights_bf16<<<64, 256, 0, s>>>(P, w->wb);
+    CUtensorMap mx, mw1, mh1, mw2, mw3;
+    if (!kmajor_map(&mx, w->Xb, 64, n, 64, TC_BM) || !kmajor_map(&mw1, w->wb + WB_W1T, 64, H, 64, TC_BM) ||
+        !kmajor_map(&mh1, w->H2b, H, n, H, TC_BM) || !kmajor_map(&mw2, w->wb + WB_W2T, 2 * H, H, 2 * H, TC_BM) ||
+        !kmajor_map(&mw3, w->wb + WB_W3T, H, 16, H, 16))
+        return LA_ERR_CUDA;
+    LA_PCK(cudaFuncSetAttribute(k_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, INF_SMEM));
+    k_infer<<<1, TC_THREADS, INF_SMEM, s>>>(mx, mw1, mh1, mw2, mw3, P, w->wb, n, w->inst, w->H2b, w->Y,
+                                             reinterpret_cast<long long *>(prices_out), w->err);
     LA_PCK(cudaGetLastError());
     float inst_h[2] = {0, 0}, calib[2] = {0, 0};
     LA_PCK(cudaMemcpyAsync(inst_h, w->inst, sizeof(inst_h), cudaMemcpyDeviceToHost, s));

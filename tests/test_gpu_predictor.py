@@ -136,6 +136,28 @@ def test_training_fits_a_simple_target(la):
     assert loss.value < 0.1 * first
 
 
+@pytest.mark.parametrize("kind,n", [("uniform", 1), ("geometric", 77), ("uniform", 128), ("geometric", 129),
+                                    ("geometric", 1000), ("uniform", 2049)])
+def test_fused_inference_matches_oracle(la, kind, n):
+    """la_predict_prices runs the three layers, the pooling and the price
+    rounding in one tcgen05 kernel. Its prices must be those of the
+    oracle's forward pass with BF16 operands, round((n+1) T (y - max y)),
+    within twice the forward test's FP32-accumulation bound (y and max y
+    each within 5e-3 of the range of y) plus one for the rounding, on
+    partial and whole tiles."""
+    import torch
+    P = _params(9)
+    C = synth.uniform_costs(n, 0, 5000, n) if kind == "uniform" else synth.geometric_costs(n, n)
+    prices, eps0 = la.predict_prices(_dev(C, np.int32), _dev(P, np.float32))
+    X, T = se.features(C)
+    y = se.forward(P.astype(np.float32).astype(np.float64), X, np.array([0, n]), quant=True)
+    ref = (y - y.max()) * T * (n + 1)
+    got = prices.cpu().numpy().astype(np.float64)
+    scale = max(1.0, (np.abs(y).max() + 1e-9) * T * (n + 1))
+    assert np.abs(got - ref).max() <= 1e-2 * scale + 1, (np.abs(got - ref).max(), scale)
+    assert int(prices.max()) == 0 or n == 1
+
+
 @pytest.mark.parametrize("kind,n", [("geometric", 100), ("uniform", 300), ("geometric", 1000)])
 def test_warm_solve_is_exact_with_any_weights(la, kind, n):
     import torch
