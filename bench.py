@@ -604,8 +604,9 @@ def bench_warm(args, la, synth, dev):
     for n, cnt in ((1024, args.warm_n1024), (8192, args.warm_n8192)):
         if cnt <= 0:
             continue
-        tc = tw = 0.0
+        tc = tw = tp = 0.0
         sc = sw = 0
+        stream = torch.cuda.current_stream(dev)
         for s in range(cnt):
             C = torch.from_numpy(synth.geometric_costs(n, 2_000_000 + s)).to(dev)
             if s == 0:
@@ -621,12 +622,21 @@ def bench_warm(args, la, synth, dev):
             t2 = time.perf_counter()
             if warm.cost != cold.cost:
                 raise RuntimeError("warm and cold costs differ")
+            # the predictor alone (features, BF16 weights, the fused network
+            # launch), timed by CUDA events on the stream it runs on
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            la.predict_prices(C, P)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            tp += e0.elapsed_time(e1)
             tc += t1 - t0
             tw += t2 - t1
             sc += cold.stats["scans"]
             sw += warm.stats["scans"]
         out[f"n{n}"] = {"instances": cnt, "cold_ms": 1e3 * tc / cnt, "warm_ms": 1e3 * tw / cnt,
                         "speedup": tc / tw, "cold_scans": sc / cnt, "warm_scans": sw / cnt,
+                        "predictor_ms": tp / cnt, "predictor_share_of_warm": (tp / cnt) / (1e3 * tw / cnt),
                         "identical_cost": True, "warm_includes": "features + set encoder + solve"}
     return out
 

@@ -77,6 +77,8 @@ __global__ void k_row_stats(const int32_t *__restrict__ C, int n, float *__restr
     }
 }
 
+constexpr int kColBlocks = 64;   // row blocks of the column pass (partials merged by k_features)
+
 // Column pass over a block of rows: per column, min and second min of C and
 // of the row-reduced C - rowmin, and the sum. Partials [rb][n][5].
 __global__ void k_col_stats(const int32_t *__restrict__ C, int n, const float *__restrict__ rowmin,
@@ -168,9 +170,12 @@ k_features(int n, int rb, const float *__restrict__ part, const int *__restrict_
         f[6] = lt;
         f[7] = ln;
         for (int k = 8; k < F; ++k) f[k] = 0.f;
-        if (xb) {   // layer 1's operand: BF16, rows padded to the 64-wide TMA box
-            __nv_bfloat16 *o = xb + (size_t)y * 64;
-            for (int k = 0; k < 64; ++k) o[k] = __float2bfloat16_rn(k < 8 ? f[k] : 0.f);
+    }
+    if (xb) {   // layer 1's operand: BF16, rows padded to the 64-wide TMA box (coalesced)
+        __syncthreads();
+        for (int e = tid; e < n * 64; e += blockDim.x) {
+            const int y = e >> 6, k = e & 63;
+            xb[e] = __float2bfloat16_rn(k < 8 ? feats[(size_t)y * F + k] : 0.f);
         }
     }
 }
@@ -360,25 +365,30 @@ __global__ void k_weights_bf16(const float *__restrict__ P, __nv_bfloat16 *__res
 
 // ------------------------------------------------------------ fused inference
 
-// The whole network for one instance in one launch, on one CTA of 128
-// threads: layer 1, the set pooling, layers 2 and 3 and the rounding of
-// the predicted prices. Every product runs on tcgen05 with operands in
-// shared memory and FP32 accumulators in TMEM:
-//   pass 1, per 128-row tile: X (TMA) * W1^T -> relu(+ b1) = H1; H1 goes
-//     to global memory in BF16 and its column sums to shared memory;
-//   the pooled context enters layer 2 as a bias: [H1 ; c] W2 = H1 W2_top +
-//     c W2_bottom, so b2' = b2 + c W2_bottom is formed once (CUDA cores,
-//     BF16 operands and FP32 sums, as the products round them);
-//   pass 2, per tile: H1 (TMA) * W2_top^T -> relu(+ b2') = H2, written into
+// The whole network for one instance in one launch: a cluster of up to
+// eight CTAs of 128 threads (co-scheduled, with distributed shared memory),
+// CTA r taking the 128-row tiles r, r + 8, ... Every product is a tcgen05
+// MMA with operands in shared memory and FP32 accumulators in TMEM:
+//   pass 1, per tile: X (TMA) * W1^T -> relu(+ b1) = H1; only the column
+//     sums of H1 are kept (shared memory);
+//   the cluster adds its CTAs' column sums (DSMEM) into the pooled context
+//     c, which enters layer 2 as a bias: [H1 ; c] W2 = H1 W2_top +
+//     c W2_bottom, so b2' = b2 + c W2_bottom is formed once per CTA (CUDA
+//     cores, BF16 operands and FP32 sums, as the products round them);
+//   pass 2, per tile: layer 1 again (one MMA), H1 written in BF16 into
 //     shared memory in the swizzled K-major layout the next MMA reads;
+//     H1 * W2_top^T -> relu(+ b2') = H2, written the same way;
 //     H2 * W3^T + b3 = y (TMEM columns 128..143);
-//   prices: p_j = round((n+1) T (y_j - max y)), the paper's sign with
-//     max 0 (a uniform shift of all prices changes nothing).
+//   the cluster's largest y (DSMEM), then p_j = round((n+1) T (y_j - max y)):
+//     the paper's sign with max 0 (a uniform shift changes no reduced cost).
 // Shared memory (1024-aligned): W1^T 16 KB, W2_top^T 2 x 16 KB, W3^T
-// 2 x 2 KB, X tile 16 KB, H1 tile 2 x 16 KB, H2 tile 2 x 16 KB.
+// 2 x 2 KB, X tile 16 KB, H1 tile 2 x 16 KB, H2 tile 2 x 16 KB. Every wait
+// is bounded; on a timeout the kernel still passes every cluster barrier,
+// frees its TMEM and sets *err.
 constexpr int INF_W1 = 0, INF_W2 = INF_W1 + 16384, INF_W3 = INF_W2 + 32768, INF_X = INF_W3 + 4096,
               INF_H1 = INF_X + 16384, INF_H2 = INF_H1 + 32768, INF_BYTES = INF_H2 + 32768;
 constexpr int INF_SMEM = 1024 + INF_BYTES + 2048;
+constexpr int INF_CLUSTER = 8;
 
 __device__ __forceinline__ int float_order(float x) {   // order-preserving float -> int
     const int i = __float_as_int(x);
@@ -386,41 +396,52 @@ __device__ __forceinline__ int float_order(float x) {   // order-preserving floa
 }
 __device__ __forceinline__ float order_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
 
+// 16 BF16 values of row r (0..127), columns c0..c0+15 (c0 a multiple of
+// 16), into a [128 x 128] K-major tile with the 128-byte swizzle: two
+// 64-column halves of 16 KB; within a half, row r is 128 bytes and its
+// 16-byte unit u sits at unit u ^ (r % 8).
+__device__ __forceinline__ void store_swizzled(uint8_t *tile, int r, int c0, const uint32_t (&p)[8]) {
+    const int half = c0 / 64, u = (c0 % 64) / 8;
+    uint8_t *rowp = tile + half * 16384 + r * 128;
+    *reinterpret_cast<uint4 *>(rowp + ((u ^ (r & 7)) * 16)) = make_uint4(p[0], p[1], p[2], p[3]);
+    *reinterpret_cast<uint4 *>(rowp + (((u + 1) ^ (r & 7)) * 16)) = make_uint4(p[4], p[5], p[6], p[7]);
+}
+
 __global__ void __launch_bounds__(TC_THREADS)
 k_infer(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapW1,
-        const __grid_constant__ CUtensorMap mapH1, const __grid_constant__ CUtensorMap mapW2,
-        const __grid_constant__ CUtensorMap mapW3, const float *__restrict__ P, const __nv_bfloat16 *__restrict__ wb,
-        int n, const float *__restrict__ inst, __nv_bfloat16 *__restrict__ h1g, float *__restrict__ Y,
-        long long *__restrict__ prices, int *__restrict__ err) {
+        const __grid_constant__ CUtensorMap mapW2, const __grid_constant__ CUtensorMap mapW3,
+        const float *__restrict__ P, const __nv_bfloat16 *__restrict__ wb, int n, const float *__restrict__ inst,
+        float *__restrict__ Y, long long *__restrict__ prices, int *__restrict__ err) {
     extern __shared__ uint8_t in_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t raw = tc::smem_addr(in_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *sm = in_raw + (base - raw);
-    float *colsum = reinterpret_cast<float *>(sm + INF_BYTES);          // [128]
-    float *bias2 = colsum + H;                                           // [128]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(bias2 + H);            // weights, X, H1, MMA
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
+    float *colsum = reinterpret_cast<float *>(sm + INF_BYTES);           // [128]
+    float *bias2 = colsum + H;                                            // [128]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(bias2 + H);             // weights, X, MMA
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 3);
     int *ymax = reinterpret_cast<int *>(tslot + 1);
+    int *s_ok = ymax + 1;
     constexpr unsigned long long kLimit = 1000000000ull;
+    const int rank = (int)tc::cluster_rank(), csize = (int)tc::cluster_size();
     const int tiles = (n + TC_BM - 1) / TC_BM;
 
     if (warp == 0) tc::tmem_alloc(tslot, 256);
     colsum[tid] = 0.f;
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) tc::mbar_init(bars + i, 1);
+        for (int i = 0; i < 3; ++i) tc::mbar_init(bars + i, 1);
         *ymax = float_order(-INFINITY);
+        *s_ok = 1;
         tc::fence_mbar_init();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    int ok = 1;                     // thread 0's view; shared through s_ok below
-    __shared__ int s_ok;
-    uint32_t mph = 0;               // MMA barrier phase (every thread waits on every use)
+    bool ok = true;                 // thread 0's view
+    uint32_t mph = 0, xph = 0;      // phases of the MMA and X barriers
     if (tid == 0) {
-        s_ok = 1;
         tc::mbar_expect_tx(bars + 0, 16384 + 32768 + 4096);
         tc::tma_load_2d(sm + INF_W1, &mapW1, bars + 0, 0, 0);
         tc::tma_load_2d(sm + INF_W2, &mapW2, bars + 0, 0, 0);
@@ -429,89 +450,125 @@ k_infer(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
         tc::tma_load_2d(sm + INF_W3 + 2048, &mapW3, bars + 0, 64, 0);
         ok = tc::mbar_wait(bars + 0, 0, kLimit);
     }
-    // MMA issue by thread 0, completion seen by everyone (bounded)
-    auto wait_mma = [&]() {
-        const bool d = tc::mbar_wait(bars + 3, mph, kLimit);
-        mph ^= 1;
-        if (!d) atomicExch(&s_ok, 0);
-        tc::fence_after_sync();
-    };
     const float *b1 = P + OFF_B1, *b2 = P + OFF_B2, *b3 = P + OFF_B3;
+    constexpr uint32_t id128 = tc::idesc_bf16(TC_BM, H), id16 = tc::idesc_bf16(TC_BM, 16);
+    // thread 0: X tile t into shared memory, then layer 1 into TMEM columns 0..127
+    auto layer1 = [&](int t) {
+        if (ok) {
+            tc::mbar_expect_tx(bars + 1, 16384);
+            tc::tma_load_2d(sm + INF_X, &mapX, bars + 1, 0, t * TC_BM);
+            ok = tc::mbar_wait(bars + 1, xph, kLimit);
+            xph ^= 1;
+        }
+        if (ok) {
+            tc::fence_after_sync();
+            tc::mma_bf16(tmem, tc::desc_k128(base + INF_X), tc::desc_k128(base + INF_W1), id128, 0u);
+        }
+        tc::mma_commit(bars + 2);   // arrives at once when nothing was issued
+    };
+    // everyone: the MMAs committed last are done (bounded)
+    auto wait_mma = [&]() {
+        if (!tc::mbar_wait(bars + 2, mph, kLimit)) atomicExch(s_ok, 0);
+        mph ^= 1;
+        tc::fence_after_sync();
+        __syncwarp();
+    };
+    const uint32_t lanes = (uint32_t)(warp * 32) << 16;
 
     // pass 1: layer 1 and the column sums of H1
-    for (int t = 0; t < tiles; ++t) {
-        if (tid == 0) {
-            if (ok) {
-                tc::mbar_expect_tx(bars + 1, 16384);
-                tc::tma_load_2d(sm + INF_X, &mapX, bars + 1, 0, t * TC_BM);
-                ok = tc::mbar_wait(bars + 1, t & 1, kLimit);
-            }
-            if (ok) {
-                tc::fence_after_sync();
-                tc::mma_bf16(tmem, tc::desc_k128(base + INF_X), tc::desc_k128(base + INF_W1), tc::idesc_bf16(TC_BM, H), 0u);
-            }
-            tc::mma_commit(bars + 3);   // arrives at once when nothing was issued
-            if (!ok) s_ok = 0;
-        }
+    for (int t = rank; t < tiles; t += csize) {
+        if (tid == 0) layer1(t);
         wait_mma();
-        __syncwarp();
         const int row = t * TC_BM + warp * 32 + lane;
 #pragma unroll 1
         for (int c0 = 0; c0 < H; c0 += 16) {
             float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tc::tmem_ld16(tmem + lanes + (uint32_t)c0, v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const float h = row < n ? fmaxf(v[i] + b1[c0 + i], 0.f) : 0.f;
-                if (row < n) h1g[(size_t)row * H + c0 + i] = __float2bfloat16_rn(h);
-                float sum = h;
-                for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-                if (lane == 0) atomicAdd(colsum + c0 + i, sum);
+            for (int i = 0; i < 16; ++i) v[i] = row < n ? fmaxf(v[i] + b1[c0 + i], 0.f) : 0.f;
+            // sums of the 16 columns over the warp's 32 rows in 16 shuffles: each
+            // step keeps half of the columns and adds the partner lane's sums of
+            // them; lane l ends with column (l >> 1) & 15, twice
+#pragma unroll
+            for (int st = 0; st < 4; ++st) {
+                const int off = 16 >> st, half = 8 >> st;
+                const bool up = (lane & off) != 0;
+#pragma unroll
+                for (int i = 0; i < half; ++i) {
+                    const float send = up ? v[i] : v[i + half];
+                    const float keep = up ? v[i + half] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                }
             }
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+            if ((lane & 1) == 0) atomicAdd(colsum + c0 + ((lane >> 1) & 15), v[0]);
         }
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
     }
-    // H1 is read back by TMA (the async proxy) in pass 2
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    // the pooled context as a bias of layer 2: b2'[j] = b2[j] + sum_i bf16(c_i) W2[128 + i][j]
-    {
-        const __nv_bfloat16 *w2b = wb + WB_W2N + (size_t)H * H;   // rows 128..255 of W2
+    // W2's bottom rows (c's weights, 32 KB) into the H1 buffer, which pass 2
+    // fills only after they are used; completes on the X barrier
+    if (tid == 0 && ok) {
+        tc::mbar_expect_tx(bars + 1, (uint32_t)(H * H * 2));
+        tc::bulk_load(sm + INF_H1, wb + WB_W2N + (size_t)H * H, (uint32_t)(H * H * 2), bars + 1);
+    }
+    // the pooled context: the cluster's column sums over n
+    tc::cluster_sync();
+    float c = 0.f;
+    for (int q = 0; q < csize; ++q) c += tc::ld_cluster_f32(colsum + tid, (uint32_t)q);
+    bias2[tid] = __bfloat162float(__float2bfloat16_rn(c / (float)n));   // c_i, as layer 2 rounds it
+    __syncthreads();
+    {   // b2'[j] = b2[j] + sum_i c_i W2[128 + i][j], W2's bottom rows staged in the H1 buffer
+        if (tid == 0) {
+            if (ok) ok = tc::mbar_wait(bars + 1, xph, kLimit);   // the bulk copy issued after pass 1
+            xph ^= 1;
+        }
+        __syncthreads();
+        const __nv_bfloat16 *w2s = reinterpret_cast<const __nv_bfloat16 *>(sm + INF_H1);
         float acc = b2[tid];
-        for (int i = 0; i < H; ++i)
-            acc += __bfloat162float(__float2bfloat16_rn(colsum[i] / (float)n)) * __bfloat162float(w2b[(size_t)i * H + tid]);
+#pragma unroll 8
+        for (int i = 0; i < H; ++i) acc += bias2[i] * __bfloat162float(w2s[i * H + tid]);
+        __syncthreads();
         bias2[tid] = acc;
     }
     __syncthreads();
 
-    // pass 2: layers 2 and 3
-    for (int t = 0; t < tiles; ++t) {
-        if (tid == 0) {
-            if (ok) {
-                tc::mbar_expect_tx(bars + 2, 32768);
-                tc::tma_load_2d(sm + INF_H1, &mapH1, bars + 2, 0, t * TC_BM);
-                tc::tma_load_2d(sm + INF_H1 + 16384, &mapH1, bars + 2, 64, t * TC_BM);
-                ok = tc::mbar_wait(bars + 2, t & 1, kLimit);
-            }
-            if (ok) {
-                tc::fence_after_sync();
-                for (int ch = 0; ch < 2; ++ch)
-                    for (int kk = 0; kk < 4; ++kk)
-                        tc::mma_bf16(tmem, tc::desc_k128(base + INF_H1 + ch * 16384 + 32 * kk),
-                                     tc::desc_k128(base + INF_W2 + ch * 16384 + 32 * kk), tc::idesc_bf16(TC_BM, H),
-                                     (ch | kk) ? 1u : 0u);
-            }
-            tc::mma_commit(bars + 3);
-            if (!ok) s_ok = 0;
-        }
+    // pass 2: layer 1 again, then layers 2 and 3
+    for (int t = rank; t < tiles; t += csize) {
+        if (tid == 0) layer1(t);
         wait_mma();
-        __syncwarp();
         const int r = warp * 32 + lane;   // row within the tile
 #pragma unroll 1
         for (int c0 = 0; c0 < H; c0 += 16) {
             float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tc::tmem_ld16(tmem + lanes + (uint32_t)c0, v);
+            uint32_t p[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const __nv_bfloat162 pr = __floats2bfloat162_rn(fmaxf(v[2 * i] + b1[c0 + 2 * i], 0.f),
+                                                                 fmaxf(v[2 * i + 1] + b1[c0 + 2 * i + 1], 0.f));
+                p[i] = *reinterpret_cast<const uint32_t *>(&pr);
+            }
+            store_swizzled(sm + INF_H1, r, c0, p);
+        }
+        tc::fence_proxy_async();   // written by this thread, read next by the MMA (async proxy)
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            if (ok)
+                for (int ch = 0; ch < 2; ++ch)
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc::mma_bf16(tmem, tc::desc_k128(base + INF_H1 + ch * 16384 + 32 * kk),
+                                     tc::desc_k128(base + INF_W2 + ch * 16384 + 32 * kk), id128, (ch | kk) ? 1u : 0u);
+            tc::mma_commit(bars + 2);
+        }
+        wait_mma();
+#pragma unroll 1
+        for (int c0 = 0; c0 < H; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + lanes + (uint32_t)c0, v);
             uint32_t p[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -519,13 +576,9 @@ k_infer(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                                                                  fmaxf(v[2 * i + 1] + bias2[c0 + 2 * i + 1], 0.f));
                 p[i] = *reinterpret_cast<const uint32_t *>(&pr);
             }
-            // K-major, 128-byte swizzle: 16-byte unit u of row r sits at unit u ^ (r % 8)
-            const int ch = c0 / 64, u = (c0 % 64) / 8;
-            uint8_t *rowp = sm + INF_H2 + ch * 16384 + r * 128;
-            *reinterpret_cast<uint4 *>(rowp + ((u ^ (r & 7)) * 16)) = make_uint4(p[0], p[1], p[2], p[3]);
-            *reinterpret_cast<uint4 *>(rowp + (((u + 1) ^ (r & 7)) * 16)) = make_uint4(p[4], p[5], p[6], p[7]);
+            store_swizzled(sm + INF_H2, r, c0, p);
         }
-        tc::fence_proxy_async();   // H2 written by this thread, read next by the MMA (async proxy)
+        tc::fence_proxy_async();
         tc::fence_before_sync();
         __syncthreads();
         if (tid == 0) {
@@ -534,15 +587,13 @@ k_infer(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                 for (int ch = 0; ch < 2; ++ch)
                     for (int kk = 0; kk < 4; ++kk)
                         tc::mma_bf16(tmem + 128, tc::desc_k128(base + INF_H2 + ch * 16384 + 32 * kk),
-                                     tc::desc_k128(base + INF_W3 + ch * 2048 + 32 * kk), tc::idesc_bf16(TC_BM, 16),
-                                     (ch | kk) ? 1u : 0u);
-            tc::mma_commit(bars + 3);
+                                     tc::desc_k128(base + INF_W3 + ch * 2048 + 32 * kk), id16, (ch | kk) ? 1u : 0u);
+            tc::mma_commit(bars + 2);
         }
         wait_mma();
-        __syncwarp();
         {
             float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 128u, v);
+            tc::tmem_ld16(tmem + lanes + 128u, v);
             const int row = t * TC_BM + r;
             const float y = v[0] + b3[0];
             int m = row < n ? float_order(y) : float_order(-INFINITY);
@@ -554,10 +605,20 @@ k_infer(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
         __syncthreads();
         tc::fence_after_sync();
     }
-    // prices in the paper's sign, max 0 (a uniform shift changes nothing)
-    const double top = (double)order_float(*ymax), T = inst[0];
-    for (int j = tid; j < n; j += TC_THREADS) prices[j] = (long long)llround(((double)Y[j] - top) * T * (double)(n + 1));
-    if (tid == 0 && !s_ok) atomicExch(err, 1);
+    // the cluster's largest y, then the prices of this CTA's rows
+    tc::cluster_sync();
+    int mx = float_order(-INFINITY);
+    for (int q = 0; q < csize; ++q) mx = max(mx, tc::ld_cluster_s32(ymax, (uint32_t)q));
+    const double top = (double)order_float(mx), T = inst[0];
+    for (int t = rank; t < tiles; t += csize) {
+        const int row = t * TC_BM + tid;
+        if (row < n) prices[row] = (long long)llround(((double)Y[row] - top) * T * (double)(n + 1));
+    }
+    if (tid == 0 && !ok) *s_ok = 0;
+    __syncthreads();
+    if (tid == 0 && !*s_ok) atomicExch(err, 1);
+    // no CTA leaves while another may still read its shared memory
+    tc::cluster_sync();
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_free(tmem, 256);
@@ -733,7 +794,7 @@ la_status ensure_pws(PredWorkspace &w, size_t nrows, size_t ninst, int nmat) {
         w.cap_n = c;
         w.ldt = t;
         // column-pass partials for a single matrix of this size
-        if (!grow(w.part, c * 5 * (size_t)((c + 255) / 256))) return LA_ERR_NOMEM;
+        if (!grow(w.part, c * 5 * (size_t)kColBlocks)) return LA_ERR_NOMEM;
     }
     if (ninst + 1 > w.cap_i) {
         const size_t c = std::max(ninst + 1, (size_t)64);
@@ -817,7 +878,7 @@ la_status features_one(cudaStream_t s, const int32_t *C, int n, PredWorkspace &w
                        __nv_bfloat16 *xb = nullptr) {
     if (cudaMemsetAsync(w.pop, 0, sizeof(int) * n, s) != cudaSuccess) return LA_ERR_CUDA;
     k_row_stats<<<(n * 32 + 255) / 256, 256, 0, s>>>(C, n, w.rowmin, w.pop);
-    const int rpb = 256;
+    const int rpb = std::max(16, (n + kColBlocks - 1) / kColBlocks);   // at most kColBlocks row blocks
     const int rb = (n + rpb - 1) / rpb;
     dim3 grid((n + 127) / 128, rb);
     k_col_stats<<<grid, 128, 0, s>>>(C, n, w.rowmin, w.part, rpb);
@@ -1001,15 +1062,30 @@ la_status la_predict_prices_ex(const int32_t *cost, int32_t n, const void *weigh
     // launch (k_infer)
     if (la_status e = features_one(s, cost, n, *w, w->feats, w->inst, w->Xb)) return e;
     k_weights_bf16<<<64, 256, 0, s>>>(P, w->wb);
-    CUtensorMap mx, mw1, mh1, mw2, mw3;
+    CUtensorMap mx, mw1, mw2, mw3;
     if (!kmajor_map(&mx, w->Xb, 64, n, 64, TC_BM) || !kmajor_map(&mw1, w->wb + WB_W1T, 64, H, 64, TC_BM) ||
-        !kmajor_map(&mh1, w->H2b, H, n, H, TC_BM) || !kmajor_map(&mw2, w->wb + WB_W2T, 2 * H, H, 2 * H, TC_BM) ||
-        !kmajor_map(&mw3, w->wb + WB_W3T, H, 16, H, 16))
+        !kmajor_map(&mw2, w->wb + WB_W2T, 2 * H, H, 2 * H, TC_BM) || !kmajor_map(&mw3, w->wb + WB_W3T, H, 16, H, 16))
         return LA_ERR_CUDA;
     LA_PCK(cudaFuncSetAttribute(k_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, INF_SMEM));
-    k_infer<<<1, TC_THREADS, INF_SMEM, s>>>(mx, mw1, mh1, mw2, mw3, P, w->wb, n, w->inst, w->H2b, w->Y,
-                                             reinterpret_cast<long long *>(prices_out), w->err);
-    LA_PCK(cudaGetLastError());
+    {   // one cluster: up to eight CTAs, each taking every eighth 128-row tile
+        const int tiles = (n + TC_BM - 1) / TC_BM;
+        const unsigned cl = (unsigned)std::min(INF_CLUSTER, tiles);
+        cudaLaunchConfig_t cfg;
+        std::memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3(cl);
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = INF_SMEM;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        LA_PCK(cudaLaunchKernelEx(&cfg, k_infer, mx, mw1, mw2, mw3, P, (const __nv_bfloat16 *)w->wb, n,
+                                  (const float *)w->inst, w->Y, reinterpret_cast<long long *>(prices_out), w->err));
+    }
     float inst_h[2] = {0, 0}, calib[2] = {0, 0};
     LA_PCK(cudaMemcpyAsync(inst_h, w->inst, sizeof(inst_h), cudaMemcpyDeviceToHost, s));
     LA_PCK(cudaMemcpyAsync(calib, P + 4, sizeof(calib), cudaMemcpyDeviceToHost, s));
