@@ -77,7 +77,7 @@ __global__ void k_row_stats(const int32_t *__restrict__ C, int n, float *__restr
     }
 }
 
-constexpr int kColBlocks = 64;   // row blocks of the column pass (partials merged by k_features)
+constexpr int kColBlocks = 16;   // row blocks of the column pass (partials merged by k_features)
 
 // Column pass over a block of rows: per column, min and second min of C and
 // of the row-reduced C - rowmin, and the sum. Partials [rb][n][5].
