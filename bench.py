@@ -495,7 +495,7 @@ def measure_line(args, la, synth, dev, stream, workload, spec, steps, warmup, ra
 
 # ---------------------------------------------------------------- extra lines
 
-def bench_batched(args, la, synth, dev, stream):
+def bench_batched(args, la, synth, dev, stream, l2_gbps=None):
     """10,000 instances, n log-uniform in [16, 1024] (half uniform [0, 10^4],
     half geometric): one persistent launch replayed from a CUDA graph, versus
     one la_solve call per instance on a sample."""
@@ -530,9 +530,14 @@ def bench_batched(args, la, synth, dev, stream):
         la.solve(dc[int(off[i]):int(off[i]) + n * n].view(n, n))
     torch.cuda.synchronize(dev)
     per = len(idx) / (time.perf_counter() - t2)
+    scan_gbps = stats["scan_bytes"] / (stats["device_ms"] * 1e-3) / 1e9
     return {"workload": f"{args.batch} instances, n log-uniform [16,1024], half uniform [0,1e4], half geometric",
             "solves_per_s": args.batch / best, "ms": 1e3 * best, "device_ms": stats["device_ms"],
-            "graph": stats["graph"], "scan_GBps": stats["scan_bytes"] / (stats["device_ms"] * 1e-3) / 1e9,
+            "graph": stats["graph"], "scan_GBps": scan_gbps,
+            "scan_GBps_note": "algorithmic arc-scan bytes (4 n per row scan); rows are staged through shared "
+                              "memory and mostly served by L2 (DRAM reads about 17x the compulsory bytes, "
+                              "profiles/batched_mixed_1500.md); compare with l2_frac, not with HBM",
+            "l2_frac": scan_gbps / l2_gbps if l2_gbps else None,
             "scans": stats["scans"], "cost_bytes": int(flat.size) * 4,
             "per_instance_la_solve_per_s": per, "per_instance_sample": len(idx),
             "speedup_vs_per_instance": (args.batch / best) / per, "generate_s": gen_s,
@@ -755,7 +760,7 @@ def run_gpu(args):
                     u4096_alpha = r[1]
         extra["lines"] = lines
     if "batched" in wanted:
-        extra["batched"] = guarded(bench_batched, args, la, synth, dev, stream)
+        extra["batched"] = guarded(bench_batched, args, la, synth, dev, stream, l2_gbps)
     if "concurrent" in wanted:
         extra["concurrent_n4096"] = guarded(bench_concurrent, args, la, synth, dev, stream, u4096_alpha)
     if "warm" in wanted:
