@@ -54,7 +54,7 @@ HEADLINE = "geometric-n8192"
 # Each single-solve line: instances (seeds 0..count-1, whose optima are
 # stored), alpha (0: tuned on two untimed instances) and further la_options.
 LINES = {
-    "geometric-n8192": dict(count=8, alpha=10, options={"price_updates": 8}),
+    "geometric-n8192": dict(count=8, alpha=10, options={"price_updates": 4, "tail_threshold": 128}),
     "uniform-n4096-c2^20": dict(count=10, alpha=48, options={}),
     "uniform-n256-c1000": dict(count=100, alpha=10, options={}, steps=100),
 }
@@ -132,10 +132,11 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload, alpha, kernel):
+def recorded_traffic(workload, alpha, kernel, options=None):
     """DRAM bytes (read + write) per launch of ``kernel`` from the committed
-    ncu record, if one was taken on this workload at this alpha and on the
-    kernel source that is built now; None otherwise."""
+    ncu record, if one was taken on this workload at this alpha with these
+    solver options and on the kernel source that is built now; None
+    otherwise."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         rec = json.load(open(path))
@@ -143,7 +144,8 @@ def recorded_traffic(workload, alpha, kernel):
         return None
     h = kernel_hash()
     for e in rec.get("entries", []):
-        if e.get("kernel_hash") == h and e.get("workload") == workload and e.get("alpha") == alpha:
+        if (e.get("kernel_hash") == h and e.get("workload") == workload and e.get("alpha") == alpha
+                and (e.get("options") or {}) == (options or {})):
             return e.get("dram_bytes_per_launch", {}).get(kernel)
     return None
 
@@ -266,7 +268,7 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- single solves
 
-def kernel_rooflines(workload, alpha, n, stats, peak, peak_src, l2_gbps=None):
+def kernel_rooflines(workload, alpha, n, stats, peak, peak_src, l2_gbps=None, options=None):
     """Roofline entries of the refine-phase kernels from the per-solve
     counters: algorithmic bytes (4 n per full row scan, the list's bytes per
     candidate-list scan) over each kernel's own CUDA-event time (events on
@@ -295,7 +297,7 @@ def kernel_rooflines(workload, alpha, n, stats, peak, peak_src, l2_gbps=None):
         kbytes = 4.0 * n * kfull + list_bytes * klist
         ach = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else 0.0
         r = {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": peak, "peak_source": peak_src,
-             "unit": "GB/s", "frac": ach / peak, "traffic": recorded_traffic(workload, alpha, kname),
+             "unit": "GB/s", "frac": ach / peak, "traffic": recorded_traffic(workload, alpha, kname, options),
              "algorithmic_bytes_per_launch": kbytes / max(1, launches),
              "avg_launch_ms": kms / max(1, launches), "launches": launches,
              "share_of_refine_time": kms / phase_ms if phase_ms > 0 else None,
@@ -390,7 +392,7 @@ def measure_line(args, la, synth, dev, stream, workload, spec, steps, warmup, ra
     if probe_l2:
         la.probe_read_gbps(dmats[0], 1, stream=stream)
         l2_gbps = max(la.probe_read_gbps(dmats[0], 20, stream=stream) for _ in range(3))
-    per_kernel, dominant = kernel_rooflines(workload, alpha, n, stats, peak, peak_src, l2_gbps)
+    per_kernel, dominant = kernel_rooflines(workload, alpha, n, stats, peak, peak_src, l2_gbps, extra_opts)
 
     # e2e through the public API: pinned host matrices, copies and the
     # readback of the matching and cost inside the timed region; the next
