@@ -287,13 +287,18 @@ def kernel_rooflines(workload, alpha, n, stats, peak, peak_src, l2_gbps=None, op
     phases_run = sum(s["phases"] for s in stats)
     tail_launches = sum(s["tail_phases"] for s in stats)
     per_kernel = {}
-    for kname, kfull, klist, kms, launches in (
+    if stats and all(st.get("small_kernel") for st in stats):
+        # small instances: the whole solve is one launch of the shared-memory kernel
+        roles = (("k_small", full, 0, phase_ms, len(stats)),)
+    else:
+        roles = (
             # the bulk sweep: the k_refine launch that opens each phase (each row's first bid)
             ("k_refine_sweep", sweep_full, sweep_scans - sweep_full, sweep_ms, phases_run),
             # the grid refine launches that carry the displacement chains
             ("k_refine", full - tail_full - sweep_full, listed - (tail_scans - tail_full) - (sweep_scans - sweep_full),
              phase_ms - tail_ms - sweep_ms, phases_run),
-            ("k_tail", tail_full, tail_scans - tail_full, tail_ms, max(1, tail_launches))):
+            ("k_tail", tail_full, tail_scans - tail_full, tail_ms, max(1, tail_launches)))
+    for kname, kfull, klist, kms, launches in roles:
         kbytes = 4.0 * n * kfull + list_bytes * klist
         ach = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else 0.0
         r = {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": peak, "peak_source": peak_src,
@@ -301,7 +306,9 @@ def kernel_rooflines(workload, alpha, n, stats, peak, peak_src, l2_gbps=None, op
              "algorithmic_bytes_per_launch": kbytes / max(1, launches),
              "avg_launch_ms": kms / max(1, launches), "launches": launches,
              "share_of_refine_time": kms / phase_ms if phase_ms > 0 else None,
-             "regime": "latency: dependent displacement chains, few warps busy at once"}
+             "regime": ("latency: the chains of bids on one CTA, rows read from shared memory after one load"
+                        if kname == "k_small" else
+                        "latency: dependent displacement chains, few warps busy at once")}
         if l2_gbps:
             r["l2"] = {"peak": l2_gbps, "frac": ach / l2_gbps, "unit": "GB/s"}
         per_kernel[kname] = r

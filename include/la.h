@@ -139,6 +139,14 @@ typedef struct {
    LA_FLAG_CHECK_PHASES the eps-CS check of a fixed row covers its kept
    arcs. */
 #define LA_FLAG_NO_ARC_FIXING 4
+/* la_options.flags: solve small instances through the general path as well.
+   By default an instance with n <= 300 and max C - min C <= 65535 (16-bit
+   costs), or n <= 224 (32-bit), is solved by one CTA with the whole matrix
+   and the column keys in shared memory, every phase in one launch (no
+   candidate lists, tail kernel, arc fixing or sweep launch: each bid scans
+   its row from shared memory). LA_FLAG_CHECK_PHASES, a phase cutoff and
+   price updates also select the general path. */
+#define LA_FLAG_NO_SMALL_KERNEL 8
 
 /* Phases whose counters la_stats records one by one. */
 #define LA_STATS_PHASES 32
@@ -206,6 +214,10 @@ typedef struct {
     double sweep_ms;
     int64_t sweep_scans;
     int64_t sweep_full_scans;
+    /* 1 if the solve ran on the one-CTA shared-memory kernel for small
+       instances (see LA_FLAG_NO_SMALL_KERNEL): every scan is a full scan of
+       the row in shared memory, refine_ms is that launch's time. */
+    int32_t small_kernel;
 } la_stats;
 
 /*

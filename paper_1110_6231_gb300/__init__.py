@@ -35,6 +35,7 @@ LA_NOALLOC_MAX_N = 16384
 LA_FLAG_NO_CANDIDATE_LISTS = 1
 LA_FLAG_CHECK_PHASES = 2
 LA_FLAG_NO_ARC_FIXING = 4
+LA_FLAG_NO_SMALL_KERNEL = 8
 
 
 class la_options(ctypes.Structure):
@@ -94,6 +95,7 @@ class la_stats(ctypes.Structure):
         ("sweep_ms", ctypes.c_double),
         ("sweep_scans", ctypes.c_int64),
         ("sweep_full_scans", ctypes.c_int64),
+        ("small_kernel", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

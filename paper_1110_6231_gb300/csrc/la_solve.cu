@@ -530,6 +530,149 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
 }
 
 // ------------------------------------------------------------------------
+// Small instances: the whole solve on one CTA, the cost matrix in shared
+// memory. For n up to a few hundred a solve is a few thousand bids, most of
+// them in sequence (the chains that end each phase), and in the grid path
+// every bid pays a round trip to global memory for its row and its prices.
+// Here the matrix is copied once into shared memory, as C - min C in 16 bits
+// when the cost range allows it (else 32), the column keys live there too,
+// and every phase runs in the same launch:
+//   * phase initialisation (Alg. 5.2): the least q is taken out of every
+//     price (a uniform shift), every mate is cleared;
+//   * the bidding (Alg. 5.4 as the double push): each warp takes the next
+//     row of the phase's queue and carries its displacement chain to its
+//     end (a bid that lands on an unassigned column); a lost bid is retried.
+//     When the queue is empty and every warp's chain has ended, every row is
+//     matched: the CTA barrier that follows ends the phase.
+// The bid itself is the grid refine's: exact best and second best over the
+// whole row (from shared memory), one atomicMin on the packed key, stale
+// price reads only ever making a bid lose (Lemma 5.2). The keys go back to
+// global memory at the end for k_finalize.
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallMaxN16 = 300;    // 2 n^2 + 8 n bytes of shared memory
+constexpr int kSmallMaxN32 = 224;    // 4 n^2 + 8 n bytes
+
+template <bool WIDE, bool C16>
+__global__ void __launch_bounds__(kSmallThreads)
+k_small(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, const unsigned long long *__restrict__ sched,
+        int nph, unsigned long long qlim, unsigned long long *__restrict__ key, Ctrl *__restrict__ ctrl,
+        unsigned long long budget) {
+    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    using CT = typename std::conditional<C16, uint16_t, uint32_t>::type;
+    extern __shared__ unsigned long long small_smem[];
+    unsigned long long *skey = small_smem;                        // [n]
+    CT *cs = reinterpret_cast<CT *>(skey + n);                    // [n][n], C - cmin
+    __shared__ int s_head, s_status;
+    __shared__ unsigned long long s_scans, s_qmin;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const size_t nn = (size_t)n * n;
+    for (size_t e = tid; e < nn; e += blockDim.x) cs[e] = (CT)(uint32_t)(C[e] - cmin);
+    for (int y = tid; y < n; y += blockDim.x) skey[y] = key[y];
+    if (tid == 0) {
+        s_status = 0;
+        s_scans = 0;
+    }
+    __syncthreads();
+    const volatile unsigned long long *vkey = skey;
+    unsigned long long wins = 0, displaced = 0, chain_max = 0;
+    for (int ph = 0; ph < nph; ++ph) {
+        const unsigned long long eps = sched[ph];
+        // phase initialisation: shift the prices so that min q = 0, clear the mates
+        if (tid == 0) s_qmin = ~0ull;
+        __syncthreads();
+        unsigned long long m = ~0ull;
+        for (int y = tid; y < n; y += blockDim.x) m = min(m, key_q(skey[y]));
+        m = warp_min(m);
+        if (lane == 0) atomicMin(&s_qmin, m);
+        __syncthreads();
+        const unsigned long long qmin = s_qmin;
+        bool bad = false;
+        for (int y = tid; y < n; y += blockDim.x) {
+            const unsigned long long q = key_q(skey[y]) - qmin;
+            bad |= q > qlim;
+            skey[y] = pack_key(q, kNone);
+        }
+        if (bad) atomicCAS(&s_status, 0, (int)LA_ERR_OVERFLOW);
+        if (tid == 0) {
+            s_head = 0;
+            ctrl->phase_start_scans[ph & 63] = s_scans;
+            if (*reinterpret_cast<volatile int *>(&ctrl->status) == 0) ctrl->phase_now = ph;
+        }
+        __syncthreads();
+        // the bidding: a warp carries each row it takes to the end of its chain
+        int row = -1;
+        unsigned long long chain = 0;
+        unsigned pending = 0;
+        for (;;) {
+            if (*reinterpret_cast<volatile int *>(&s_status) != 0) break;
+            if (row < 0) {
+                int r = 0;
+                if (lane == 0) r = atomicAdd(&s_head, 1);
+                row = __shfl_sync(0xffffffffu, r, 0);
+                if (row >= n) break;
+            }
+            if (++pending == 8) {   // the scan budget, 8 scans at a time
+                pending = 0;
+                unsigned long long sc = 0;
+                if (lane == 0) sc = atomicAdd(&s_scans, 8ull);
+                sc = __shfl_sync(0xffffffffu, sc, 0);
+                if (sc + 8 > budget) {
+                    if (lane == 0) atomicCAS(&s_status, 0, (int)LA_ERR_ITER_LIMIT);
+                    break;
+                }
+            }
+            ++chain;
+            // best and second best of v(x,y) = (C[x][y] - cmin)(n+1) + q(y) over the row
+            const CT *crow = cs + (size_t)row * n;
+            Lane2<V> t;
+            lane2_init(t);
+            for (int y = lane; y < n; y += 32) lane2_push<V>(t, (V)crow[y] * np1 + (V)key_q(vkey[y]), y);
+            const V c1 = t.w1 >= 0 ? (V)crow[t.w1] * np1 : (V)0;
+            ScanResult<V> r{t.b1, t.b2, c1, t.w1 < 0 ? INT_MAX : t.w1};
+            warp_merge(r);
+            if (r.b2 == (V)~(V)0) r.b2 = r.b1;   // n = 1 cannot reach here; a lone column bids by eps
+            // double push: x -> w, relabel w (its price drops by second - best + eps)
+            const unsigned long long nq = (unsigned long long)(r.b1 - r.c1) + (r.b2 - r.b1) + eps;
+            if (r.w >= n || nq > qlim) {
+                if (lane == 0) atomicCAS(&s_status, 0, (int)(r.w >= n ? LA_ERR_INTERNAL : LA_ERR_OVERFLOW));
+                break;
+            }
+            const unsigned long long nk = pack_key(nq, (uint32_t)row);
+            unsigned long long old = 0;
+            if (lane == 0) old = atomicMin(skey + r.w, nk);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            if (old > nk) {
+                ++wins;
+                const uint32_t mate = key_mate(old);
+                if (mate != kNone) {
+                    ++displaced;
+                    row = (int)mate;
+                } else {
+                    row = -1;
+                }
+            }
+            // else: a lower price got there first; rescan this row
+        }
+        chain_max = max(chain_max, chain);
+        if (lane == 0 && pending) atomicAdd(&s_scans, (unsigned long long)pending);
+        __syncthreads();   // every row is matched (or the solve has stopped)
+        if (s_status != 0) break;
+    }
+    for (int y = tid; y < n; y += blockDim.x) key[y] = skey[y];
+    if (lane == 0) {
+        atomicAdd(&ctrl->wins, wins);
+        atomicAdd(&ctrl->displaced, displaced);
+        atomicMax(&ctrl->max_chain, chain_max);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        ctrl->scans += s_scans;
+        ctrl->full_scans += s_scans;
+        if (s_status) set_status(ctrl, s_status);
+    }
+}
+
+// ------------------------------------------------------------------------
 // Global price update (Sect. 5.2, Algorithm 5.3), run when a phase is down
 // to a few free rows. It labels every node with its distance, in units of
 // eps, to the nearest free column (a node with negative excess) over the
@@ -1405,8 +1548,41 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
             cudaMalloc(&chk_seen, sizeof(int) * n) != cudaSuccess)
             return LA_ERR_NOMEM;
     }
+    // small instances: the whole solve on one CTA with the matrix in shared memory
+    const bool c16 = range <= 65535 && n <= kSmallMaxN16;
+    const bool small = !check && stop_free == 0 && pu_rounds == 0 && !(opt && (opt->flags & LA_FLAG_NO_SMALL_KERNEL)) &&
+                       (c16 || n <= kSmallMaxN32) && (int)sched.size() <= kMaxPhases;
     int ph = 0;
-    for (; ph < (int)sched.size(); ++ph) {
+    if (small) {
+        unsigned long long *dsched = reinterpret_cast<unsigned long long *>(ws.tail_rows);   // n >= 2 ints: room for
+        if (ws.cap < (int64_t)(2 * sched.size())) return LA_ERR_INTERNAL;                   // the eps schedule
+        LA_CK(cudaMemcpyAsync(dsched, sched.data(), sizeof(unsigned long long) * sched.size(), cudaMemcpyHostToDevice, s));
+        const int smem = (int)(sizeof(unsigned long long) * n + (size_t)n * n * (c16 ? 2 : 4));
+        if (profile) LA_CK(cudaEventRecord(ws.ev[0], s));
+        const int nph = (int)sched.size();
+        if (wide) {
+            if (c16) {
+                LA_CK(cudaFuncSetAttribute(k_small<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                k_small<true, true><<<1, kSmallThreads, smem, s>>>(cost, n, cmin, (uint32_t)np1, dsched, nph, qlim, ws.key, ws.ctrl, budget);
+            } else {
+                LA_CK(cudaFuncSetAttribute(k_small<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                k_small<true, false><<<1, kSmallThreads, smem, s>>>(cost, n, cmin, (uint32_t)np1, dsched, nph, qlim, ws.key, ws.ctrl, budget);
+            }
+        } else {
+            if (c16) {
+                LA_CK(cudaFuncSetAttribute(k_small<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                k_small<false, true><<<1, kSmallThreads, smem, s>>>(cost, n, cmin, (uint32_t)np1, dsched, nph, qlim, ws.key, ws.ctrl, budget);
+            } else {
+                LA_CK(cudaFuncSetAttribute(k_small<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                k_small<false, false><<<1, kSmallThreads, smem, s>>>(cost, n, cmin, (uint32_t)np1, dsched, nph, qlim, ws.key, ws.ctrl, budget);
+            }
+        }
+        if (profile) LA_CK(cudaEventRecord(ws.ev[4], s));
+        LA_CK(cudaGetLastError());
+        launches += 1;
+        ph = nph;
+    }
+    for (; !small && ph < (int)sched.size(); ++ph) {
         const int slot = ph & 1;
         k_qmin<<<sg, 256, 0, s>>>(ws.key, n, ws.ctrl, slot);
         if (wide) k_reset<true><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds);
@@ -1469,7 +1645,8 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.wins = (int64_t)c1.wins;
     stats.displaced = (int64_t)c1.displaced;
     stats.launches = launches;
-    stats.refine_launches = (int64_t)sched.size() * (1 + pu_rounds + (tail_T > 0 ? 1 : 0) + (sweep ? 1 : 0));
+    stats.refine_launches = small ? 1 : (int64_t)sched.size() * (1 + pu_rounds + (tail_T > 0 ? 1 : 0) + (sweep ? 1 : 0));
+    stats.small_kernel = small ? 1 : 0;
     stats.price_updates = (int64_t)c1.pu_updates;
     stats.price_update_sweeps = (int64_t)c1.pu_iters;
     stats.price_update_levels = (int64_t)c1.pu_levels;
@@ -1500,7 +1677,11 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.stop_phase = c1.status ? c1.phase_now : -1;
     stats.stop_eps = c1.status ? (int64_t)sched[std::min<int>(std::max(c1.phase_now, 0), (int)sched.size() - 1)] : 0;
     stats.check_violations = (int64_t)c1.check_violations;
-    if (profile) {
+    if (profile && small) {   // one launch for every phase
+        float t = 0;
+        LA_CK(cudaEventElapsedTime(&t, ws.ev[0], ws.ev[4]));
+        stats.refine_ms = t;
+    } else if (profile) {
         double ms = 0, tail_ms = 0, sweep_ms = 0;
         for (int k = 0; k < ph; ++k) {
             float t = 0, tt = 0;

@@ -36,6 +36,9 @@ def la():
 def solve(la, C, **kw):
     import torch
     t = torch.from_numpy(np.ascontiguousarray(C, dtype=np.int32)).cuda()
+    # arc fixing belongs to the general path (small instances are otherwise
+    # solved whole in one CTA's shared memory)
+    kw["flags"] = kw.get("flags", 0) | la.LA_FLAG_NO_SMALL_KERNEL
     sol = la.solve(t, **kw)
     return sol.cost, sol.match.cpu().numpy(), sol.stats
 
@@ -72,7 +75,7 @@ def test_arc_fixing_keeps_the_optimum(la, name, alpha):
 def test_no_arc_fixing_when_prices_are_requested(la):
     import torch
     C = synth.uniform_costs(600, 0, 1000, 7)
-    sol = la.solve(torch.from_numpy(C).cuda(), want_prices=True)
+    sol = la.solve(torch.from_numpy(C).cuda(), want_prices=True, flags=la.LA_FLAG_NO_SMALL_KERNEL)
     assert sol.stats["fixed_rows"] == 0
     assert oracle.check_eps_cs(C, sol.match.cpu().numpy(), sol.prices.cpu().numpy(), 1) == 0
 

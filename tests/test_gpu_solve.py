@@ -297,8 +297,9 @@ def test_profile_counts(la):
 def test_candidate_lists_on_and_off(la, kind, n):
     C = synth.uniform_costs(n, 0, (1 << 20) - 1, 5) if kind == "uniform" else synth.geometric_costs(n, 5)
     ref = oracle.hungarian(C)[0]
-    on = check(la, C, ref)
-    off = check(la, C, ref, flags=la.LA_FLAG_NO_CANDIDATE_LISTS)
+    general = la.LA_FLAG_NO_SMALL_KERNEL    # lists belong to the general path
+    on = check(la, C, ref, flags=general)
+    off = check(la, C, ref, flags=general | la.LA_FLAG_NO_CANDIDATE_LISTS)
     assert off["list_scans"] == 0 and off["full_scans"] == off["scans"]
     assert on["list_scans"] + on["full_scans"] == on["scans"]
     assert on["list_scans"] > 0
