@@ -147,6 +147,11 @@ typedef struct {
    its row from shared memory). LA_FLAG_CHECK_PHASES, a phase cutoff and
    price updates also select the general path. */
 #define LA_FLAG_NO_SMALL_KERNEL 8
+/* la_options.flags: when the one-CTA tail kernel takes a phase over, it
+   first runs one global price update (Sect. 5.2, Algorithm 5.3) on its own
+   CTA: the labels of la_options.price_updates' grid update, computed with
+   the labels in shared memory and CTA barriers between sweeps. */
+#define LA_FLAG_TAIL_PRICE_UPDATE 16
 
 /* Phases whose counters la_stats records one by one. */
 #define LA_STATS_PHASES 32
@@ -218,6 +223,10 @@ typedef struct {
        instances (see LA_FLAG_NO_SMALL_KERNEL): every scan is a full scan of
        the row in shared memory, refine_ms is that launch's time. */
     int32_t small_kernel;
+    /* Time the tail kernel spent in its own price updates
+       (LA_FLAG_TAIL_PRICE_UPDATE), summed over phases, read from the GPU's
+       global timer. */
+    double tail_price_update_ms;
 } la_stats;
 
 /*
@@ -270,11 +279,17 @@ la_status la_release_workspace(void);
  * prices (the best 4 columns of each of the 32 lanes; all n columns when
  * n <= 128); a matched row's label is capped by the bound on its unlisted
  * columns, which keeps it eps-optimal over every arc. For n <= 128 the
- * labels are therefore the exact truncated distances. Uses the per-device
- * workspace. Blocks until done.
+ * labels are therefore the exact truncated distances.
+ *   kernel      0: the grid update of la_options.price_updates; 1: the
+ *               one-CTA update of LA_FLAG_TAIL_PRICE_UPDATE (labels and
+ *               keys in shared memory; n <= 16384, else LA_ERR_INVALID).
+ *               Both compute the same labels. Any other value is
+ *               LA_ERR_INVALID.
+ * Uses the per-device workspace. Blocks until done.
  */
 la_status la_debug_price_update(const int32_t *cost, int32_t n, const int64_t *prices, const int32_t *row_match,
-                                int64_t eps, void *stream, int32_t *labels_out, int64_t *prices_out);
+                                int64_t eps, void *stream, int32_t *labels_out, int64_t *prices_out,
+                                int32_t kernel);
 
 /* Library version as major * 10000 + minor * 100 + patch. */
 int32_t la_version(void);

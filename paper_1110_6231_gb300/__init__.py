@@ -36,6 +36,7 @@ LA_FLAG_NO_CANDIDATE_LISTS = 1
 LA_FLAG_CHECK_PHASES = 2
 LA_FLAG_NO_ARC_FIXING = 4
 LA_FLAG_NO_SMALL_KERNEL = 8
+LA_FLAG_TAIL_PRICE_UPDATE = 16
 
 
 class la_options(ctypes.Structure):
@@ -96,6 +97,7 @@ class la_stats(ctypes.Structure):
         ("sweep_scans", ctypes.c_int64),
         ("sweep_full_scans", ctypes.c_int64),
         ("small_kernel", ctypes.c_int32),
+        ("tail_price_update_ms", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -196,7 +198,7 @@ def lib() -> ctypes.CDLL:
             P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
             L.la_solve.argtypes = [P, i32, P, P, P]
             L.la_solve_ex.argtypes = [P, i32, P, P, P, P, P]
-            L.la_debug_price_update.argtypes = [P, i32, P, P, i64, P, P, P]
+            L.la_debug_price_update.argtypes = [P, i32, P, P, i64, P, P, P, i32]
             L.la_solve_noalloc.argtypes = [P, i32, P, P, P]
             L.la_solve_sparse.argtypes = [P, P, P, i32, i32, P, P, P]
             L.la_solve_sparse_ex.argtypes = [P, P, P, i32, i32, P, P, P, P, P]
@@ -263,9 +265,9 @@ def la_solve_ex(cost, n, opt, stream, match_out, cost_out, stats_out) -> int:
                              None if stats_out is None else ctypes.byref(stats_out))
 
 
-def la_debug_price_update(cost, n, prices, row_match, eps, stream, labels_out, prices_out) -> int:
+def la_debug_price_update(cost, n, prices, row_match, eps, stream, labels_out, prices_out, kernel=0) -> int:
     return lib().la_debug_price_update(_ptr(cost), int(n), _ptr(prices), _ptr(row_match), int(eps),
-                                       _stream(stream), _ptr(labels_out), _ptr(prices_out))
+                                       _stream(stream), _ptr(labels_out), _ptr(prices_out), int(kernel))
 
 
 def la_solve_noalloc(cost, n, stream, match_out, cost_out) -> int:

@@ -65,6 +65,7 @@ struct Ctrl {
     unsigned long long pu_mark;      // scans at the phase start or the last update
     unsigned long long pu_updates;   // price updates applied (all phases)
     unsigned long long pu_iters;     // relaxation sweeps they took
+    unsigned long long pu_tail_ns;   // time in the tail kernel's own updates
     unsigned long long pu_levels;    // sum of their truncation levels
     unsigned long long pu_qmax;      // largest q before an update
     unsigned pu_bar[2];              // grid barrier: arrivals, generation
@@ -237,6 +238,13 @@ __device__ __forceinline__ V warp_min(V v) {
         const unsigned lo = __reduce_min_sync(0xffffffffu, (unsigned)(v >> 32) == hi ? (unsigned)v : 0xffffffffu);
         return ((V)hi << 32) | (V)lo;
     }
+}
+
+// Warp-wide maximum of a 64-bit unsigned value (high word, then low word).
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+    const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(v >> 32));
+    const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(v >> 32) == hi ? (unsigned)v : 0u);
+    return ((unsigned long long)hi << 32) | (unsigned long long)lo;
 }
 
 // Merge of the lanes' (b1, w, c1, b2): every lane ends with the row's best

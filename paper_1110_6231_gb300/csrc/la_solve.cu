@@ -362,6 +362,198 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
     }
 }
 
+constexpr unsigned kMaxPuLevel = 2048;
+// Labels are kept clamped at kLabelTop: every update truncates them at a
+// level K <= kMaxPuLevel, and the fixed point of the clamped relaxation is
+// min(exact label, kLabelTop), so the truncated labels are the same.
+constexpr unsigned kLabelTop = kMaxPuLevel + 1;
+
+// min(floor(t / e), kLabelTop) for e >= 1: an estimate from the FP32
+// reciprocal inv of e, corrected to the exact floor by one step either way.
+// Below 2^12 the estimate's relative error (three FP32 roundings, under
+// 2^-22) keeps it within one of t / e; FP32 because this part's FP64 rate
+// is a small fraction of it. Since floor is monotone, a row's min over its
+// arcs of label(y) + floor(d_y / e) is label_quot(min over its arcs of
+// label(y) * e + d_y): one quotient per row instead of one per arc.
+__device__ __forceinline__ unsigned label_quot(unsigned long long t, unsigned long long e, float inv) {
+    if ((t >> 12) >= e) return kLabelTop;   // the quotient is at least 2^12
+    unsigned q = (unsigned)(__ull2float_rz(t) * inv);
+    const unsigned long long p = (unsigned long long)q * e;
+    if (p > t) --q;
+    else if (t - p >= e) ++q;
+    return min(q, kLabelTop);
+}
+
+// The global price update (Sect. 5.2, Algorithm 5.3) on the tail kernel's
+// own CTA, before its chains start: the same labels as k_pu (below), with
+// the labels in shared memory and CTA barriers between the Bellman-Ford
+// sweeps instead of grid barriers. Labels are distances in units of eps to
+// the nearest free column over the residual graph of the candidate lists
+// (a matched row's label capped by the bound theta on its unlisted
+// columns), run to a fixed point (the last free row's bucket finished, as
+// Algorithm 5.3 requires), truncated at one more than the largest label of
+// a free row; every price then falls by eps * label (q grows).
+//
+// One SM has to hide L2 latency alone, so the work is indexed by column:
+// a matched column's row is the mate in its shared-memory key, its
+// v(x, M(x)) and cap are kept per column (vref, cap: global scratch of n
+// entries), and a warp relaxes kPuBatch columns at a time with their lists'
+// loads all in flight. Only the lists are read in a sweep; a column whose
+// label is 0 is skipped. The matched rows are marked in a bitmap of n bits
+// after the labels (mark).
+constexpr int kPuBatch = 4;
+
+// Shared memory of the update beyond the n keys: labels, and the row marks.
+inline int tail_pu_smem(int n) { return (int)(sizeof(unsigned) * ((size_t)n + (n + 31) / 32)); }
+
+template <bool WIDE>
+__device__ void tail_price_update(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1,
+                                  unsigned long long eps, unsigned long long qlim, unsigned long long *skey,
+                                  unsigned *lab, unsigned *mark, const RowLists &L, unsigned long long R,
+                                  unsigned long long *vref, unsigned *cap, Ctrl *ctrl) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const float inv = 1.0f / (float)eps;
+    const unsigned long long t0 = tid == 0 ? global_timer_ns() : 0ull;
+    __shared__ unsigned s_last;
+    __shared__ unsigned long long s_qmax;
+    for (int i = tid; i < (n + 31) / 32; i += blockDim.x) mark[i] = 0;
+    if (tid == 0) {
+        s_last = 0;
+        s_qmax = 0;
+    }
+    __syncthreads();
+    // per column: the start label, the matched row's mark, v(x, M(x)) and the
+    // cap from theta (thread per column, the loads of a thread independent)
+    unsigned long long qmx = 0;
+    for (int y = tid; y < n; y += blockDim.x) {
+        const unsigned long long k = skey[y];
+        const uint32_t x = key_mate(k);
+        qmx = max(qmx, key_q(k));
+        unsigned l = 0;
+        if (x < (uint32_t)n) {
+            atomicOr(mark + (x >> 5), 1u << (x & 31));
+            const unsigned long long th = __ldca(L.theta + x);
+            const unsigned long long vr =
+                (unsigned long long)(uint32_t)(ld_row1(C + (size_t)x * n + y) - cmin) * np1 + key_q(k);
+            if (th == 0) {
+                l = 0;                                   // no list: label 0 is always safe
+            } else if (th == ~0ull) {
+                l = kLabelTop;                           // every arc is listed
+            } else {
+                const unsigned long long tf = th > R + 1 ? th - R - 1 : 0;
+                l = tf + eps >= vr ? label_quot(tf + eps - vr, eps, inv) : 0u;
+            }
+            vref[y] = vr;
+            cap[y] = l;
+        }
+        lab[y] = l;
+    }
+    qmx = warp_max_u64(qmx);
+    if (lane == 0) atomicMax(&s_qmax, qmx);
+    __syncthreads();
+    // Bellman-Ford sweeps until no label falls
+    bool settled = false;
+    int sweeps = 0;
+    while (sweeps < 256) {
+        ++sweeps;
+        int changed = 0;
+        for (int base = warp * kPuBatch; base < n; base += nwarps * kPuBatch) {
+            LaneList e[kPuBatch];
+            unsigned long long vr[kPuBatch];
+            unsigned cur[kPuBatch];
+            bool act[kPuBatch];
+#pragma unroll
+            for (int j = 0; j < kPuBatch; ++j) {
+                const int w = base + j;
+                act[j] = false;
+                if (w < n) {
+                    cur[j] = lab[w];
+                    const uint32_t x = key_mate(skey[w]);
+                    act[j] = cur[j] != 0 && x < (uint32_t)n;   // a label of 0 cannot fall
+                    if (act[j]) {
+                        e[j] = load_lane_list<true>(L, (int)x, lane);
+                        vr[j] = __ldcg(vref + w);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kPuBatch; ++j) {
+                if (!act[j]) continue;
+                const int w = base + j;
+                unsigned long long t = ~0ull;   // min of label(y) * eps + (v(x,y) + eps - v(x,w))
+#pragma unroll
+                for (int k = 0; k < kListK; ++k) {
+                    const int y = e[j].y[k];
+                    if (y < 0 || y >= n || y == w) continue;
+                    const unsigned long long vy = (unsigned long long)(uint32_t)(e[j].c[k] - cmin) * np1 + key_q(skey[y]);
+                    const unsigned long long d = vy + eps >= vr[j] ? vy + eps - vr[j] : 0;
+                    t = min(t, (unsigned long long)lab[y] * eps + d);
+                }
+                t = warp_min(t);
+                const unsigned best = min(__ldcg(cap + w), label_quot(t, eps, inv));
+                if (lane == 0 && best < cur[j]) {
+                    atomicMin(lab + w, best);
+                    changed = 1;
+                }
+            }
+        }
+        if (!__syncthreads_or(changed)) {
+            settled = true;
+            break;
+        }
+    }
+    // the free rows' labels set the truncation level
+    unsigned mx = 0;
+    for (int x = warp; x < n; x += nwarps) {
+        if (mark[x >> 5] & (1u << (x & 31))) continue;
+        const unsigned long long th = __ldca(L.theta + x);
+        unsigned long long best = 0;
+        if (th != 0) {
+            const LaneList e = load_lane_list<true>(L, x, lane);
+            unsigned long long m = ~0ull;
+#pragma unroll
+            for (int j = 0; j < kListK; ++j)
+                if (e.y[j] >= 0 && e.y[j] < n)
+                    m = min(m, (unsigned long long)(uint32_t)(e.c[j] - cmin) * np1 + key_q(skey[e.y[j]]));
+            m = warp_min(m);
+            const unsigned long long tf = th == ~0ull ? ~0ull : (th > R + 1 ? th - R - 1 : 0);
+            const unsigned long long vr = min(m, tf);   // <= the row's best value
+            unsigned long long t = ~0ull;
+#pragma unroll
+            for (int j = 0; j < kListK; ++j) {
+                const int y = e.y[j];
+                if (y < 0 || y >= n) continue;
+                const unsigned long long vy = (unsigned long long)(uint32_t)(e.c[j] - cmin) * np1 + key_q(skey[y]);
+                t = min(t, (unsigned long long)lab[y] * eps + (vy >= vr ? vy - vr : 0));
+            }
+            t = warp_min(t);
+            best = min(th == ~0ull ? kLabelTop : label_quot(tf - vr, eps, inv), label_quot(t, eps, inv));
+        }
+        mx = max(mx, (unsigned)best);
+    }
+    if (lane == 0) atomicMax(&s_last, mx);
+    __syncthreads();
+    unsigned long long K = settled ? (unsigned long long)s_last + 1 : 0;
+    K = min(K, (unsigned long long)kMaxPuLevel);
+    K = min(K, qlim > s_qmax ? (qlim - s_qmax) / eps : 0ull);
+    for (int y = tid; y < n && K > 0; y += blockDim.x) {
+        const unsigned long long lb = min((unsigned long long)lab[y], K);
+        if (lb == 0) continue;
+        const unsigned long long k = skey[y];
+        skey[y] = pack_key(key_q(k) + eps * lb, key_mate(k));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        atomicAdd(&ctrl->pu_tail_ns, global_timer_ns() - t0);
+        atomicAdd(&ctrl->pu_iters, (unsigned long long)sweeps);
+        if (K > 0) {
+            atomicAdd(&ctrl->pu_updates, 1ull);
+            atomicAdd(&ctrl->pu_levels, K);
+        }
+    }
+    __syncthreads();
+}
+
 // The end of a refine phase on one CTA. Once few rows are free (the refine
 // kernel's hand-off), every step of their displacement chains is latency
 // bound; here the column keys live in shared memory, so a step's price reads
@@ -379,7 +571,8 @@ __global__ void __launch_bounds__(tail_threads<WIDE>())
 k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
        unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
        Ctrl *__restrict__ ctrl, unsigned long long budget, RowLists L, const int *__restrict__ tail_rows,
-       int *__restrict__ qlist0, int *__restrict__ qlist1) {
+       int *__restrict__ qlist0, int *__restrict__ qlist1, int pu_tail, unsigned long long *__restrict__ pu_vref,
+       unsigned *__restrict__ pu_cap) {
     extern __shared__ unsigned long long skey[];
     __shared__ int s_next, s_tc, s_q0, s_count, s_back, s_stop, s_status;
     __shared__ unsigned s_full, s_hits;
@@ -410,6 +603,9 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
     // are kept in shared memory and published at the end.
     const unsigned long long scans0 = ctrl->scans;
     const unsigned long long R = ctrl->rebase_total;
+    if (pu_tail && L.cols && s_count > 0)   // labels, then the row marks, after the n keys in shared memory
+        tail_price_update<WIDE>(C, n, cmin, np1, eps, qlim, skey, reinterpret_cast<unsigned *>(skey + n),
+                                reinterpret_cast<unsigned *>(skey + n) + n, L, R, pu_vref, pu_cap, ctrl);
     const SharedKeyPrices<WIDE> prices{skey};
     volatile int *stop = &s_stop;
     int row = -1;
@@ -693,8 +889,6 @@ k_small(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, const unsi
 // bucket is included). Bellman-Ford sweeps run to a fixed point between grid
 // barriers of a cooperatively launched (co-resident) grid; if they do not
 // settle within the sweep limit, no price changes.
-constexpr unsigned kLabelInf = 0x7fffffffu;
-constexpr unsigned kMaxPuLevel = 2048;
 
 // Barrier of a co-resident grid. A wait longer than 2 s sets
 // LA_ERR_INTERNAL and returns false instead of spinning on.
@@ -739,6 +933,7 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
     const int gtid = blockIdx.x * blockDim.x + tid, gthreads = gridDim.x * blockDim.x;
     const int gwarp = gtid >> 5, nwarps = gthreads >> 5;
     const unsigned long long R = ctrl->rebase_total;
+    const float inv = 1.0f / (float)eps;
     // A0: clear the row -> column map and the sweep flags
     for (int x = gtid; x < n; x += gthreads) rowcol[x] = -1;
     if (gtid == 0) {
@@ -753,7 +948,7 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
         const unsigned long long k = key[y];
         const uint32_t m = key_mate(k);
         if (m != kNone && m < (uint32_t)n) rowcol[m] = y;
-        lab[y] = m == kNone ? 0u : kLabelInf;
+        lab[y] = m == kNone ? 0u : kLabelTop;
         qmx = max(qmx, key_q(k));
     }
     for (int o = 16; o; o >>= 1) qmx = max(qmx, __shfl_xor_sync(0xffffffffu, qmx, o));
@@ -784,14 +979,13 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
             if (th == 0) {
                 c = 0;                                   // no list: label 0 is always safe
             } else if (th == ~0ull) {
-                c = kLabelInf;                           // every column is listed
+                c = kLabelTop;                           // every column is listed
             } else {
                 const unsigned long long tf = th - R - 1, add = w >= 0 ? eps : 0;
-                const unsigned long long len = tf + add >= vr ? (tf + add - vr) / eps : 0;
-                c = (unsigned)min(len, (unsigned long long)kLabelInf);
+                c = tf + add >= vr ? label_quot(tf + add - vr, eps, inv) : 0u;
             }
             cap[x] = c;
-            if (w >= 0 && c < kLabelInf) lab[w] = c;
+            if (w >= 0) lab[w] = c;
         }
     }
     if (!pu_grid_sync(ctrl, &s_ok)) return;
@@ -811,17 +1005,17 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
             if (th == 0) continue;
             const unsigned long long vr = vref[x];
             const LaneList e = load_lane_list(L, x, lane);
-            unsigned long long best = cap[x];
+            unsigned long long t = ~0ull;   // min of label(y) * eps + (v(x,y) + eps - v(x,w))
 #pragma unroll
             for (int k = 0; k < kListK; ++k) {
                 const int y = e.y[k];
                 if (y < 0 || y >= n || y == w) continue;
                 const unsigned long long vy = (unsigned long long)(uint32_t)(e.c[k] - cmin) * np1 + key_q(__ldcg(key + y));
-                const unsigned long long len = vy + eps >= vr ? (vy + eps - vr) / eps : 0;
-                best = min(best, (unsigned long long)__ldcg(lab + y) + len);
+                const unsigned long long d = vy + eps >= vr ? vy + eps - vr : 0;
+                t = min(t, (unsigned long long)__ldcg(lab + y) * eps + d);
             }
-            for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-            const unsigned b = (unsigned)min(best, (unsigned long long)kLabelInf);
+            t = warp_min(t);
+            const unsigned b = min(cap[x], label_quot(t, eps, inv));
             if (lane == 0 && b < __ldcg(lab + w)) {
                 lab[w] = b;
                 changed = true;
@@ -840,21 +1034,22 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
     for (int x = gwarp; x < n; x += nwarps) {
         if (rowcol[x] >= 0) continue;
         const unsigned long long th = L.cols ? __ldcg(L.theta + x) : 0ull;
-        unsigned long long best = cap[x];
+        unsigned best = cap[x];
         if (th != 0) {
             const unsigned long long vr = vref[x];
             const LaneList e = load_lane_list(L, x, lane);
+            unsigned long long t = ~0ull;
 #pragma unroll
             for (int k = 0; k < kListK; ++k) {
                 const int y = e.y[k];
                 if (y < 0 || y >= n) continue;
                 const unsigned long long vy = (unsigned long long)(uint32_t)(e.c[k] - cmin) * np1 + key_q(__ldcg(key + y));
-                const unsigned long long len = vy >= vr ? (vy - vr) / eps : 0;
-                best = min(best, (unsigned long long)__ldcg(lab + y) + len);
+                t = min(t, (unsigned long long)__ldcg(lab + y) * eps + (vy >= vr ? vy - vr : 0));
             }
-            for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+            t = warp_min(t);
+            best = min(best, label_quot(t, eps, inv));
         }
-        mx = max(mx, (unsigned)min(best, (unsigned long long)kLabelInf));
+        mx = max(mx, best);
     }
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) atomicMax(&ctrl->pu_last, mx);
@@ -1233,7 +1428,7 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
                           unsigned long long eps, unsigned long long qlim, Workspace &ws,
                           unsigned long long budget, const RowLists &L, int tail_T, int pu_T, int pu_rounds,
                           int64_t &launches, int stop_free, cudaEvent_t ev_sweep, cudaEvent_t ev_tail,
-                          cudaEvent_t ev_fin, bool sweep) {
+                          cudaEvent_t ev_fin, bool sweep, bool tail_pu) {
     if (sweep) {   // the phase's bulk sweep: every row bids once
         k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L,
                                                    0, ws.tail_rows, 0, ws.qlist[0], ws.qlist[1], 0, 1);
@@ -1261,14 +1456,16 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
     }
     if (tail_T > 0) {
         ++launches;
-        const int smem = (int)(sizeof(unsigned long long) * n);
+        // the column keys, and with the in-tail price update its labels and row marks
+        const int smem = (int)(sizeof(unsigned long long) * n + (tail_pu ? tail_pu_smem(n) : 0));
         {   // A per-device attribute, set on every launch (a host call, no GPU work). Without it the
             // kernel's static shared memory and `smem` together may not pass 48 KB (n near 6144).
             cudaError_t e = cudaFuncSetAttribute(k_tail<WIDE, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
         }
         k_tail<WIDE, VEC><<<1, tail_threads<WIDE>(), smem, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget,
-                                                         L, ws.tail_rows, ws.qlist[0], ws.qlist[1]);
+                                                         L, ws.tail_rows, ws.qlist[0], ws.qlist[1], tail_pu ? 1 : 0,
+                                                         ws.pu_vref, ws.pu_cap);
         if (ev_fin) {
             cudaError_t e = cudaEventRecord(ev_fin, s);
             if (e != cudaSuccess) return e;
@@ -1347,6 +1544,24 @@ k_dbg_lists(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, const 
         (void)full_scan<WIDE, VEC, 1>(C + (size_t)x * n, x, n, cmin, np1, MirrorPrices<WIDE>{qmv}, lane, L, 0ull);
 }
 
+// The one-CTA update of the tail kernel on the same state: keys and labels
+// in shared memory, written back for k_dbg_out.
+template <bool WIDE>
+__global__ void __launch_bounds__(tail_threads<WIDE>())
+k_dbg_tail_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
+              unsigned long long qlim, unsigned long long *__restrict__ key, Ctrl *__restrict__ ctrl, RowLists L,
+              unsigned long long *__restrict__ vref, unsigned *__restrict__ cap, unsigned *__restrict__ lab_out) {
+    extern __shared__ unsigned long long skey[];
+    unsigned *lab = reinterpret_cast<unsigned *>(skey + n);
+    for (int y = threadIdx.x; y < n; y += blockDim.x) skey[y] = key[y];
+    __syncthreads();
+    tail_price_update<WIDE>(C, n, cmin, np1, eps, qlim, skey, lab, lab + n, L, 0ull, vref, cap, ctrl);
+    for (int y = threadIdx.x; y < n; y += blockDim.x) {
+        key[y] = skey[y];
+        lab_out[y] = lab[y];
+    }
+}
+
 // Truncated labels and the new prices in the caller's sign and units.
 __global__ void k_dbg_out(const unsigned long long *__restrict__ key, const unsigned *__restrict__ lab, int n,
                           const Ctrl *ctrl, int32_t *labels_out, int64_t *prices_out) {
@@ -1358,13 +1573,25 @@ __global__ void k_dbg_out(const unsigned long long *__restrict__ key, const unsi
     }
 }
 
+template <bool WIDE>
+cudaError_t launch_dbg_tail_pu(cudaStream_t s, const int32_t *C, int n, int cmin, uint32_t np1, unsigned long long eps,
+                               unsigned long long qlim, Workspace &ws, const RowLists &L) {
+    const int smem = (int)(sizeof(unsigned long long) * n + tail_pu_smem(n));
+    cudaError_t e = cudaFuncSetAttribute(k_dbg_tail_pu<WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_dbg_tail_pu<WIDE><<<1, tail_threads<WIDE>(), smem, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.ctrl, L,
+                                                              ws.pu_vref, ws.pu_cap, ws.pu_lab);
+    return cudaGetLastError();
+}
+
 static la_status debug_price_update_locked(const int32_t *cost, int32_t n, const int64_t *prices,
                                            const int32_t *row_match, int64_t eps, cudaStream_t s,
-                                           int32_t *labels_out, int64_t *prices_out) {
+                                           int32_t *labels_out, int64_t *prices_out, int32_t kernel) {
     int dev = 0;
     LA_CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return LA_ERR_INVALID;
     Workspace &ws = g_ws[dev];
+    if (kernel == 1 && n > kTailMaxN) return LA_ERR_INVALID;   // the keys and labels must fit one SM
     if (la_status e = ensure_ws(ws, n)) return e;
     Ctrl init;
     std::memset(&init, 0, sizeof(init));
@@ -1398,13 +1625,15 @@ static la_status debug_price_update_locked(const int32_t *cost, int32_t n, const
         k_dbg_mirror<true><<<sg, 256, 0, s>>>(ws.key, n, ws.qm, ws.ctrl);
         if (vec) k_dbg_lists<true, true><<<lg, 256, 0, s>>>(cost, n, c0.cmin, (uint32_t)np1, ws.qm, L);
         else k_dbg_lists<true, false><<<lg, 256, 0, s>>>(cost, n, c0.cmin, (uint32_t)np1, ws.qm, L);
-        LA_CK(launch_pu<true>(s, cost, n, c0.cmin, (uint32_t)np1, (unsigned long long)eps, qlim, ws, L));
+        if (kernel == 1) LA_CK(launch_dbg_tail_pu<true>(s, cost, n, c0.cmin, (uint32_t)np1, (unsigned long long)eps, qlim, ws, L));
+        else LA_CK(launch_pu<true>(s, cost, n, c0.cmin, (uint32_t)np1, (unsigned long long)eps, qlim, ws, L));
     } else {
         k_dbg_state<false><<<sg, 256, 0, s>>>(row_match, n, ws.key, ws.qm, ws.ctrl);
         k_dbg_mirror<false><<<sg, 256, 0, s>>>(ws.key, n, ws.qm, ws.ctrl);
         if (vec) k_dbg_lists<false, true><<<lg, 256, 0, s>>>(cost, n, c0.cmin, (uint32_t)np1, ws.qm, L);
         else k_dbg_lists<false, false><<<lg, 256, 0, s>>>(cost, n, c0.cmin, (uint32_t)np1, ws.qm, L);
-        LA_CK(launch_pu<false>(s, cost, n, c0.cmin, (uint32_t)np1, (unsigned long long)eps, qlim, ws, L));
+        if (kernel == 1) LA_CK(launch_dbg_tail_pu<false>(s, cost, n, c0.cmin, (uint32_t)np1, (unsigned long long)eps, qlim, ws, L));
+        else LA_CK(launch_pu<false>(s, cost, n, c0.cmin, (uint32_t)np1, (unsigned long long)eps, qlim, ws, L));
     }
     k_dbg_out<<<sg, 256, 0, s>>>(ws.key, ws.pu_lab, n, ws.ctrl, labels_out, prices_out);
     LA_CK(cudaGetLastError());
@@ -1433,6 +1662,7 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     // (off unless asked: see la_options.phase_cutoff)
     const int stop_free = (opt && opt->phase_cutoff > 0) ? opt->phase_cutoff : 0;
     const bool sweep = true;   // every phase opens with its bulk sweep
+    const bool tail_pu = lists && opt && (opt->flags & LA_FLAG_TAIL_PRICE_UPDATE);
     // arc fixing needs an eps-optimal flow at every phase end (no cutoff);
     // the final prices certify only the arcs kept, so not with prices_out
     const bool arcfix = lists && !(opt && (opt->flags & LA_FLAG_NO_ARC_FIXING)) && stop_free == 0 &&
@@ -1598,11 +1828,11 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         cudaEvent_t evt = profile ? ws.ev[5 * ph + 2] : nullptr;
         cudaEvent_t evf = profile ? ws.ev[5 * ph + 3] : nullptr;
         if (wide) {
-            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep)));
-            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep)));
+            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu)));
+            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu)));
         } else {
-            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep)));
-            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep)));
+            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu)));
+            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu)));
         }
         if (profile) LA_CK(cudaEventRecord(ws.ev[5 * ph + 4], s));
         if (check) {
@@ -1647,6 +1877,7 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.launches = launches;
     stats.refine_launches = small ? 1 : (int64_t)sched.size() * (1 + pu_rounds + (tail_T > 0 ? 1 : 0) + (sweep ? 1 : 0));
     stats.small_kernel = small ? 1 : 0;
+    stats.tail_price_update_ms = 1e-6 * (double)c1.pu_tail_ns;
     stats.price_updates = (int64_t)c1.pu_updates;
     stats.price_update_sweeps = (int64_t)c1.pu_iters;
     stats.price_update_levels = (int64_t)c1.pu_levels;
@@ -1735,12 +1966,14 @@ const char *la_status_string(la_status s) {
 }
 
 la_status la_debug_price_update(const int32_t *cost, int32_t n, const int64_t *prices, const int32_t *row_match,
-                                int64_t eps, void *stream, int32_t *labels_out, int64_t *prices_out) {
-    if (n < 2 || n > LA_MAX_N || eps < 1 || !cost || !prices || !row_match || !labels_out || !prices_out)
+                                int64_t eps, void *stream, int32_t *labels_out, int64_t *prices_out,
+                                int32_t kernel) {
+    if (n < 2 || n > LA_MAX_N || eps < 1 || !cost || !prices || !row_match || !labels_out || !prices_out ||
+        (kernel != 0 && kernel != 1))
         return LA_ERR_INVALID;
     std::lock_guard<std::mutex> lock(g_mu);
     return debug_price_update_locked(cost, n, prices, row_match, eps, static_cast<cudaStream_t>(stream),
-                                     labels_out, prices_out);
+                                     labels_out, prices_out, kernel);
 }
 
 la_status la_release_workspace(void) {

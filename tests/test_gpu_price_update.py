@@ -5,7 +5,9 @@ states.
 The states come from the oracle's sequential cost scaling stopped after a
 random number of bids inside a random phase (``oracle.price_update``): every
 matched row is eps-optimal and some rows are free. ``la_debug_price_update``
-runs the kernel the refine uses (``k_pu``) once on such a state. For
+runs one update on such a state, with either kernel the refine can use:
+the grid update (``k_pu``) or the one-CTA update the tail kernel runs with
+``LA_FLAG_TAIL_PRICE_UPDATE`` (labels in shared memory). For
 n <= 128 a row's candidate list holds every column, so the GPU's labels
 must equal the oracle's exactly and its new prices must be the given ones
 less eps times the labels. For larger n the lists hold part of each row and
@@ -34,7 +36,7 @@ def la():
     return la
 
 
-def _gpu_update(la, C, state):
+def _gpu_update(la, C, state, kernel):
     import torch
     cs, q, holder, free, e = state
     n = C.shape[0]
@@ -49,7 +51,7 @@ def _gpu_update(la, C, state):
     tm = torch.from_numpy(row_match).to(dev)
     lab = torch.full((n,), -1, dtype=torch.int32, device=dev)
     pout = torch.zeros(n, dtype=torch.int64, device=dev)
-    rc = la.la_debug_price_update(tC, n, tp, tm, e, None, lab, pout)
+    rc = la.la_debug_price_update(tC, n, tp, tm, e, None, lab, pout, kernel)
     torch.cuda.synchronize()
     assert rc == la.LA_OK, la.la_status_string(rc)
     return lab.cpu().numpy().astype(np.int64), pout.cpu().numpy(), prices
@@ -73,12 +75,16 @@ def _states(count, seed, nmin, nmax):
     return out
 
 
-def test_labels_equal_the_dial_buckets_when_every_column_is_listed(la):
+KERNELS = pytest.mark.parametrize("kernel", [0, 1], ids=["grid", "one_cta"])
+
+
+@KERNELS
+def test_labels_equal_the_dial_buckets_when_every_column_is_listed(la, kernel):
     moved = 0
     for C, st in _states(40, 1, 5, 128):
         cs, q, holder, free, e = st
         want = pu.dial_labels(cs, q, holder, free, e)
-        lab, pout, p = _gpu_update(la, C, st)
+        lab, pout, p = _gpu_update(la, C, st, kernel)
         assert list(lab) == want
         assert np.array_equal(pout, p - e * lab)
         assert pu.eps_optimal(cs, pu.apply(q, want, e), holder, e)
@@ -86,11 +92,12 @@ def test_labels_equal_the_dial_buckets_when_every_column_is_listed(la):
     assert moved >= 10        # the update moves prices in many of these states
 
 
-def test_capped_labels_on_partial_lists_keep_eps_optimality(la):
+@KERNELS
+def test_capped_labels_on_partial_lists_keep_eps_optimality(la, kernel):
     for C, st in _states(3, 2, 150, 200):
         cs, q, holder, free, e = st
         want = pu.dial_labels(cs, q, holder, free, e)
-        lab, pout, p = _gpu_update(la, C, st)
+        lab, pout, p = _gpu_update(la, C, st, kernel)
         assert (lab >= 0).all() and (lab <= np.array(want)).all()
         q2 = list(-pout + int(pout.max()))
         assert pu.eps_optimal(cs, q2, holder, e)
@@ -104,4 +111,14 @@ def test_invalid_state_is_rejected(la):
     m = torch.tensor([0, 0, -1, -1, -1, -1], dtype=torch.int32, device="cuda")   # column 0 twice
     lab = torch.zeros(n, dtype=torch.int32, device="cuda")
     out = torch.zeros(n, dtype=torch.int64, device="cuda")
-    assert la.la_debug_price_update(C, n, p, m, 1, None, lab, out) == la.LA_ERR_INVALID
+    for kernel in (0, 1):
+        assert la.la_debug_price_update(C, n, p, m, 1, None, lab, out, kernel) == la.LA_ERR_INVALID
+    m = torch.tensor([0, 1, -1, -1, -1, -1], dtype=torch.int32, device="cuda")
+    assert la.la_debug_price_update(C, n, p, m, 1, None, lab, out, 2) == la.LA_ERR_INVALID   # no such kernel
+
+
+def test_both_kernels_give_the_same_labels_on_partial_lists(la):
+    for C, st in _states(3, 3, 300, 400):
+        lab0, pout0, _ = _gpu_update(la, C, st, 0)
+        lab1, pout1, _ = _gpu_update(la, C, st, 1)
+        assert np.array_equal(lab0, lab1) and np.array_equal(pout0, pout1)

@@ -376,6 +376,23 @@ def test_price_updates_happen_on_a_large_instance(la):
     assert st["price_updates"] > 0
 
 
+@pytest.mark.parametrize("pu", [0, 4])
+def test_price_update_in_the_tail_kernel_keeps_the_optimum(la, pu):
+    """LA_FLAG_TAIL_PRICE_UPDATE runs one Alg. 5.3 update on the tail
+    kernel's CTA each time it takes a phase over: prices only, so the optimum
+    and the certificate are unchanged, alone or with the grid updates."""
+    cases = json.load(open(os.path.join(GOLDEN, "optimal_costs.json")))["cases"]
+    ref = [c["cost"] for c in cases if c["workload"] == "uniform-n4096-c2^20" and c["seed"] == 1][0]
+    tail_updates = 0
+    for C, want in ((synth.uniform_costs(1500, 0, (1 << 20) - 1, 8), None), (synth.geometric_costs(1200, 9), None),
+                    (synth.uniform_costs(700, 0, 1000, 10), None), (synth.uniform_costs(4096, 0, (1 << 20) - 1, 1), ref)):
+        st = check(la, C, want, flags=la.LA_FLAG_TAIL_PRICE_UPDATE, price_updates=pu)
+        if pu == 0:   # every update counted was the tail kernel's
+            tail_updates += st["price_updates"]
+            assert st["price_updates"] <= st["tail_phases"]
+    assert pu > 0 or tail_updates > 0
+
+
 @pytest.mark.parametrize("cut", [1, 4])
 def test_phase_cutoff_keeps_the_optimum(la, cut):
     """Cutting intermediate phases short leaves the optimum and the final
