@@ -152,6 +152,13 @@ typedef struct {
    CTA: the labels of la_options.price_updates' grid update, computed with
    the labels in shared memory and CTA barriers between sweeps. */
 #define LA_FLAG_TAIL_PRICE_UPDATE 16
+/* la_options.flags: by default, once at most 2 rows per SM are free (and
+   candidate lists are on), a phase is carried on by one CTA of 8 warps per
+   free row, its warps sharing each full row scan (best and second best,
+   Sect. 5.3, and the row's candidate list), then by the tail kernel as
+   usual. This flag keeps one warp per row throughout. The optimum is the
+   same either way. */
+#define LA_FLAG_NO_TEAM_REFINE 32
 
 /* Phases whose counters la_stats records one by one. */
 #define LA_STATS_PHASES 32
@@ -227,6 +234,11 @@ typedef struct {
        (LA_FLAG_TAIL_PRICE_UPDATE), summed over phases, read from the GPU's
        global timer. */
     double tail_price_update_ms;
+    /* Phases the team refine took over (see LA_FLAG_NO_TEAM_REFINE), its
+       row scans and, of those, full row scans. */
+    int32_t team_phases;
+    int64_t team_scans;
+    int64_t team_full_scans;
 } la_stats;
 
 /*

@@ -37,6 +37,7 @@ LA_FLAG_CHECK_PHASES = 2
 LA_FLAG_NO_ARC_FIXING = 4
 LA_FLAG_NO_SMALL_KERNEL = 8
 LA_FLAG_TAIL_PRICE_UPDATE = 16
+LA_FLAG_NO_TEAM_REFINE = 32
 
 
 class la_options(ctypes.Structure):
@@ -98,6 +99,9 @@ class la_stats(ctypes.Structure):
         ("sweep_full_scans", ctypes.c_int64),
         ("small_kernel", ctypes.c_int32),
         ("tail_price_update_ms", ctypes.c_double),
+        ("team_phases", ctypes.c_int32),
+        ("team_scans", ctypes.c_int64),
+        ("team_full_scans", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -86,6 +86,14 @@ struct Ctrl {
     unsigned sweep_done;                       // sweep: blocks finished (last one switches the queue)
     unsigned long long sweep_scans;            // row scans made by the sweep launches
     unsigned long long sweep_full;             // ... of which full row scans
+    int team_T;                                // team refine: free rows at the hand-off (0: off)
+    int team_go;                               // team refine: the refine handed its rows to it
+    int team_next;                             // team refine: next hand-off item to claim
+    int team_back;                             // team refine: rows queued for the tail kernel
+    unsigned team_done;                        // team refine: CTAs finished (the last sets the queue)
+    int team_phases;                           // phases the team refine took over
+    unsigned long long team_scans;             // row scans made by the team refine
+    unsigned long long team_full;              // ... of which full row scans
 };
 
 // Global nanosecond timer (bounds every wait in the kernels).

@@ -186,18 +186,19 @@ __device__ __forceinline__ auto full_scan(const int32_t *__restrict__ crow, int 
 // its candidate list: for stretches where the lists keep failing (a large
 // eps moves prices past theta after a bid or two), the top-4 insertion
 // network and the list write would be wasted. The list is left as it was
-// (its bound stays a valid lower bound: prices only fall).
+// (its bound stays a valid lower bound: prices only fall). scan_top2_range
+// ranks columns [y0, y1) only (the team refine splits a row among warps).
 template <bool WIDE, bool VEC, class P>
-__device__ __forceinline__ auto full_scan_top2(const int32_t *__restrict__ crow, int n, int cmin, uint32_t np1,
-                                               const P &prices, int lane) {
+__device__ __forceinline__ auto scan_top2_range(const int32_t *__restrict__ crow, int y0, int y1, int cmin,
+                                                uint32_t np1, const P &prices, int lane) {
     using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
     Lane2<V> t;
     lane2_init(t);
-    if (VEC) {
+    if (VEC) {   // y0 and y1 are multiples of 4
         const int4 *r4 = reinterpret_cast<const int4 *>(crow);
-        const int nv = n >> 2;
+        const int j1 = y1 >> 2;
 #pragma unroll 8
-        for (int j = lane; j < nv; j += 32) {
+        for (int j = (y0 >> 2) + lane; j < j1; j += 32) {
             const int4 c = ld_row4(r4 + j);
             const int y = j << 2;
             V qa, qb, qc, qd;
@@ -208,13 +209,53 @@ __device__ __forceinline__ auto full_scan_top2(const int32_t *__restrict__ crow,
             lane2_push<V>(t, (V)(uint32_t)(c.w - cmin) * np1 + qd, y + 3);
         }
     } else {
-        for (int y = lane; y < n; y += 32)
+        for (int y = y0 + lane; y < y1; y += 32)
             lane2_push<V>(t, (V)(uint32_t)(ld_row1(crow + y) - cmin) * np1 + prices.q(y), y);
     }
     const V c1 = t.w1 >= 0 ? (V)(uint32_t)(ld_row1(crow + t.w1) - cmin) * np1 : (V)0;
     ScanResult<V> r{t.b1, t.b2, c1, t.w1 < 0 ? INT_MAX : t.w1};
     warp_merge(r);
     return r;
+}
+
+// The lane's kListK best (value, column) pairs over columns [y0, y1) of a
+// row (y0, y1 multiples of 4 when VEC) and how many columns the lane saw:
+// one warp's share of a list rebuilt by the team refine, which merges the
+// warps' pairs lane by lane.
+template <bool WIDE, bool VEC, class P>
+__device__ __forceinline__ void scan_topk_range(const int32_t *__restrict__ crow, int y0, int y1, int cmin,
+                                                uint32_t np1, const P &prices, int lane,
+                                                LaneK<typename std::conditional<WIDE, unsigned long long, uint32_t>::type,
+                                                      kListK> &t,
+                                                int &cnt) {
+    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    lanek_init(t);
+    if (VEC) {
+        const int4 *r4 = reinterpret_cast<const int4 *>(crow);
+        const int j0 = y0 >> 2, j1 = y1 >> 2;
+        cnt = j0 + lane < j1 ? 4 * ((j1 - j0 - lane + 31) >> 5) : 0;
+#pragma unroll 4
+        for (int j = j0 + lane; j < j1; j += 32) {
+            const int4 c = ld_row4(r4 + j);
+            const int y = j << 2;
+            V qa, qb, qc, qd;
+            prices.q4(y, qa, qb, qc, qd);
+            lanek_push<V, kListK>(t, (V)(uint32_t)(c.x - cmin) * np1 + qa, y);
+            lanek_push<V, kListK>(t, (V)(uint32_t)(c.y - cmin) * np1 + qb, y + 1);
+            lanek_push<V, kListK>(t, (V)(uint32_t)(c.z - cmin) * np1 + qc, y + 2);
+            lanek_push<V, kListK>(t, (V)(uint32_t)(c.w - cmin) * np1 + qd, y + 3);
+        }
+    } else {
+        cnt = y0 + lane < y1 ? ((y1 - y0 - lane + 31) >> 5) : 0;
+        for (int y = y0 + lane; y < y1; y += 32)
+            lanek_push<V, kListK>(t, (V)(uint32_t)(ld_row1(crow + y) - cmin) * np1 + prices.q(y), y);
+    }
+}
+
+template <bool WIDE, bool VEC, class P>
+__device__ __forceinline__ auto full_scan_top2(const int32_t *__restrict__ crow, int n, int cmin, uint32_t np1,
+                                               const P &prices, int lane) {
+    return scan_top2_range<WIDE, VEC>(crow, 0, n, cmin, np1, prices, lane);
 }
 
 // Short scan of row x over its candidate list (kListK entries per lane).

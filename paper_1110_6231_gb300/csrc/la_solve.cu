@@ -176,20 +176,23 @@ __global__ void k_reset(unsigned long long *__restrict__ key, void *__restrict__
 
 // The refine phase: persistent grid, one warp per free row.
 //
-// With `sweep` set, the launch is the phase's bulk sweep: every row of the
+// With mode 1, the launch is the phase's bulk sweep: every row of the
 // queue bids once, and the row its bid leaves free (the displaced mate, or
 // the row itself after a lost bid) is queued for the next launch instead of
 // bidding at once. The last block to finish makes that queue the current
 // one. The sweep is the bandwidth part of a phase (each row's first scan,
 // all rows in flight); the launch after it carries the displacement chains.
+// Mode 2 is a chain launch that hands its rows to the team refine (k_team)
+// once at most ctrl->team_T rows are free; mode 0 a chain launch without.
 template <bool WIDE, bool VEC>
 __global__ void __launch_bounds__(256)
 k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
          unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
          Ctrl *__restrict__ ctrl, unsigned long long budget, RowLists L, int tail_T,
          int *__restrict__ tail_rows, int pu_T, int *__restrict__ qlist0,
-         int *__restrict__ qlist1, int stop_free, int sweep) {
+         int *__restrict__ qlist1, int stop_free, int mode) {
     constexpr unsigned kFlush = 8;       // scans between budget / status / hand-off checks
+    const bool sweep = mode == 1;
     int miss = 0;                        // this warp's consecutive scans that the lists did not answer
     const int lane = threadIdx.x & 31;
     const unsigned long long R = ctrl->rebase_total;
@@ -314,13 +317,16 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
                 // Hand the last rows to the one-CTA tail kernel only while
                 // the candidate lists answer most scans (>= 3 of 4): its
                 // single SM is then spent on cheap list scans, not rescans.
-                if (lane == 0 && (tail_T > 0 || pu_on || stop_free > 0)) {
+                if (lane == 0 && (tail_T > 0 || mode == 2 || pu_on || stop_free > 0)) {
                     const int fr = atomicSub(&ctrl->free_rows, 1) - 1;
                     // An intermediate phase only prepares prices for the next
                     // one, whose initialisation makes any prices eps-optimal
                     // (Alg. 5.2): it may stop with a few rows still free.
                     if (stop_free > 0 && fr <= stop_free) atomicCAS(&ctrl->handoff, 0, 3);
-                    if (!pu_on && tail_T > 0 && fr <= tail_T) {
+                    if (mode == 2 && fr <= ctrl->team_T) {
+                        // at most one free row per team CTA: the team refine takes over
+                        if (atomicCAS(&ctrl->handoff, 0, 4) == 0) ctrl->team_go = 1;
+                    } else if (!pu_on && tail_T > 0 && fr <= tail_T) {
                         const unsigned long long pf = *reinterpret_cast<volatile unsigned long long *>(&ctrl->ph_full);
                         const unsigned long long ph = *reinterpret_cast<volatile unsigned long long *>(&ctrl->ph_hits);
                         if (ph >= 3 * pf) atomicCAS(&ctrl->handoff, 0, 1);
@@ -358,6 +364,279 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
                 ctrl->pend = 0;
                 ctrl->sweep_done = 0;
             }
+        }
+    }
+}
+
+// Team refine (on unless LA_FLAG_NO_TEAM_REFINE). Once at most one row per CTA of its
+// grid is free, the refine's chains are latency bound, and where the lists
+// keep failing each step is a lone warp's full scan: n / 32 values ranked
+// per lane behind n / 1024 dependent rounds of loads. Here a CTA of
+// kTeamWarps warps carries one chain and every warp ranks its own slice of
+// the row: the best two only once the lists keep failing, as the refine
+// does, else the lanes' best kListK, merged into the row's new list;
+// thread 0 merges the slices and commits the same double push. A list scan
+// is warp 0's alone. The rows are the refine's hand-off (tail_rows and the
+// rest of the queue). When at most tail_T rows are free and the lists
+// answer (as for the refine's own hand-off), or when a price update is due
+// (pu_T, as in the refine), the rows still held and those never claimed
+// become the queue of the next kernel (the one-CTA tail kernel, or k_pu and
+// the refine launch after it); the last CTA to finish sets it up.
+constexpr int kTeamWarps = 8;
+
+template <bool WIDE, bool VEC>
+__global__ void __launch_bounds__(32 * kTeamWarps)
+k_team(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
+       unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
+       Ctrl *__restrict__ ctrl, unsigned long long budget, RowLists L, int tail_T,
+       const int *__restrict__ tail_rows, int *__restrict__ qlist0, int *__restrict__ qlist1, int stop_free,
+       int pu_T) {
+    using V = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+    constexpr unsigned kFlush = 8;
+    __shared__ ScanResult<V> s_part[kTeamWarps];
+    __shared__ V s_kv[kTeamWarps][kListK][32];     // list rebuild: each warp's lane lists
+    __shared__ int s_kw[kTeamWarps][kListK][32];
+    __shared__ int s_kc[kTeamWarps][32];
+    __shared__ int s_row, s_exit, s_try, s_ok;
+    // team_go stays set for the whole launch (handoff may move on from 4),
+    // so every CTA takes part and the last one to finish is seen
+    if (*reinterpret_cast<volatile int *>(&ctrl->team_go) == 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned long long R = ctrl->rebase_total;
+    const int qmode = ctrl->qmode, qlen = ctrl->qlen, qsel = ctrl->qsel, tc = ctrl->tail_count;
+    const int *qold = qsel ? qlist1 : qlist0;
+    int *qnew = qsel ? qlist0 : qlist1;   // the tail kernel's queue, if it takes over
+    const int qend = qmode ? qlen : n;
+    const int q0 = min(ctrl->next_row, qend);
+    const int items = tc + (qend - q0);
+    // this warp's slice of a row (16-byte aligned when VEC)
+    int y0, y1;
+    if (VEC) {
+        const int g = ((n >> 2) + kTeamWarps - 1) / kTeamWarps;
+        y0 = min(n, 4 * g * warp);
+        y1 = min(n, 4 * g * (warp + 1));
+    } else {
+        const int g = (n + kTeamWarps - 1) / kTeamWarps;
+        y0 = min(n, g * warp);
+        y1 = min(n, g * (warp + 1));
+    }
+    const MirrorPrices<WIDE> prices{qmv};
+    const V inf = (V)~(V)0;
+    // thread 0's state
+    int row = -1, miss = 0, fail = 0;
+    unsigned pending = 0;
+    unsigned long long wins = 0, displaced = 0, total = 0, full = 0, hits = 0, chain = 0, longest = 0;
+    unsigned long long full_pub = 0, hits_pub = 0;
+    for (;;) {
+        __syncthreads();   // the last step's shared results have been read
+        if (tid == 0) {
+            int ex = fail ? 2 : 0;
+            if (!ex && row < 0) {
+                longest = max(longest, chain);
+                chain = 0;
+                const int k = atomicAdd(&ctrl->team_next, 1);
+                if (k >= items) ex = 1;
+                else row = k < tc ? __ldcg(tail_rows + k) : (qmode ? __ldcg(qold + q0 + (k - tc)) : q0 + (k - tc));
+            }
+            if (!ex && pending >= kFlush) {
+                const unsigned long long sc = atomicAdd(&ctrl->scans, (unsigned long long)pending);
+                atomicAdd(&ctrl->ph_full, full - full_pub);
+                atomicAdd(&ctrl->ph_hits, hits - hits_pub);
+                full_pub = full;
+                hits_pub = hits;
+                pending = 0;
+                const int st = *reinterpret_cast<volatile int *>(&ctrl->status);
+                int ho = *reinterpret_cast<volatile int *>(&ctrl->handoff);
+                // few free rows and a stretch of bidding since the last update:
+                // stop for a global price update, as the refine does
+                if (ho == 4 && pu_T > 0 && *reinterpret_cast<volatile int *>(&ctrl->pu_left) > 0) {
+                    const int fr = *reinterpret_cast<volatile int *>(&ctrl->free_rows);
+                    const unsigned long long mark = *reinterpret_cast<volatile unsigned long long *>(&ctrl->pu_mark);
+                    if (fr <= pu_T && sc >= mark + 8ull * (unsigned long long)pu_T + 256ull) {
+                        atomicCAS(&ctrl->handoff, 4, 2);
+                        ho = *reinterpret_cast<volatile int *>(&ctrl->handoff);
+                    }
+                }
+                if (st != 0 || ho == 3) {
+                    ex = 2;
+                } else if (sc + kFlush > budget) {
+                    set_status(ctrl, LA_ERR_ITER_LIMIT);
+                    ex = 2;
+                } else if (ho == 1 || ho == 2) {   // the tail kernel or the price update takes this row
+                    qnew[atomicAdd(&ctrl->team_back, 1)] = row;
+                    row = -1;
+                    ex = 3;
+                }
+            }
+            s_row = row;
+            s_exit = ex;
+            s_try = L.cols && (miss < 3 || (total & 7) == 0);
+            s_ok = 0;
+        }
+        __syncthreads();
+        if (s_exit) break;
+        const int r = s_row;
+        const int32_t *crow = C + (size_t)r * n;
+        if (s_try && warp == 0) {   // uniform across the CTA
+            unsigned long long th = 0;
+            const auto t = list_scan<WIDE, false>(r, n, cmin, np1, prices, lane, L, ListAhead{-1, 0ull, {}}, th);
+            // exact when the list's second best does not exceed theta (see scan_for_bid)
+            const bool ok = th != 0 && (th == ~0ull || (unsigned long long)t.b2 + R + 1 <= th);
+            if (lane == 0) {
+                s_ok = ok;
+                if (ok) s_part[0] = t;
+            }
+        }
+        if (s_try) __syncthreads();
+        const bool ok = s_ok != 0;
+        // A list that was tried and failed is rebuilt, as the refine does:
+        // every warp keeps its lanes' kListK best pairs over its slice, and
+        // lane l of warp 0 merges the eight lists of lane l (columns outside
+        // them lost kListK times within that lane's columns, so theta keeps
+        // its meaning). In a stretch of failing lists (no try) the best two
+        // of each slice are enough.
+        const bool build = !ok && s_try;
+        if (build) {
+            LaneK<V, kListK> t;
+            int cnt;
+            scan_topk_range<WIDE, VEC>(crow, y0, y1, cmin, np1, prices, lane, t, cnt);
+#pragma unroll
+            for (int k = 0; k < kListK; ++k) {
+                s_kv[warp][k][lane] = t.b[k];
+                s_kw[warp][k][lane] = t.w[k];
+            }
+            s_kc[warp][lane] = cnt;
+            __syncthreads();
+            if (warp == 0) {
+                LaneK<V, kListK> m;
+                lanek_init(m);
+                int c = 0;
+                for (int w = 0; w < kTeamWarps; ++w) {
+                    c += s_kc[w][lane];
+#pragma unroll
+                    for (int k = 0; k < kListK; ++k)   // an empty entry (~0, -1) inserts nothing
+                        lanek_insert<V, kListK>(m, s_kv[w][k][lane], s_kw[w][k][lane]);
+                }
+                int craw[kListK];
+#pragma unroll
+                for (int k = 0; k < kListK; ++k) craw[k] = m.w[k] >= 0 ? ld_row1(crow + m.w[k]) : 0;
+                const size_t base = (size_t)r * kListLen + kListK * lane;
+#pragma unroll
+                for (int g = 0; g < kListK / 4; ++g) {
+                    reinterpret_cast<int4 *>(L.cols + base)[g] =
+                        make_int4(m.w[4 * g], m.w[4 * g + 1], m.w[4 * g + 2], m.w[4 * g + 3]);
+                    reinterpret_cast<int4 *>(L.costs + base)[g] =
+                        make_int4(craw[4 * g], craw[4 * g + 1], craw[4 * g + 2], craw[4 * g + 3]);
+                }
+                const V th = warp_min<V>(c > kListK ? m.b[kListK - 1] : inf);
+                if (lane == 0) L.theta[r] = th == inf ? ~0ull : (unsigned long long)th + R + 1;
+                __threadfence();   // the list is complete before this row can change hands
+                ScanResult<V> res{m.b[0], m.b[1], m.w[0] >= 0 ? (V)(uint32_t)(craw[0] - cmin) * np1 : (V)0,
+                                  m.w[0] < 0 ? INT_MAX : m.w[0]};
+                warp_merge(res);
+                if (lane == 0) s_part[0] = res;
+            }
+            __syncthreads();
+        } else if (!ok) {
+            const auto t = scan_top2_range<WIDE, VEC>(crow, y0, y1, cmin, np1, prices, lane);
+            if (lane == 0) s_part[warp] = t;
+            __syncthreads();
+        }
+        if (tid == 0) {
+            ScanResult<V> m = s_part[0];
+            if (!ok && !build) {   // lowest value, then lowest column; the second best over every slice
+                for (int k = 1; k < kTeamWarps; ++k) {
+                    const ScanResult<V> p = s_part[k];
+                    if (p.b1 < m.b1 || (p.b1 == m.b1 && (unsigned)p.w < (unsigned)m.w)) {
+                        m.b2 = min(m.b1, p.b2);
+                        m.b1 = p.b1;
+                        m.c1 = p.c1;
+                        m.w = p.w;
+                    } else {
+                        m.b2 = min(m.b2, p.b1);
+                    }
+                }
+                if (m.b2 == inf) m.b2 = m.b1;
+            }
+            ++pending;
+            ++total;
+            ++chain;
+            if (ok) {
+                ++hits;
+                miss = 0;
+            } else {
+                ++full;
+                ++miss;
+            }
+            // double push: x -> w, relabel w, w's old mate becomes free
+            const unsigned long long nq = (unsigned long long)(m.b1 - m.c1) + (m.b2 - m.b1) + eps;
+            if (m.w < 0 || m.w >= n || nq > qlim) {
+                set_status(ctrl, (m.w < 0 || m.w >= n) ? LA_ERR_INTERNAL : LA_ERR_OVERFLOW);
+                fail = 1;
+            } else {
+                const unsigned long long nk = pack_key(nq, (uint32_t)r);
+                const unsigned long long old = atomicMin(key + m.w, nk);
+                const unsigned long long qnow = old > nk ? nq : key_q(old);
+                if (WIDE) atomicMax(static_cast<unsigned long long *>(qmv) + m.w, qnow);
+                else atomicMax(static_cast<uint32_t *>(qmv) + m.w, (uint32_t)qnow);
+                if (old > nk) {
+                    ++wins;
+                    const uint32_t mate = key_mate(old);
+                    if (mate != kNone) {
+                        ++displaced;
+                        row = (int)mate;
+                    } else {
+                        row = -1;
+                        const int fr = atomicSub(&ctrl->free_rows, 1) - 1;
+                        if (stop_free > 0 && fr <= stop_free) atomicCAS(&ctrl->handoff, 4, 3);
+                        if (pu_T == 0 && tail_T > 0 && fr <= tail_T) {   // no update left in this phase
+                            const unsigned long long pf = *reinterpret_cast<volatile unsigned long long *>(&ctrl->ph_full);
+                            const unsigned long long ph = *reinterpret_cast<volatile unsigned long long *>(&ctrl->ph_hits);
+                            if (ph >= 3 * pf) atomicCAS(&ctrl->handoff, 4, 1);
+                        }
+                    }
+                }
+                // else: a lower price got there first; rescan this row
+            }
+        }
+    }
+    if (tid == 0) {
+        longest = max(longest, chain);
+        atomicAdd(&ctrl->scans, (unsigned long long)pending);
+        atomicAdd(&ctrl->ph_full, full - full_pub);
+        atomicAdd(&ctrl->ph_hits, hits - hits_pub);
+        if (total) {
+            atomicAdd(&ctrl->wins, wins);
+            atomicAdd(&ctrl->displaced, displaced);
+            atomicAdd(&ctrl->full_scans, full);
+            atomicAdd(&ctrl->list_scans, hits);
+            atomicAdd(&ctrl->team_scans, total);
+            atomicAdd(&ctrl->team_full, full);
+            atomicMax(&ctrl->max_chain, longest);
+        }
+        __threadfence();
+        if (atomicAdd(&ctrl->team_done, 1u) == gridDim.x - 1) {   // every CTA has finished
+            __threadfence();
+            const int ho = *reinterpret_cast<volatile int *>(&ctrl->handoff);
+            if (ho == 1 || ho == 2) {
+                // rows never claimed go to the next kernel too
+                int back = *reinterpret_cast<volatile int *>(&ctrl->team_back);
+                for (int k = min(*reinterpret_cast<volatile int *>(&ctrl->team_next), items); k < items; ++k)
+                    qnew[back++] = k < tc ? __ldcg(tail_rows + k) : (qmode ? __ldcg(qold + q0 + (k - tc)) : q0 + (k - tc));
+                ctrl->qsel = qsel ^ 1;
+                ctrl->qlen = back;
+            } else {
+                if (ho == 4) ctrl->handoff = 0;   // the phase ended here
+                ctrl->qlen = 0;
+            }
+            ctrl->qmode = 1;
+            ctrl->next_row = 0;
+            ctrl->tail_count = 0;
+            ctrl->team_next = 0;
+            ctrl->team_back = 0;
+            ctrl->team_done = 0;
+            ctrl->team_go = 0;
+            ctrl->team_phases += 1;
         }
     }
 }
@@ -1428,7 +1707,7 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
                           unsigned long long eps, unsigned long long qlim, Workspace &ws,
                           unsigned long long budget, const RowLists &L, int tail_T, int pu_T, int pu_rounds,
                           int64_t &launches, int stop_free, cudaEvent_t ev_sweep, cudaEvent_t ev_tail,
-                          cudaEvent_t ev_fin, bool sweep, bool tail_pu) {
+                          cudaEvent_t ev_fin, bool sweep, bool tail_pu, int team_T) {
     if (sweep) {   // the phase's bulk sweep: every row bids once
         k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L,
                                                    0, ws.tail_rows, 0, ws.qlist[0], ws.qlist[1], 0, 1);
@@ -1447,8 +1726,14 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
         // the last refine of a phase never stops for a price update
         k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L,
                                                    tail_T, ws.tail_rows, r < pu_rounds ? pu_T : 0,
-                                                   ws.qlist[0], ws.qlist[1], stop_free, 0);
+                                                   ws.qlist[0], ws.qlist[1], stop_free, team_T > 0 ? 2 : 0);
         ++launches;
+        if (team_T > 0) {   // one CTA per row the refine hands over (at most team_T)
+            k_team<WIDE, VEC><<<team_T, 32 * kTeamWarps, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl,
+                                                                 budget, L, tail_T, ws.tail_rows, ws.qlist[0],
+                                                                 ws.qlist[1], stop_free, r < pu_rounds ? pu_T : 0);
+            ++launches;
+        }
     }
     if (ev_tail) {
         cudaError_t e = cudaEventRecord(ev_tail, s);
@@ -1684,6 +1969,9 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     if (dev < 0 || dev >= kMaxDevices) return LA_ERR_INVALID;
     Workspace &ws = g_ws[dev];
     if (la_status e = ensure_ws(ws, n)) return e;
+    // team refine: one CTA of kTeamWarps warps per free row once at most 2
+    // per SM are free (every variant of k_team fits 2 CTAs per SM)
+    const int team_T = (lists && !(opt && (opt->flags & LA_FLAG_NO_TEAM_REFINE))) ? std::min(2 * ws.num_sms, n / 2) : 0;
 
     Ctrl init;
     std::memset(&init, 0, sizeof(init));
@@ -1691,6 +1979,7 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     init.cmax = INT_MIN;
     init.qmin[0] = init.qmin[1] = ~0ull;
     init.pmax = LLONG_MIN;
+    init.team_T = team_T;
     *ws.h_ctrl = init;
     LA_CK(cudaMemcpyAsync(ws.ctrl, ws.h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
     int64_t launches = 0;
@@ -1828,11 +2117,11 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         cudaEvent_t evt = profile ? ws.ev[5 * ph + 2] : nullptr;
         cudaEvent_t evf = profile ? ws.ev[5 * ph + 3] : nullptr;
         if (wide) {
-            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu)));
-            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu)));
+            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu, team_T)));
+            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu, team_T)));
         } else {
-            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu)));
-            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu)));
+            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu, team_T)));
+            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu, team_T)));
         }
         if (profile) LA_CK(cudaEventRecord(ws.ev[5 * ph + 4], s));
         if (check) {
@@ -1875,9 +2164,12 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.wins = (int64_t)c1.wins;
     stats.displaced = (int64_t)c1.displaced;
     stats.launches = launches;
-    stats.refine_launches = small ? 1 : (int64_t)sched.size() * (1 + pu_rounds + (tail_T > 0 ? 1 : 0) + (sweep ? 1 : 0));
+    stats.refine_launches = small ? 1 : (int64_t)sched.size() * (1 + pu_rounds + (tail_T > 0 ? 1 : 0) + (sweep ? 1 : 0) + (team_T > 0 ? 1 + pu_rounds : 0));
     stats.small_kernel = small ? 1 : 0;
     stats.tail_price_update_ms = 1e-6 * (double)c1.pu_tail_ns;
+    stats.team_phases = c1.team_phases;
+    stats.team_scans = (int64_t)c1.team_scans;
+    stats.team_full_scans = (int64_t)c1.team_full;
     stats.price_updates = (int64_t)c1.pu_updates;
     stats.price_update_sweeps = (int64_t)c1.pu_iters;
     stats.price_update_levels = (int64_t)c1.pu_levels;

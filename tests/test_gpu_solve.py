@@ -278,10 +278,12 @@ def test_profile_counts(la):
     C = synth.uniform_costs(1024, 0, 1000, 1)
     st = check(la, C, profile=True)
     assert st["phases"] == 6
-    # per phase: the bulk sweep, the refine grid that carries the chains and,
-    # after the one-CTA tail kernel, a refine launch for any rows the tail
-    # gives back (no price-update rounds by default)
-    assert st["refine_launches"] == 3 * st["phases"]
+    # per phase: the bulk sweep, the refine grid that carries the chains, the
+    # team refine it hands its last rows to and, after the one-CTA tail
+    # kernel, a refine launch for any rows the tail gives back (no
+    # price-update rounds by default)
+    assert st["refine_launches"] == 4 * st["phases"]
+    assert st["team_scans"] <= st["scans"] - st["sweep_scans"] - st["tail_scans"]
     # the sweep makes exactly one bid per row in every phase
     assert st["sweep_scans"] == 1024 * st["phases"]
     assert 0 <= st["sweep_full_scans"] <= st["sweep_scans"] and st["sweep_ms"] > 0
@@ -391,6 +393,34 @@ def test_price_update_in_the_tail_kernel_keeps_the_optimum(la, pu):
             tail_updates += st["price_updates"]
             assert st["price_updates"] <= st["tail_phases"]
     assert pu > 0 or tail_updates > 0
+
+
+@pytest.mark.parametrize("pu", [0, 4])
+def test_team_refine_keeps_the_optimum(la, pu):
+    """The team refine (on by default) hands the last rows of a phase to CTAs
+    of 8 warps that share each full row scan and rebuild the row's list from
+    their lanes' lists: the same bids, so the optimum and the certificate are
+    the same as with one warp per row (LA_FLAG_NO_TEAM_REFINE), with and
+    without price updates (the team kernel then stops for them as the refine
+    does), with the tail kernel off, and on a size that is not a multiple of
+    4 (scalar row loads, uneven slices)."""
+    cases = json.load(open(os.path.join(GOLDEN, "optimal_costs.json")))["cases"]
+    geo = [c for c in cases if c["workload"] == "geometric-n8192" and c["n"] == 8192][0]
+    uni = [c for c in cases if c["workload"] == "uniform-n4096-c2^20" and c["seed"] == 2][0]
+    team = 0
+    for C, want, kw in ((synth.instance(geo["workload"], geo["seed"]), geo["cost"], {"tail_threshold": 128}),
+                        (synth.instance(uni["workload"], uni["seed"]), uni["cost"], {}),
+                        (synth.geometric_costs(1200, 9), None, {}),
+                        (synth.geometric_costs(1001, 4), None, {}),
+                        (synth.uniform_costs(1500, 0, (1 << 20) - 1, 8), None, {"tail_threshold": -1})):
+        if want is None:
+            want = oracle.hungarian(C)[0]
+        st = check(la, C, want, price_updates=pu, **kw)
+        team += st["team_phases"]
+        assert st["team_full_scans"] <= st["team_scans"]
+        st = check(la, C, want, flags=la.LA_FLAG_NO_TEAM_REFINE, price_updates=pu, **kw)
+        assert st["team_phases"] == 0 and st["team_scans"] == 0
+    assert team > 0
 
 
 @pytest.mark.parametrize("cut", [1, 4])
