@@ -1199,7 +1199,7 @@ __device__ bool pu_grid_sync(Ctrl *ctrl, int *s_ok) {
 }
 
 template <bool WIDE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
      unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
      Ctrl *__restrict__ ctrl, RowLists L, const int *__restrict__ tail_rows, int *__restrict__ qlist0,
@@ -1221,54 +1221,40 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
         ctrl->pu_changed[2] = 0;
     }
     if (!pu_grid_sync(ctrl, &s_ok)) return;
-    // A1: matched columns, start labels, largest q
+    // A1: per column, the largest q, the row map, and for a matched column
+    // v(x, M(x)) and the cap from theta (kept per column: vref, cap), which is
+    // its start label; a free column starts at 0
     unsigned long long qmx = 0;
     for (int y = gtid; y < n; y += gthreads) {
         const unsigned long long k = key[y];
-        const uint32_t m = key_mate(k);
-        if (m != kNone && m < (uint32_t)n) rowcol[m] = y;
-        lab[y] = m == kNone ? 0u : kLabelTop;
+        const uint32_t x = key_mate(k);
         qmx = max(qmx, key_q(k));
+        unsigned l = 0;
+        if (x < (uint32_t)n) {
+            rowcol[x] = y;
+            const unsigned long long th = L.cols ? __ldcg(L.theta + x) : 0ull;
+            const unsigned long long vr =
+                (unsigned long long)(uint32_t)(ld_row1(C + (size_t)x * n + y) - cmin) * np1 + key_q(k);
+            if (th == 0) {
+                l = 0;                                   // no list: label 0 is always safe
+            } else if (th == ~0ull) {
+                l = kLabelTop;                           // every column is listed
+            } else {
+                const unsigned long long tf = th > R + 1 ? th - R - 1 : 0;
+                l = tf + eps >= vr ? label_quot(tf + eps - vr, eps, inv) : 0u;
+            }
+            vref[y] = vr;
+            cap[y] = l;
+        }
+        lab[y] = l;
     }
     for (int o = 16; o; o >>= 1) qmx = max(qmx, __shfl_xor_sync(0xffffffffu, qmx, o));
     if (lane == 0) atomicMax(&ctrl->pu_qmax, qmx);
     if (!pu_grid_sync(ctrl, &s_ok)) return;
-    // A2: per row, v(x, M(x)) (or a lower bound of min_y v(x,y) for a free row)
-    // and the cap from theta
-    for (int x = gwarp; x < n; x += nwarps) {
-        const int w = rowcol[x];
-        const unsigned long long th = L.cols ? __ldcg(L.theta + x) : 0ull;
-        unsigned long long vr = 0;
-        if (w >= 0) {
-            vr = (unsigned long long)(uint32_t)(ld_row1(C + (size_t)x * n + w) - cmin) * np1 + key_q(__ldcg(key + w));
-        } else if (th != 0) {
-            // free row: min over the list and theta is <= min_y v(x,y)
-            const LaneList e = load_lane_list(L, x, lane);
-            unsigned long long m = ~0ull;
-#pragma unroll
-            for (int k = 0; k < kListK; ++k)
-                if (e.y[k] >= 0 && e.y[k] < n)
-                    m = min(m, (unsigned long long)(uint32_t)(e.c[k] - cmin) * np1 + key_q(__ldcg(key + e.y[k])));
-            for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
-            vr = th == ~0ull ? m : min(m, th - R - 1);
-        }
-        if (lane == 0) {
-            vref[x] = vr;
-            unsigned c;
-            if (th == 0) {
-                c = 0;                                   // no list: label 0 is always safe
-            } else if (th == ~0ull) {
-                c = kLabelTop;                           // every column is listed
-            } else {
-                const unsigned long long tf = th - R - 1, add = w >= 0 ? eps : 0;
-                c = tf + add >= vr ? label_quot(tf + add - vr, eps, inv) : 0u;
-            }
-            cap[x] = c;
-            if (w >= 0) lab[w] = c;
-        }
-    }
-    if (!pu_grid_sync(ctrl, &s_ok)) return;
-    // B: Bellman-Ford sweeps over the matched rows until no label falls
+    // B: Bellman-Ford sweeps over the matched columns until no label falls;
+    // a warp relaxes kPuBatch columns at a time, their rows' lists loaded
+    // together (the mate read from the column's key, which no kernel changes
+    // during the update); a label of 0 cannot fall
     int it = 0;
     bool settled = false;
     for (; it < max_sweeps; ++it) {
@@ -1277,27 +1263,44 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
         // cleared now.
         const int par = it % 3;
         bool changed = false;
-        for (int x = gwarp; x < n; x += nwarps) {
-            const int w = rowcol[x];
-            if (w < 0) continue;
-            const unsigned long long th = L.cols ? __ldcg(L.theta + x) : 0ull;
-            if (th == 0) continue;
-            const unsigned long long vr = vref[x];
-            const LaneList e = load_lane_list(L, x, lane);
-            unsigned long long t = ~0ull;   // min of label(y) * eps + (v(x,y) + eps - v(x,w))
+        for (int base = gwarp * kPuBatch; base < n; base += nwarps * kPuBatch) {
+            LaneList e[kPuBatch];
+            unsigned long long vr[kPuBatch];
+            unsigned cur[kPuBatch];
+            bool act[kPuBatch];
 #pragma unroll
-            for (int k = 0; k < kListK; ++k) {
-                const int y = e.y[k];
-                if (y < 0 || y >= n || y == w) continue;
-                const unsigned long long vy = (unsigned long long)(uint32_t)(e.c[k] - cmin) * np1 + key_q(__ldcg(key + y));
-                const unsigned long long d = vy + eps >= vr ? vy + eps - vr : 0;
-                t = min(t, (unsigned long long)__ldcg(lab + y) * eps + d);
+            for (int j = 0; j < kPuBatch; ++j) {
+                const int w = base + j;
+                act[j] = false;
+                if (w < n) {
+                    cur[j] = __ldcg(lab + w);
+                    const uint32_t x = key_mate(__ldcg(key + w));
+                    act[j] = cur[j] != 0 && x < (uint32_t)n;
+                    if (act[j]) {
+                        e[j] = load_lane_list(L, (int)x, lane);
+                        vr[j] = __ldcg(vref + w);
+                    }
+                }
             }
-            t = warp_min(t);
-            const unsigned b = min(cap[x], label_quot(t, eps, inv));
-            if (lane == 0 && b < __ldcg(lab + w)) {
-                lab[w] = b;
-                changed = true;
+#pragma unroll
+            for (int j = 0; j < kPuBatch; ++j) {
+                if (!act[j]) continue;
+                const int w = base + j;
+                unsigned long long t = ~0ull;   // min of label(y) * eps + (v(x,y) + eps - v(x,w))
+#pragma unroll
+                for (int k = 0; k < kListK; ++k) {
+                    const int y = e[j].y[k];
+                    if (y < 0 || y >= n || y == w) continue;
+                    const unsigned long long vy = (unsigned long long)(uint32_t)(e[j].c[k] - cmin) * np1 + key_q(__ldcg(key + y));
+                    const unsigned long long d = vy + eps >= vr[j] ? vy + eps - vr[j] : 0;
+                    t = min(t, (unsigned long long)__ldcg(lab + y) * eps + d);
+                }
+                t = warp_min(t);
+                const unsigned b = min(__ldcg(cap + w), label_quot(t, eps, inv));
+                if (lane == 0 && b < cur[j]) {
+                    lab[w] = b;
+                    changed = true;
+                }
             }
         }
         if (changed) ctrl->pu_changed[par] = 1;
@@ -1308,15 +1311,23 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
             break;
         }
     }
-    // C: the free rows' labels set the truncation level
+    // C: the free rows' labels set the truncation level (a free row's value
+    // bound: the least listed value, or theta if that is lower)
     unsigned mx = 0;
     for (int x = gwarp; x < n; x += nwarps) {
         if (rowcol[x] >= 0) continue;
         const unsigned long long th = L.cols ? __ldcg(L.theta + x) : 0ull;
-        unsigned best = cap[x];
+        unsigned best = 0;
         if (th != 0) {
-            const unsigned long long vr = vref[x];
             const LaneList e = load_lane_list(L, x, lane);
+            unsigned long long m = ~0ull;
+#pragma unroll
+            for (int k = 0; k < kListK; ++k)
+                if (e.y[k] >= 0 && e.y[k] < n)
+                    m = min(m, (unsigned long long)(uint32_t)(e.c[k] - cmin) * np1 + key_q(__ldcg(key + e.y[k])));
+            m = warp_min(m);
+            const unsigned long long tf = th == ~0ull ? ~0ull : (th > R + 1 ? th - R - 1 : 0);
+            const unsigned long long vr = min(m, tf);
             unsigned long long t = ~0ull;
 #pragma unroll
             for (int k = 0; k < kListK; ++k) {
@@ -1326,7 +1337,7 @@ k_pu(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long
                 t = min(t, (unsigned long long)__ldcg(lab + y) * eps + (vy >= vr ? vy - vr : 0));
             }
             t = warp_min(t);
-            best = min(best, label_quot(t, eps, inv));
+            best = min(th == ~0ull ? kLabelTop : label_quot(tf - vr, eps, inv), label_quot(t, eps, inv));
         }
         mx = max(mx, best);
     }
