@@ -111,6 +111,9 @@ typedef struct {
        unchanged. Large values make the next phase pay for the unresolved
        conflicts (small eps, long price wars); keep it small. */
     int32_t phase_cutoff;
+    /* Free rows at which the team refine takes a phase over (see
+       LA_FLAG_NO_TEAM_REFINE); 0 means 2 per SM, capped at n / 2. */
+    int32_t team_threshold;
 } la_options;
 
 /* la_options.flags: scan every row in full on every bid instead of using

@@ -53,6 +53,7 @@ class la_options(ctypes.Structure):
         ("tail_threshold", ctypes.c_int32),
         ("price_updates", ctypes.c_int32),
         ("phase_cutoff", ctypes.c_int32),
+        ("team_threshold", ctypes.c_int32),
     ]
 
 
@@ -406,7 +407,7 @@ class Solution:
 
 def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bool = False,
           scan_budget: int = 0, profile: bool = False, block_threads: int = 0,
-          flags: int = 0, tail_threshold: int = 0, price_updates: int = 0, phase_cutoff: int = 0,
+          flags: int = 0, tail_threshold: int = 0, price_updates: int = 0, phase_cutoff: int = 0, team_threshold: int = 0,
           stream=None, check: bool = True) -> Solution:
     """Exact minimum-cost assignment of a square int32 CUDA tensor ``C``.
 
@@ -440,6 +441,7 @@ def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bo
     opt.tail_threshold = tail_threshold
     opt.price_updates = price_updates
     opt.phase_cutoff = phase_cutoff
+    opt.team_threshold = team_threshold
     st = la_stats()
     with torch.cuda.device(dev):
         rc = la_solve_ex(C, n, opt, stream, match, cost, st)

@@ -1982,7 +1982,9 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     if (la_status e = ensure_ws(ws, n)) return e;
     // team refine: one CTA of kTeamWarps warps per free row once at most 2
     // per SM are free (every variant of k_team fits 2 CTAs per SM)
-    const int team_T = (lists && !(opt && (opt->flags & LA_FLAG_NO_TEAM_REFINE))) ? std::min(2 * ws.num_sms, n / 2) : 0;
+    const int team_T = (lists && !(opt && (opt->flags & LA_FLAG_NO_TEAM_REFINE)))
+                           ? std::max(1, std::min((opt && opt->team_threshold > 0) ? opt->team_threshold : 2 * ws.num_sms, n / 2))
+                           : 0;
 
     Ctrl init;
     std::memset(&init, 0, sizeof(init));
