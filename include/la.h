@@ -114,6 +114,10 @@ typedef struct {
     /* Free rows at which the team refine takes a phase over (see
        LA_FLAG_NO_TEAM_REFINE); 0 means 2 per SM, capped at n / 2. */
     int32_t team_threshold;
+    /* Global price updates (Sect. 5.2, Algorithm 5.3) the one-CTA tail
+       kernel may stop for in each phase, after 2n row scans of its own each;
+       0 (the default) or negative: none. */
+    int32_t tail_updates;
 } la_options;
 
 /* la_options.flags: scan every row in full on every bid instead of using

@@ -54,6 +54,7 @@ class la_options(ctypes.Structure):
         ("price_updates", ctypes.c_int32),
         ("phase_cutoff", ctypes.c_int32),
         ("team_threshold", ctypes.c_int32),
+        ("tail_updates", ctypes.c_int32),
     ]
 
 
@@ -408,6 +409,7 @@ class Solution:
 def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bool = False,
           scan_budget: int = 0, profile: bool = False, block_threads: int = 0,
           flags: int = 0, tail_threshold: int = 0, price_updates: int = 0, phase_cutoff: int = 0, team_threshold: int = 0,
+          tail_updates: int = 0,
           stream=None, check: bool = True) -> Solution:
     """Exact minimum-cost assignment of a square int32 CUDA tensor ``C``.
 
@@ -442,6 +444,7 @@ def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bo
     opt.price_updates = price_updates
     opt.phase_cutoff = phase_cutoff
     opt.team_threshold = team_threshold
+    opt.tail_updates = tail_updates
     st = la_stats()
     with torch.cuda.device(dev):
         rc = la_solve_ex(C, n, opt, stream, match, cost, st)

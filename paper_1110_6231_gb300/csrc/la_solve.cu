@@ -851,7 +851,7 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
        unsigned long long qlim, unsigned long long *__restrict__ key, void *__restrict__ qmv,
        Ctrl *__restrict__ ctrl, unsigned long long budget, RowLists L, const int *__restrict__ tail_rows,
        int *__restrict__ qlist0, int *__restrict__ qlist1, int pu_tail, unsigned long long *__restrict__ pu_vref,
-       unsigned *__restrict__ pu_cap) {
+       unsigned *__restrict__ pu_cap, unsigned long long yield_scans) {
     extern __shared__ unsigned long long skey[];
     __shared__ int s_next, s_tc, s_q0, s_count, s_back, s_stop, s_status;
     __shared__ unsigned s_full, s_hits;
@@ -920,6 +920,9 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
                 if (lane == 0) atomicCAS(&s_status, 0, (int)LA_ERR_ITER_LIMIT);
                 break;
             }
+            // a stretch of bidding: stop for a global price update (the rows
+            // go back, and k_pu runs next)
+            if (yield_scans > 0 && s + kFlush > yield_scans && lane == 0) atomicCAS(&s_stop, 0, 2);
         }
         ++pending;
         ++total;
@@ -998,9 +1001,10 @@ k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned lo
         ctrl->qmode = 1;
         ctrl->qlen = *stop ? s_back : 0;
         ctrl->next_row = 0;
-        ctrl->handoff = 0;
+        ctrl->tail_count = 0;                 // the hand-off list has been taken
+        ctrl->handoff = *stop == 2 ? 2 : 0;   // 2: a price update takes the rows first
         ctrl->tail_phases += 1;
-        ctrl->tail_giveups += *stop ? 1 : 0;
+        ctrl->tail_giveups += *stop == 1 ? 1 : 0;
     }
 }
 
@@ -1718,7 +1722,7 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
                           unsigned long long eps, unsigned long long qlim, Workspace &ws,
                           unsigned long long budget, const RowLists &L, int tail_T, int pu_T, int pu_rounds,
                           int64_t &launches, int stop_free, cudaEvent_t ev_sweep, cudaEvent_t ev_tail,
-                          cudaEvent_t ev_fin, bool sweep, bool tail_pu, int team_T) {
+                          cudaEvent_t ev_fin, bool sweep, bool tail_pu, int team_T, int tail_updates) {
     if (sweep) {   // the phase's bulk sweep: every row bids once
         k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L,
                                                    0, ws.tail_rows, 0, ws.qlist[0], ws.qlist[1], 0, 1);
@@ -1759,9 +1763,31 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
             cudaError_t e = cudaFuncSetAttribute(k_tail<WIDE, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
         }
-        k_tail<WIDE, VEC><<<1, tail_threads<WIDE>(), smem, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget,
-                                                         L, ws.tail_rows, ws.qlist[0], ws.qlist[1], tail_pu ? 1 : 0,
-                                                         ws.pu_vref, ws.pu_cap);
+        // Each tail launch but the last may stop after 2n scans for a grid
+        // price update; the refine (and team refine) launch after the update
+        // hands the rows straight back to the next tail launch.
+        const unsigned long long yield = 2ull * (unsigned long long)n;
+        for (int r = 0; r <= tail_updates; ++r) {
+            if (r > 0) {
+                cudaError_t e = launch_pu<WIDE>(s, C, n, cmin, np1, eps, qlim, ws, L);
+                if (e != cudaSuccess) return e;
+                k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget,
+                                                           L, tail_T, ws.tail_rows, 0, ws.qlist[0], ws.qlist[1],
+                                                           stop_free, team_T > 0 ? 2 : 0);
+                launches += 2;
+                if (team_T > 0) {
+                    k_team<WIDE, VEC><<<team_T, 32 * kTeamWarps, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm,
+                                                                         ws.ctrl, budget, L, tail_T, ws.tail_rows,
+                                                                         ws.qlist[0], ws.qlist[1], stop_free, 0);
+                    ++launches;
+                }
+                ++launches;
+            }
+            k_tail<WIDE, VEC><<<1, tail_threads<WIDE>(), smem, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl,
+                                                                   budget, L, ws.tail_rows, ws.qlist[0], ws.qlist[1],
+                                                                   tail_pu ? 1 : 0, ws.pu_vref, ws.pu_cap,
+                                                                   r < tail_updates ? yield : 0ull);
+        }
         if (ev_fin) {
             cudaError_t e = cudaEventRecord(ev_fin, s);
             if (e != cudaSuccess) return e;
@@ -1954,6 +1980,8 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     int pu_rounds = (opt && opt->price_updates) ? opt->price_updates : kDefaultPuRounds;
     if (pu_rounds < 0 || !lists) pu_rounds = 0;
     const int pu_T = std::max(16, n / 128);
+    // grid price updates the tail kernel may stop for in each phase
+    const int tail_updates = (lists && tail_T > 0 && opt && opt->tail_updates > 0) ? opt->tail_updates : 0;
     // intermediate phases stop at this many free rows (the last phase never does)
     // (off unless asked: see la_options.phase_cutoff)
     const int stop_free = (opt && opt->phase_cutoff > 0) ? opt->phase_cutoff : 0;
@@ -2117,8 +2145,8 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     for (; !small && ph < (int)sched.size(); ++ph) {
         const int slot = ph & 1;
         k_qmin<<<sg, 256, 0, s>>>(ws.key, n, ws.ctrl, slot);
-        if (wide) k_reset<true><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds);
-        else k_reset<false><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds);
+        if (wide) k_reset<true><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds + tail_updates);
+        else k_reset<false><<<sg, 256, 0, s>>>(ws.key, ws.qm, n, qlim, ws.ctrl, slot, ph, pu_rounds + tail_updates);
         launches += 2;
         if (check) {
             k_check_snapshot<<<sg, 256, 0, s>>>(ws.key, n, chk_q0);
@@ -2130,11 +2158,11 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
         cudaEvent_t evt = profile ? ws.ev[5 * ph + 2] : nullptr;
         cudaEvent_t evf = profile ? ws.ev[5 * ph + 3] : nullptr;
         if (wide) {
-            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu, team_T)));
-            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu, team_T)));
+            if (vec) LA_CK((launch_refine<true, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu, team_T, tail_updates)));
+            else LA_CK((launch_refine<true, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu, team_T, tail_updates)));
         } else {
-            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu, team_T)));
-            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu, team_T)));
+            if (vec) LA_CK((launch_refine<false, true>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu, team_T, tail_updates)));
+            else LA_CK((launch_refine<false, false>(s, grid, block, cost, n, cmin, (uint32_t)np1, sched[ph], qlim, ws, budget, L, tail_T, pu_T, pu_rounds, launches, sf, evs, evt, evf, sweep, tail_pu, team_T, tail_updates)));
         }
         if (profile) LA_CK(cudaEventRecord(ws.ev[5 * ph + 4], s));
         if (check) {
@@ -2177,7 +2205,8 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.wins = (int64_t)c1.wins;
     stats.displaced = (int64_t)c1.displaced;
     stats.launches = launches;
-    stats.refine_launches = small ? 1 : (int64_t)sched.size() * (1 + pu_rounds + (tail_T > 0 ? 1 : 0) + (sweep ? 1 : 0) + (team_T > 0 ? 1 + pu_rounds : 0));
+    stats.refine_launches = small ? 1 : (int64_t)sched.size() * (1 + pu_rounds + (tail_T > 0 ? 1 : 0) + (sweep ? 1 : 0) + (team_T > 0 ? 1 + pu_rounds : 0) +
+                                                      tail_updates * (team_T > 0 ? 2 : 1));
     stats.small_kernel = small ? 1 : 0;
     stats.tail_price_update_ms = 1e-6 * (double)c1.pu_tail_ns;
     stats.team_phases = c1.team_phases;

@@ -423,6 +423,25 @@ def test_team_refine_keeps_the_optimum(la, pu):
     assert team > 0
 
 
+@pytest.mark.parametrize("tu", [1, 3])
+def test_tail_price_updates_keep_the_optimum(la, tu):
+    """la_options.tail_updates lets the tail kernel stop after 2n scans for a
+    grid price update, its rows going to k_pu and back: prices only, so the
+    optimum and the certificate are unchanged, with and without the refine's
+    own updates and the team refine."""
+    cases = json.load(open(os.path.join(GOLDEN, "optimal_costs.json")))["cases"]
+    geo = [c for c in cases if c["workload"] == "geometric-n8192" and c["n"] == 8192][1]
+    updates = 0
+    for C, want, kw in ((synth.instance(geo["workload"], geo["seed"]), geo["cost"],
+                         {"tail_threshold": 128, "price_updates": 4}),
+                        (synth.geometric_costs(1200, 9), None, {"tail_threshold": 64}),
+                        (synth.geometric_costs(1001, 4), None, {"flags": la.LA_FLAG_NO_TEAM_REFINE}),
+                        (synth.uniform_costs(700, 0, 1000, 10), None, {})):
+        st = check(la, C, want, tail_updates=tu, **kw)
+        updates += st["price_updates"]
+    assert updates > 0
+
+
 @pytest.mark.parametrize("cut", [1, 4])
 def test_phase_cutoff_keeps_the_optimum(la, cut):
     """Cutting intermediate phases short leaves the optimum and the final
