@@ -1792,10 +1792,19 @@ cudaError_t launch_refine(cudaStream_t s, int grid, int block, const int32_t *C,
             cudaError_t e = cudaEventRecord(ev_fin, s);
             if (e != cudaSuccess) return e;
         }
-        // rows the tail kernel gave back, if any (an empty queue otherwise)
+        // rows the tail kernel gave back, if any (an empty queue otherwise):
+        // the lists stopped answering, so the team refine takes them at once,
+        // and no tail kernel follows
         k_refine<WIDE, VEC><<<grid, block, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl, budget, L,
-                                                   0, ws.tail_rows, 0, ws.qlist[0], ws.qlist[1], stop_free, 0);
+                                                   0, ws.tail_rows, 0, ws.qlist[0], ws.qlist[1], stop_free,
+                                                   team_T > 0 ? 2 : 0);
         ++launches;
+        if (team_T > 0) {
+            k_team<WIDE, VEC><<<team_T, 32 * kTeamWarps, 0, s>>>(C, n, cmin, np1, eps, qlim, ws.key, ws.qm, ws.ctrl,
+                                                                 budget, L, 0, ws.tail_rows, ws.qlist[0], ws.qlist[1],
+                                                                 stop_free, 0);
+            ++launches;
+        }
     } else if (ev_fin) {
         cudaError_t e = cudaEventRecord(ev_fin, s);
         if (e != cudaSuccess) return e;
@@ -2205,7 +2214,7 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.wins = (int64_t)c1.wins;
     stats.displaced = (int64_t)c1.displaced;
     stats.launches = launches;
-    stats.refine_launches = small ? 1 : (int64_t)sched.size() * (1 + pu_rounds + (tail_T > 0 ? 1 : 0) + (sweep ? 1 : 0) + (team_T > 0 ? 1 + pu_rounds : 0) +
+    stats.refine_launches = small ? 1 : (int64_t)sched.size() * (1 + pu_rounds + (tail_T > 0 ? 1 : 0) + (sweep ? 1 : 0) + (team_T > 0 ? 1 + pu_rounds + (tail_T > 0 ? 1 : 0) : 0) +
                                                       tail_updates * (team_T > 0 ? 2 : 1));
     stats.small_kernel = small ? 1 : 0;
     stats.tail_price_update_ms = 1e-6 * (double)c1.pu_tail_ns;

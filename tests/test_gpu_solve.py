@@ -280,9 +280,9 @@ def test_profile_counts(la):
     assert st["phases"] == 6
     # per phase: the bulk sweep, the refine grid that carries the chains, the
     # team refine it hands its last rows to and, after the one-CTA tail
-    # kernel, a refine launch for any rows the tail gives back (no
-    # price-update rounds by default)
-    assert st["refine_launches"] == 4 * st["phases"]
+    # kernel, a refine launch and a team-refine launch for any rows the tail
+    # gives back (no price-update rounds by default)
+    assert st["refine_launches"] == 5 * st["phases"]
     assert st["team_scans"] <= st["scans"] - st["sweep_scans"] - st["tail_scans"]
     # the sweep makes exactly one bid per row in every phase
     assert st["sweep_scans"] == 1024 * st["phases"]
@@ -421,6 +421,15 @@ def test_team_refine_keeps_the_optimum(la, pu):
         st = check(la, C, want, flags=la.LA_FLAG_NO_TEAM_REFINE, price_updates=pu, **kw)
         assert st["team_phases"] == 0 and st["team_scans"] == 0
     assert team > 0
+
+
+@pytest.mark.parametrize("T", [1, 16, 5000])
+def test_team_threshold_keeps_the_optimum(la, T):
+    """la_options.team_threshold moves the point where the team refine takes
+    a phase over (capped at n / 2): the optimum is the same for any value."""
+    for C in (synth.geometric_costs(1200, 19), synth.uniform_costs(1500, 0, (1 << 20) - 1, 18)):
+        st = check(la, C, team_threshold=T)
+        assert st["team_full_scans"] <= st["team_scans"]
 
 
 @pytest.mark.parametrize("tu", [1, 3])
