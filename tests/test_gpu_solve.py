@@ -423,6 +423,33 @@ def test_team_refine_keeps_the_optimum(la, pu):
     assert team > 0
 
 
+def test_random_option_combinations_against_the_oracle(la):
+    """Thirty seeded instances (uniform with three cost ranges, geometric,
+    and 0..2 costs full of ties; n from 301 to 900) under random
+    combinations of alpha, price updates on the grid and in the tail, tail
+    and team thresholds and flags: every cost equals the oracle's Hungarian
+    optimum, and the matching and the prices pass its certificate."""
+    import random
+    import torch
+    rng = random.Random(2024)
+    for _ in range(30):
+        n = rng.randint(301, 900)
+        kind = rng.choice(["uniform", "geometric", "ties"])
+        seed = rng.randint(0, 10**6)
+        if kind == "uniform":
+            C = synth.uniform_costs(n, 0, rng.choice([100, 10**4, (1 << 20) - 1]), seed)
+        elif kind == "geometric":
+            C = synth.geometric_costs(n, seed)
+        else:
+            C = np.random.default_rng(seed).integers(0, 3, size=(n, n)).astype(np.int32)
+        opts = dict(alpha=rng.choice([4, 10, 48]), price_updates=rng.choice([0, 0, 2, 4]),
+                    tail_threshold=rng.choice([0, 0, 16, 128, -1]), tail_updates=rng.choice([0, 0, 1, 3]),
+                    team_threshold=rng.choice([0, 0, 8, 100, 5000]),
+                    flags=rng.choice([0, 0, 0, la.LA_FLAG_NO_TEAM_REFINE, la.LA_FLAG_TAIL_PRICE_UPDATE,
+                                      la.LA_FLAG_NO_SMALL_KERNEL]))
+        check(la, C, oracle.hungarian(C)[0], **opts)
+
+
 @pytest.mark.parametrize("T", [1, 16, 5000])
 def test_team_threshold_keeps_the_optimum(la, T):
     """la_options.team_threshold moves the point where the team refine takes
