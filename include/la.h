@@ -474,7 +474,9 @@ la_status la_predict_prices_ex(const int32_t *cost, int32_t n, const void *weigh
                                int64_t *prices_out, int64_t *eps0_out);
 
 /* Warm-started exact solve: la_predict_prices_ex, then la_solve_ex from the
- * predicted prices and eps0. Same results as la_solve. */
+ * predicted prices and eps0, with alpha = 4 for n >= 4096 and the default
+ * alpha (10) below: from predicted prices the smaller eps steps measured
+ * faster on large instances. Same results as la_solve. */
 la_status la_solve_warm(const int32_t *cost, int32_t n, const void *weights, void *stream,
                         int32_t *match_out, int64_t *cost_out, la_stats *stats_out);
 

@@ -1121,6 +1121,11 @@ la_status la_solve_warm(const int32_t *cost, int32_t n, const void *weights, voi
     std::memset(&opt, 0, sizeof(opt));
     opt.init_prices = prices;
     opt.eps0 = eps0;
+    // From predicted prices the phases that remain are the ones below a cost
+    // unit, where bids fight over equal costs; on large instances smaller eps
+    // steps there measured faster (geometric n = 8192: alpha 4 about 1.25x
+    // faster than 10), on small ones the default is (n = 1024: 1.3x).
+    opt.alpha = n >= 4096 ? 4 : 0;
     (void)s;
     return la_solve_ex(cost, n, &opt, stream, match_out, cost_out, stats_out);
 }

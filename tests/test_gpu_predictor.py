@@ -175,6 +175,25 @@ def test_warm_solve_is_exact_with_any_weights(la, kind, n):
 
 
 @pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="trained weights not present")
+def test_warm_solve_on_a_large_instance_takes_smaller_eps_steps(la):
+    """From n = 4096 the warm solve descends from the predicted eps0 with
+    alpha = 4 instead of 10 (more, smaller phases); the optimum is the cold
+    solve's."""
+    import torch
+    P = torch.from_numpy(np.fromfile(WEIGHTS, dtype=np.float32)).cuda()
+    C = synth.geometric_costs(4096, 2_000_100)
+    Cd = _dev(C, np.int32)
+    cold = la.solve(Cd)
+    warm = la.solve_warm(Cd, P)
+    assert warm.cost == cold.cost
+    assert oracle.check_matching(C, warm.match.cpu().numpy(), warm.cost) == 0
+    prices, eps0 = la.predict_prices(Cd, P)
+    at10 = la.solve(Cd, init_prices=prices, eps0=eps0)
+    assert at10.cost == cold.cost
+    assert warm.stats["phases"] > at10.stats["phases"]
+
+
+@pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="trained weights not present")
 def test_trained_predictor_gains_over_cold_start(la):
     """On fresh geometric instances (n = 1024, seeds never used in training),
     the trained warm start returns the same exact optimum with far fewer row
