@@ -55,7 +55,7 @@ HEADLINE = "geometric-n8192"
 # stored), alpha (0: tuned on two untimed instances) and further la_options.
 LINES = {
     "geometric-n8192": dict(count=8, alpha=10, options={"price_updates": 4, "tail_threshold": 128}),
-    "uniform-n4096-c2^20": dict(count=10, alpha=48, options={}),
+    "uniform-n4096-c2^20": dict(count=10, alpha=48, options={"alpha_fine": 4}),
     "uniform-n256-c1000": dict(count=100, alpha=10, options={}, steps=100),
 }
 GOLDEN = os.path.join(ROOT, "tests", "golden", "optimal_costs.json")

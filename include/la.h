@@ -118,6 +118,10 @@ typedef struct {
        kernel may stop for in each phase, after 2n row scans of its own each;
        0 (the default) or negative: none. */
     int32_t tail_updates;
+    /* alpha for the phases that start from eps <= 16 (n + 1), sixteen cost
+       units (the eps steps near and below a cost unit, where bids fight over
+       equal costs); 0 (the default): alpha throughout. */
+    int32_t alpha_fine;
 } la_options;
 
 /* la_options.flags: scan every row in full on every bid instead of using

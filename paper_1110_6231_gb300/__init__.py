@@ -55,6 +55,7 @@ class la_options(ctypes.Structure):
         ("phase_cutoff", ctypes.c_int32),
         ("team_threshold", ctypes.c_int32),
         ("tail_updates", ctypes.c_int32),
+        ("alpha_fine", ctypes.c_int32),
     ]
 
 
@@ -409,7 +410,7 @@ class Solution:
 def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bool = False,
           scan_budget: int = 0, profile: bool = False, block_threads: int = 0,
           flags: int = 0, tail_threshold: int = 0, price_updates: int = 0, phase_cutoff: int = 0, team_threshold: int = 0,
-          tail_updates: int = 0,
+          tail_updates: int = 0, alpha_fine: int = 0,
           stream=None, check: bool = True) -> Solution:
     """Exact minimum-cost assignment of a square int32 CUDA tensor ``C``.
 
@@ -445,6 +446,7 @@ def solve(C, *, alpha: int = 0, eps0: int = 0, init_prices=None, want_prices: bo
     opt.phase_cutoff = phase_cutoff
     opt.team_threshold = team_threshold
     opt.tail_updates = tail_updates
+    opt.alpha_fine = alpha_fine
     st = la_stats()
     with torch.cuda.device(dev):
         rc = la_solve_ex(C, n, opt, stream, match, cost, st)

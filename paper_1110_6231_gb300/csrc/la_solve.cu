@@ -2068,12 +2068,15 @@ static la_status solve_locked(const int32_t *cost, int32_t n, const la_options *
     stats.scaled_range = (int64_t)Ct;
     if (Ct >= kRangeLimit || S >= (1ull << 42)) return LA_ERR_OVERFLOW;
 
-    // epsilon schedule (Algorithm 5.0): eps <- max(1, eps / alpha) until 1
+    // epsilon schedule (Algorithm 5.0): eps <- max(1, eps / alpha) until 1,
+    // with alpha_fine (if set) once eps is down to sixteen cost units
     std::vector<unsigned long long> sched;
     {
+        const int alpha_fine = (opt && opt->alpha_fine >= 2) ? opt->alpha_fine : alpha;
         unsigned long long e = eps0 > 0 ? (unsigned long long)eps0 : Ct;
         do {
-            e = std::max<unsigned long long>(1, e / (unsigned long long)alpha);
+            const int a = e <= 16ull * np1 ? alpha_fine : alpha;
+            e = std::max<unsigned long long>(1, e / (unsigned long long)a);
             sched.push_back(e);
         } while (e > 1 && (int)sched.size() < kMaxPhases);
         if (sched.back() != 1) return LA_ERR_INVALID;

@@ -450,6 +450,21 @@ def test_random_option_combinations_against_the_oracle(la):
         check(la, C, oracle.hungarian(C)[0], **opts)
 
 
+def test_alpha_fine_splits_the_last_scales_and_keeps_the_optimum(la):
+    """la_options.alpha_fine divides eps by its own alpha once eps is down to
+    sixteen cost units: more phases at the end of the schedule, the same
+    optimum (the stored one at n = 4096)."""
+    cases = json.load(open(os.path.join(GOLDEN, "optimal_costs.json")))["cases"]
+    uni = [c for c in cases if c["workload"] == "uniform-n4096-c2^20" and c["seed"] == 3][0]
+    C = synth.instance(uni["workload"], uni["seed"])
+    base = check(la, C, uni["cost"], alpha=48)
+    fine = check(la, C, uni["cost"], alpha=48, alpha_fine=4)
+    assert fine["phases"] > base["phases"]
+    # alpha_fine below 2 means alpha throughout
+    assert check(la, C, uni["cost"], alpha=48, alpha_fine=1)["phases"] == base["phases"]
+    check(la, synth.geometric_costs(1200, 23), None, alpha_fine=3)
+
+
 @pytest.mark.parametrize("T", [1, 16, 5000])
 def test_team_threshold_keeps_the_optimum(la, T):
     """la_options.team_threshold moves the point where the team refine takes
