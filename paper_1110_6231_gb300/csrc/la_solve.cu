@@ -56,7 +56,7 @@ constexpr int kTailMaxN = 16384;      // shared-memory keys of the tail kernel (
 template <bool WIDE>
 constexpr int tail_threads() { return WIDE ? 512 : 1024; }
 constexpr int kDefaultTailRows = 32;
-constexpr unsigned kTailGiveUpFull = 64;   // full scans before the tail kernel may give its rows back
+constexpr unsigned kTailGiveUpFull = 16;   // full scans before the tail kernel may give its rows back
 constexpr int kDefaultPuRounds = 0;   // global price updates per phase (off unless asked)
 
 // ---------------------------------------------------------------- kernels
