@@ -376,7 +376,7 @@ k_refine(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned 
 // the row: the best two only once the lists keep failing, as the refine
 // does, else the lanes' best kListK, merged into the row's new list;
 // thread 0 merges the slices and commits the same double push. A list scan
-// is warp 0's alone. The rows are the refine's hand-off (tail_rows and the
+// is warp 0's alone. The rows are a refine launch's hand-off (tail_rows and the
 // rest of the queue). When at most tail_T rows are free and the lists
 // answer (as for the refine's own hand-off), or when a price update is due
 // (pu_T, as in the refine), the rows still held and those never claimed
@@ -844,7 +844,8 @@ __device__ void tail_price_update(const int32_t *__restrict__ C, int n, int cmin
 // when the lists stop answering (more than a quarter of the tail's scans,
 // after kTailGiveUpFull of them, read whole rows), the CTA stops, and every
 // row still free goes back to the row queue for a refine launch over the
-// whole grid that follows the tail kernel in every phase.
+// whole grid that follows the tail kernel in every phase (and hands the rows
+// on to the team refine, whose CTAs share each full scan among 8 warps).
 template <bool WIDE, bool VEC>
 __global__ void __launch_bounds__(tail_threads<WIDE>())
 k_tail(const int32_t *__restrict__ C, int n, int cmin, uint32_t np1, unsigned long long eps,
