@@ -36,3 +36,15 @@ def test_hashed_sources_hold_no_comment_marker_in_a_string():
     for name in bench.SINGLE_SOLVE_SOURCES:
         text = open(os.path.join(csrc, name)).read()
         assert not re.search(r'"[^"\n]*(//|/\*)[^"\n]*"', text), name
+
+
+def test_every_single_solve_line_finds_its_traffic_record():
+    """Each full bench line reports roofline.traffic from a record taken on
+    its own workload, alpha and solver options and on the kernel code built
+    now: a kernel change without a new capture shows up here, not as a null
+    in the next bench line."""
+    roles = {"uniform-n256-c1000": ("k_small",)}
+    for workload, spec in bench.LINES.items():
+        for kernel in roles.get(workload, ("k_refine_sweep", "k_refine", "k_tail")):
+            got = bench.recorded_traffic(workload, spec["alpha"], kernel, spec.get("options"))
+            assert got is not None and got > 0, (workload, kernel)
