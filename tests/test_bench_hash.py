@@ -48,3 +48,14 @@ def test_every_single_solve_line_finds_its_traffic_record():
         for kernel in roles.get(workload, ("k_refine_sweep", "k_refine", "k_tail")):
             got = bench.recorded_traffic(workload, spec["alpha"], kernel, spec.get("options"))
             assert got is not None and got > 0, (workload, kernel)
+
+
+def test_bench_line_options_are_solver_options():
+    """bench.py sets each line's options on la_options by name; a ctypes
+    structure would silently take a misspelt name as a new attribute, so
+    every name must be one of the structure's fields."""
+    import paper_1110_6231_gb300 as la
+    fields = {name for name, _ in la.la_options._fields_}
+    for workload, spec in bench.LINES.items():
+        for name in spec.get("options", {}):
+            assert name in fields, (workload, name)
